@@ -1,0 +1,264 @@
+"""CPU oracle for Parallel Space Saving (arXiv:1606.04669).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path never
+imports this package.
+
+Thin ctypes wrapper over ``pss_oracle.cpp`` (plain single-threaded C++; see
+that file for the paper passages each function follows).  Summaries are
+returned in canonical order: count descending, item ascending.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pss_oracle.cpp")
+_GEN = os.path.join(_HERE, "..", "paper_1606_04669_gb300", "gen", "pss_zipf.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+u64p = ctypes.POINTER(ctypes.c_uint64)
+u32p = ctypes.POINTER(ctypes.c_uint32)
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (single translation unit, a few seconds)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest_src = max(os.path.getmtime(_SRC), os.path.getmtime(_GEN))
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest_src:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.oracle_space_saving.restype = ctypes.c_uint32
+        lib.oracle_space_saving.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.c_uint32, u64p, u64p, u64p, u64p]
+        lib.oracle_combine.restype = ctypes.c_uint32
+        lib.oracle_combine.argtypes = ([u64p, u64p, u64p, ctypes.c_uint32, ctypes.c_uint64,
+                                        ctypes.c_uint64] * 2
+                                       + [ctypes.c_uint32, u64p, u64p, u64p, u64p, u64p])
+        lib.oracle_tree_nodes.restype = ctypes.c_uint64
+        lib.oracle_tree_nodes.argtypes = [ctypes.c_uint64]
+        lib.oracle_pss_tree.restype = ctypes.c_int
+        lib.oracle_pss_tree.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.c_uint32, ctypes.c_uint32, u64p, u64p, u64p, u32p,
+                                        u64p, u64p]
+        lib.oracle_block_summary.restype = ctypes.c_uint32
+        lib.oracle_block_summary.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                             u64p, u64p, u64p, u64p]
+        lib.oracle_query.restype = ctypes.c_uint32
+        lib.oracle_query.argtypes = [u64p, u64p, u64p, ctypes.c_uint32, ctypes.c_uint64,
+                                     ctypes.c_uint32, u64p, u64p, u64p]
+        lib.oracle_block_bounds.restype = None
+        lib.oracle_block_bounds.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                            u64p, u64p]
+        lib.oracle_philox4x32_10.restype = None
+        lib.oracle_philox4x32_10.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint32]
+        lib.oracle_gen_zipf.restype = None
+        lib.oracle_gen_zipf.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                        ctypes.c_double, ctypes.c_int]
+        lib.oracle_gen_zipf_ranks.restype = None
+        lib.oracle_gen_zipf_ranks.argtypes = [u64p, ctypes.c_uint64, ctypes.c_uint64,
+                                              ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                                              ctypes.c_uint64]
+        lib.oracle_rank_to_item.restype = ctypes.c_uint64
+        lib.oracle_rank_to_item.argtypes = [ctypes.c_uint64, ctypes.c_int]
+        lib.oracle_gen_log.restype = ctypes.c_double
+        lib.oracle_gen_log.argtypes = [ctypes.c_double]
+        lib.oracle_gen_exp.restype = ctypes.c_double
+        lib.oracle_gen_exp.argtypes = [ctypes.c_double]
+        _lib = lib
+        return lib
+
+
+def _p64(a: np.ndarray):
+    return a.ctypes.data_as(u64p)
+
+
+def _p32(a: np.ndarray):
+    return a.ctypes.data_as(u32p)
+
+
+@dataclass
+class Summary:
+    """Canonical summary: parallel arrays sorted by (count desc, item asc)."""
+    item: np.ndarray
+    count: np.ndarray
+    err: np.ndarray
+    m: int = 0
+    n_covered: int = 0
+
+    @property
+    def size(self) -> int:
+        return int(self.item.shape[0])
+
+    def entries(self):
+        return list(zip(self.item.tolist(), self.count.tolist(), self.err.tolist()))
+
+
+def _items_array(items) -> tuple[np.ndarray, int]:
+    a = np.ascontiguousarray(items)
+    if a.dtype == np.uint32:
+        return a, 4
+    if a.dtype == np.uint64:
+        return a, 8
+    raise TypeError(f"items must be uint32 or uint64, got {a.dtype}")
+
+
+def block_bounds(n: int, p: int, r: int) -> tuple[int, int]:
+    """Algorithm 1 bounds of block r of p: half-open [left, right)."""
+    lib = _load()
+    lo = np.zeros(1, np.uint64)
+    hi = np.zeros(1, np.uint64)
+    lib.oracle_block_bounds(n, p, r, _p64(lo), _p64(hi))
+    return int(lo[0]), int(hi[0])
+
+
+def space_saving(items, k: int) -> Summary:
+    """Sequential Space Saving with k counters over the whole array (Section 3)."""
+    lib = _load()
+    a, w = _items_array(items)
+    it = np.zeros(k, np.uint64); ct = np.zeros(k, np.uint64); er = np.zeros(k, np.uint64)
+    m = np.zeros(1, np.uint64)
+    sz = lib.oracle_space_saving(a.ctypes.data_as(ctypes.c_void_p), a.shape[0], w, k,
+                                 _p64(it), _p64(ct), _p64(er), _p64(m))
+    return Summary(it[:sz].copy(), ct[:sz].copy(), er[:sz].copy(), int(m[0]), int(a.shape[0]))
+
+
+def block_summary(items, k: int, p: int, r: int) -> Summary:
+    """Space Saving summary of block r of p (Algorithm 1 bounds)."""
+    lib = _load()
+    a, w = _items_array(items)
+    it = np.zeros(k, np.uint64); ct = np.zeros(k, np.uint64); er = np.zeros(k, np.uint64)
+    m = np.zeros(1, np.uint64)
+    sz = lib.oracle_block_summary(a.ctypes.data_as(ctypes.c_void_p), a.shape[0], w, k, p, r,
+                                  _p64(it), _p64(ct), _p64(er), _p64(m))
+    lo, hi = block_bounds(a.shape[0], p, r)
+    return Summary(it[:sz].copy(), ct[:sz].copy(), er[:sz].copy(), int(m[0]), hi - lo)
+
+
+def combine(a: Summary, b: Summary, k: int) -> Summary:
+    """Algorithm 2: combine(S1, S2, k) with Prune(k)."""
+    lib = _load()
+    arrs = []
+    for s in (a, b):
+        arrs.append([np.ascontiguousarray(s.item, np.uint64), np.ascontiguousarray(s.count, np.uint64),
+                     np.ascontiguousarray(s.err, np.uint64)])
+    it = np.zeros(k, np.uint64); ct = np.zeros(k, np.uint64); er = np.zeros(k, np.uint64)
+    m = np.zeros(1, np.uint64); cov = np.zeros(1, np.uint64)
+    (ai, ac, ae), (bi, bc, be) = arrs
+    sz = lib.oracle_combine(_p64(ai), _p64(ac), _p64(ae), a.size, a.m, a.n_covered,
+                            _p64(bi), _p64(bc), _p64(be), b.size, b.m, b.n_covered, k,
+                            _p64(it), _p64(ct), _p64(er), _p64(m), _p64(cov))
+    return Summary(it[:sz].copy(), ct[:sz].copy(), er[:sz].copy(), int(m[0]), int(cov[0]))
+
+
+def tree_level_sizes(p: int) -> list[int]:
+    sizes = [p]
+    while sizes[-1] > 1:
+        sizes.append((sizes[-1] + 1) // 2)
+    return sizes
+
+
+def pss_tree(items, k: int, p: int) -> list[list[Summary]]:
+    """The whole path of Algorithm 1: every level of the reduction tree.
+
+    Level 0 holds the p block summaries; the last level holds the root."""
+    lib = _load()
+    a, w = _items_array(items)
+    nodes = int(lib.oracle_tree_nodes(p))
+    it = np.zeros(nodes * k, np.uint64); ct = np.zeros(nodes * k, np.uint64)
+    er = np.zeros(nodes * k, np.uint64); sz = np.zeros(nodes, np.uint32)
+    m = np.zeros(nodes, np.uint64); cov = np.zeros(nodes, np.uint64)
+    lib.oracle_pss_tree(a.ctypes.data_as(ctypes.c_void_p), a.shape[0], w, k, p, _p64(it), _p64(ct),
+                        _p64(er), _p32(sz), _p64(m), _p64(cov))
+    levels, node = [], 0
+    for width in tree_level_sizes(p):
+        level = []
+        for _ in range(width):
+            s = int(sz[node]); base = node * k
+            level.append(Summary(it[base:base + s].copy(), ct[base:base + s].copy(),
+                                 er[base:base + s].copy(), int(m[node]), int(cov[node])))
+            node += 1
+        levels.append(level)
+    return levels
+
+
+def query(s: Summary, n: int, k: int) -> Summary:
+    """Pruned(global, n, k): entries with count * k > n, canonical order."""
+    lib = _load()
+    si = np.ascontiguousarray(s.item, np.uint64); sc = np.ascontiguousarray(s.count, np.uint64)
+    se = np.ascontiguousarray(s.err, np.uint64)
+    cap = max(s.size, 1)
+    it = np.zeros(cap, np.uint64); ct = np.zeros(cap, np.uint64); er = np.zeros(cap, np.uint64)
+    sz = lib.oracle_query(_p64(si), _p64(sc), _p64(se), s.size, n, k, _p64(it), _p64(ct), _p64(er))
+    return Summary(it[:sz].copy(), ct[:sz].copy(), er[:sz].copy(), s.m, s.n_covered)
+
+
+def parallel_space_saving(items, k: int, p: int) -> tuple[Summary, Summary]:
+    """Algorithm 1 end to end: (root summary, frequent items)."""
+    levels = pss_tree(items, k, p)
+    root = levels[-1][0]
+    n = int(np.asarray(items).shape[0])
+    return root, query(root, n, k)
+
+
+# ---------------------------------------------------------------- generator
+
+def philox4x32_10(counter, key):
+    lib = _load()
+    c = np.array(counter, np.uint32)
+    lib.oracle_philox4x32_10(_p32(c), int(key[0]), int(key[1]))
+    return [int(x) for x in c]
+
+
+def gen_zipf(count: int, *, seed: int, s: float, log2u: int, width: int = 4, stream: int = 0,
+             start: int = 0) -> np.ndarray:
+    """Items [start, start+count) of the seeded Zipf stream (host side)."""
+    lib = _load()
+    out = np.empty(count, np.uint32 if width == 4 else np.uint64)
+    lib.oracle_gen_zipf(out.ctypes.data_as(ctypes.c_void_p), start, count, width, seed, stream,
+                        float(s), log2u)
+    return out
+
+
+def gen_zipf_ranks(count: int, *, seed: int, s: float, n_ranks: int, stream: int = 0,
+                   start: int = 0) -> np.ndarray:
+    lib = _load()
+    out = np.empty(count, np.uint64)
+    lib.oracle_gen_zipf_ranks(_p64(out), start, count, seed, stream, float(s), n_ranks)
+    return out
+
+
+def rank_to_item(r: int, log2u: int) -> int:
+    return int(_load().oracle_rank_to_item(r, log2u))
+
+
+def gen_log(x: float) -> float:
+    return float(_load().oracle_gen_log(x))
+
+
+def gen_exp(x: float) -> float:
+    return float(_load().oracle_gen_exp(x))
