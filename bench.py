@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Benchmark of the Parallel Space Saving hot path on GB300: one JSON line.
+
+A step is one pass of the whole path over the workload: the p block
+summaries (Space Saving, Section 3), the binary combine tree (Algorithm 2)
+and the k-majority query with its result read back to the host (Algorithm 1).
+
+Default workload (the configuration the headline metric is quoted on):
+n = 2^30 uint32 items drawn i.i.d. from Zipf(s = 1.1) over [0, 2^24), seed 2,
+k = 2000 counters, p = 4096 equal blocks, binary merge tree, threshold n/k.
+The 4 GiB input is larger than L2 (129 MB), so no flush is needed between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank runs an independent
+replica on its own GPU (the path is replicated, not sharded) and the value is
+the items of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "items/s & input GB/s (% HBM peak), plain vs batched/served; p50/p99 latency"
+
+WORKLOADS = {
+    "plain": dict(
+        desc="plain single stream: n=2^30 uint32 Zipf(s=1.1) over [0,2^24), seed 2; k=2000; "
+             "p=4096 equal blocks; binary merge tree; query n/k",
+        n=1 << 30, w=4, s=1.1, log2u=24, seed=2, k=2000, p=4096),
+    "small": dict(
+        desc="plain single stream: n=2^20 uint32 Zipf(s=1.1) over [0,2^20), seed 1; k=100; p=8; "
+             "binary merge tree; query n/k",
+        n=1 << 20, w=4, s=1.1, log2u=20, seed=1, k=100, p=8),
+}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(wl, budget_s: float, max_blocks: int = 64):
+    """The oracle, single-threaded on a host core, over the first B blocks of
+    the workload (block summaries + their combine tree + query); B is sized so
+    the oracle works about budget_s seconds.  Input generation is not timed."""
+    import numpy as np
+
+    import oracle
+    n, k, p, w = wl["n"], wl["k"], wl["p"], wl["w"]
+    lo0, hi0 = oracle.block_bounds(n, p, 0)
+    x0 = oracle.gen_zipf(hi0 - lo0, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w)
+    t = time.perf_counter()
+    oracle.space_saving(x0, k)
+    per_block = max(time.perf_counter() - t, 1e-6)
+    blocks = int(max(2, min(max_blocks, p, budget_s / per_block)))
+    hi = oracle.block_bounds(n, p, blocks - 1)[1]
+    x = oracle.gen_zipf(hi, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w)
+    t = time.perf_counter()
+    levels = oracle.pss_tree(x, k, blocks)
+    oracle.query(levels[-1][0], hi, k)
+    dt = time.perf_counter() - t
+    return {"value": hi / dt, "unit": "items/s", "cores": 1, "kind": "oracle",
+            "sample": f"blocks 0..{blocks - 1} of the {p} blocks ({hi} items): block summaries, "
+                      f"their binary combine tree and the query, single-threaded C++",
+            "seconds": dt}
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    n, k, p, w = wl["n"], wl["k"], wl["p"], wl["w"]
+    blocks = min(p, 8)
+    hi = oracle.block_bounds(n, p, blocks - 1)[1]
+    x = oracle.gen_zipf(hi, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w)
+
+    def step():
+        levels = oracle.pss_tree(x, k, blocks)
+        oracle.query(levels[-1][0], hi, k)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t) / args.steps
+    value = hi / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "items/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32" if w == 4 else "u64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": n, "k": k, "p": p},
+        "cpu_baseline": {"value": value, "unit": "items/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: blocks 0..{blocks - 1} of {p} ({hi} items), "
+                                   "block summaries + combine tree + query"},
+        "e2e": {"value": value, "unit": "items/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, wl, rank)
+
+    import numpy as np
+    import torch
+
+    import paper_1606_04669_gb300 as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n, k, p, w = wl["n"], wl["k"], wl["p"], wl["w"]
+    x = P.gen_zipf(n, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], item_bytes=w,
+                   stream_id=rank)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sm = P.summarize(x, k, p, stream=stream)
+        q = sm.query(n, k, stream=stream)
+        sm.close()
+        return q
+
+    for _ in range(max(args.warmup, 0)):
+        q = step()
+    barrier()
+    P.profile_read(reset=True)
+    P.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        q = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = P.profile_read(reset=True)
+    P.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    barrier()
+    value = n * world / (ms / 1e3)
+    hbm, peak_kind = peaks()
+    input_gbs = n * w * world / (ms / 1e3) / 1e9
+
+    # Dominant kernel: the block summaries.  Algorithmic bytes per launch:
+    # read n*w input bytes once, write p*k summary entries (item + 8-byte
+    # count + 8-byte err) and p block headers.
+    sum_ms = prof["summarize_ms"] / max(prof["summarize_calls"], 1)
+    alg_bytes = n * w + p * k * (w + 16) + p * 24
+    achieved = alg_bytes / (sum_ms / 1e3) / 1e9
+    merge_ms = prof["merge_ms"] / max(args.steps, 1)
+    query_ms = prof["query_ms"] / max(prof["query_calls"], 1)
+
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty(n, dtype=x.dtype, pin_memory=True)
+        hx.copy_(x)
+        torch.cuda.synchronize()
+
+        def estep():
+            sm = P.summarize_host(hx, k, p, stream=stream)
+            qq = sm.query(n, k, stream=stream)
+            sm.close()
+            return qq
+
+        for _ in range(max(args.warmup, 1)):
+            qq = estep()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        esteps = max(1, args.steps // 2)
+        e0.record(stream)
+        for _ in range(esteps):
+            qq = estep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / esteps
+        if dist is not None:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": n * world / (ems / 1e3), "unit": "items/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": n * w, "d2h_bytes_per_step": 8 + 24 * qq.size,
+               "api": "pss_summarize_host + pss_query (pinned host input)"}
+        del hx
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(wl, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "items/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32" if w == 4 else "u64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "k": k, "p": p, "item_bytes": w,
+                       "zipf_s": wl["s"], "universe": f"2^{wl['log2u']}", "seed": wl["seed"],
+                       "l2": "input (4 GiB) larger than L2; no flush" if n * w > (256 << 20)
+                       else "input smaller than L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "input_gbs": input_gbs,
+            "hbm_frac": input_gbs / hbm,
+            "hbm_frac_nominal_8tbs": input_gbs / 8000.0,
+            "roofline": {"bound": "hbm", "kernel": "ss_block_kernel (block summaries)",
+                         "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "avg_launch_ms": sum_ms, "algorithmic_bytes": alg_bytes},
+            "breakdown": {"summarize_ms": sum_ms, "merge_tree_ms": merge_ms,
+                          "query_ms": query_ms,
+                          "fractional_overhead": merge_ms / sum_ms if sum_ms > 0 else None},
+            "frequent_items": int(q.size),
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(prof["launches"]),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * pss.h — C ABI of libpss: Parallel Space Saving on one GB300 (sm_103a).
+ *
+ * The method is M. Cafaro, M. Pulimeno, I. Epicoco, G. Aloisio, "Parallel
+ * Space Saving on Multi and Many-Core Processors" (arXiv:1606.04669):
+ *   - the input of n items is split into p blocks with the bounds of
+ *     Algorithm 1 (block r is [floor(r n / p), floor((r+1) n / p)));
+ *   - each block is reduced to a k-counter Space Saving summary (Section 3);
+ *   - the p summaries are merged by the combine operator of Algorithm 2
+ *     (union, count addition, the other summary's minimum added for absent
+ *     items, Prune(k)) in a binary reduction tree (Algorithm 1,
+ *     ParallelReduction);
+ *   - the query reports the k-majority candidates: entries whose count
+ *     exceeds n / k (Algorithm 1, Pruned; threshold of Section 3).
+ *
+ * Conventions shared by every call:
+ *   - Items are unsigned integers of item_bytes = 4 or 8 bytes.
+ *   - Counts and errors are exact unsigned 64-bit integers.  Every entry
+ *     satisfies count - err <= f <= count, f the item's true frequency.
+ *   - A summary keeps at most k entries; its minimum m is the smallest count
+ *     when k entries are in use and 0 otherwise.  Ties are broken
+ *     deterministically: the evicted counter is the least recently updated
+ *     among those with the minimum count; Prune(k) keeps the k largest by
+ *     (count descending, item ascending).
+ *   - Device pointers are plain CUDA device addresses; host pointers are
+ *     ordinary (pageable or pinned) host memory.  `stream` is a cudaStream_t
+ *     passed as void* (NULL = the legacy default stream).
+ *   - Calls that only enqueue GPU work are asynchronous on `stream`; calls
+ *     that return data to the host synchronize `stream`.
+ *   - Every function returns PSS_OK (0) or a negative PSS_E* code; on error
+ *     no output handle is created and nothing is enqueued.
+ *   - Summaries and trees are device-resident and owned by the library;
+ *     release them with pss_free / pss_tree_free.  Their memory comes from
+ *     CUDA's stream-ordered allocator on the stream of the creating call.
+ *     An input buffer is borrowed: it must stay valid until the work enqueued
+ *     on `stream` has passed it.
+ *   - Errors raised inside a kernel (a bounded device loop that ran out)
+ *     are recorded in the produced summary and reported as PSS_EDEVICE by
+ *     the next call that reads it back (pss_export, pss_query,
+ *     pss_tree_read_level).
+ */
+#ifndef PSS_H_
+#define PSS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSS_OK 0
+#define PSS_EINVAL (-1)    /* bad argument: null pointer, k < 2, k > PSS_MAX_K, width not 4/8 ... */
+#define PSS_EMISMATCH (-2) /* merging summaries of different k or item width */
+#define PSS_ENOMEM (-3)    /* device allocation failed */
+#define PSS_ECUDA (-4)     /* a CUDA runtime call failed (launch, copy, sync) */
+#define PSS_ETIMEOUT (-5)  /* a bounded device wait expired */
+#define PSS_EDEVICE (-6)   /* a kernel recorded an error in the summary */
+#define PSS_ERANGE (-7)    /* output capacity too small */
+
+/* Largest k the shared-memory resident summarize kernel supports. */
+#define PSS_MAX_K 4096u
+
+typedef struct pss_summary pss_summary; /* one summary (opaque, device-resident) */
+typedef struct pss_tree pss_tree;       /* every level of one reduction tree */
+
+typedef struct {
+  uint64_t item;  /* the monitored item */
+  uint64_t count; /* estimated frequency f^ (an upper bound on f) */
+  uint64_t err;   /* maximum over-estimation: count - err <= f */
+} pss_entry;
+
+/* Text of a PSS_E* code (static storage). */
+const char* pss_strerror(int code);
+
+/* ABI version of this header (incremented on incompatible changes). */
+int pss_abi_version(void);
+
+/*
+ * pss_summarize — ParallelSpaceSaving(N, n, p, k) of Algorithm 1 up to the
+ * reduction: p block summaries (Section 3 update rule) merged by Algorithm 2
+ * in a binary tree over adjacent pairs (an odd last summary is carried up).
+ *   d_items     device array of n items of item_bytes each (4 or 8);
+ *               may be NULL only when n == 0.
+ *   k           counters per summary, 2 <= k <= PSS_MAX_K.
+ *   p           number of blocks, p >= 1; blocks may be empty when n < p;
+ *               a block must hold fewer than 2^32 items.
+ *   out         receives a new summary (release with pss_free).
+ * Asynchronous on stream.
+ */
+int pss_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
+                  void* stream, pss_summary** out);
+
+/*
+ * pss_summarize_host — pss_summarize for items in HOST memory: the blocks
+ * are copied to the device in up to 16 slabs on a library-owned copy stream,
+ * each slab's block summaries starting as soon as it has landed (copies
+ * overlap the summarize kernel).  h_items should be pinned
+ * (cudaHostAlloc/cudaHostRegister) for the copies to be asynchronous; it
+ * must stay valid until the work enqueued on stream has completed.
+ * Asynchronous on stream.
+ */
+int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
+                       void* stream, pss_summary** out);
+
+/*
+ * pss_summarize_tree — the same computation as pss_summarize, keeping every
+ * level of the reduction tree (level 0 = the p block summaries, last level =
+ * the root) for inspection with pss_tree_read_level.  Asynchronous.
+ */
+int pss_summarize_tree(const void* d_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
+                       void* stream, pss_tree** out);
+
+/* Number of levels of a tree (1 + ceil(log2 p)). */
+int pss_tree_levels(const pss_tree* tree, uint32_t* levels);
+
+/* Number of summaries at `level` of a tree. */
+int pss_tree_level_nodes(const pss_tree* tree, uint32_t level, uint32_t* nodes);
+
+/*
+ * pss_tree_read_level — copy every summary of one tree level to the host,
+ * in the device layout: node j's entries are at [j*k, j*k + sizes[j]) of
+ * items/counts/errs, sorted by item ascending (items widened to 64 bits).
+ * Arrays items, counts, errs hold nodes*k values; sizes, m, n_covered hold
+ * nodes values.  Synchronizes stream.  PSS_EDEVICE if a kernel recorded an
+ * error in that level.
+ */
+int pss_tree_read_level(const pss_tree* tree, uint32_t level, uint64_t* items, uint64_t* counts,
+                        uint64_t* errs, uint32_t* sizes, uint64_t* m, uint64_t* n_covered,
+                        void* stream);
+
+/* A new summary holding a copy of the tree's root (release with pss_free). */
+int pss_tree_root(const pss_tree* tree, void* stream, pss_summary** out);
+
+/* Release a tree (stream-ordered on the stream that created it). */
+void pss_tree_free(pss_tree* tree);
+
+/*
+ * pss_merge — combine(S1, S2, k) of Algorithm 2: union of the items; an item
+ * in both gets count1 + count2 (err1 + err2); an item in one only gets the
+ * other summary's minimum added to its count and to its err; Prune(k) keeps
+ * the k largest by (count descending, item ascending).  Both summaries must
+ * have the same k and item width (else PSS_EMISMATCH).  Asynchronous.
+ */
+int pss_merge(const pss_summary* a, const pss_summary* b, void* stream, pss_summary** out);
+
+/*
+ * pss_query — Pruned(global, n, k) of Algorithm 1: the entries whose count
+ * exceeds n / k (count * k > n, i.e. count >= floor(n/k) + 1, the k-majority
+ * threshold of Section 3), in order of count descending then item
+ * ascending.  n is the length of the stream the summary describes.
+ *   host_out    array of cap entries; *n_out receives the number reported.
+ * PSS_ERANGE if more than cap entries qualify (nothing is written).
+ * Synchronizes stream.
+ */
+int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* host_out, uint32_t cap,
+              uint32_t* n_out, void* stream);
+
+/*
+ * pss_export — copy a whole summary to the host in canonical order (count
+ * descending, item ascending) with its minimum m and the number of stream
+ * items it describes.  host_out holds cap >= k entries (PSS_ERANGE if the
+ * summary holds more than cap).  Synchronizes stream.
+ */
+int pss_export(const pss_summary* summary, pss_entry* host_out, uint32_t cap, uint32_t* size,
+               uint64_t* m, uint64_t* n_covered, void* stream);
+
+/* k and item width of a summary. */
+int pss_summary_info(const pss_summary* summary, uint32_t* k, int* item_bytes);
+
+/* Release a summary (stream-ordered on the stream that created it). */
+void pss_free(pss_summary* summary);
+
+/*
+ * Profiling.  The paper reports run time and the "fractional overhead" of
+ * the reduction relative to the computation (Section 4.1); the library can
+ * time its own kernel groups with CUDA events on the launching stream.
+ */
+typedef struct {
+  uint64_t launches;        /* kernels launched by the library since the last reset (always counted) */
+  uint64_t summarize_calls; /* timed summarize-kernel launches */
+  uint64_t merge_levels;    /* timed merge-level launches */
+  uint64_t query_calls;     /* timed query/export launches */
+  double summarize_ms;      /* device time of the summarize kernels */
+  double merge_ms;          /* device time of the merge tree */
+  double query_ms;          /* device time of the query/export kernels */
+} pss_profile;
+
+/* on != 0: record CUDA events around every kernel group from now on. */
+int pss_profile_enable(int on);
+
+/* Accumulated counters (waits for the recorded events); reset != 0 zeroes them. */
+int pss_profile_read(pss_profile* out, int reset);
+
+/*
+ * pss_gen_zipf — fill d_out with items [start, start + count) of the seeded
+ * synthetic stream (seed, stream_id): Zipf(s) ranks over [1, 2^log2u] mapped
+ * by a fixed bijection onto [0, 2^log2u) (the paper's inputs are Zipf
+ * streams of skew 1.1 and 1.8, Section 4.1).  item_bytes 4 requires
+ * log2u <= 32; log2u <= 63.  Asynchronous.
+ */
+int pss_gen_zipf(void* d_out, uint64_t count, int item_bytes, uint64_t seed, uint32_t stream_id,
+                 uint64_t start, double s, int log2u, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSS_H_ */

@@ -1,0 +1,540 @@
+// api.cu — the extern "C" boundary of libpss (declared in include/pss.h).
+//
+// Argument checks, device memory of summaries (CUDA stream-ordered
+// allocator) and kernel sequencing.  Every step of the computation runs in
+// the kernels of summarize.cu, merge.cu and canon.cu.
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "pss_internal.cuh"
+#include "pss_kernels.cuh"
+
+using namespace pss;
+
+struct pss_summary {
+  uint32_t k;
+  int item_bytes;
+  void* mem;            // one set of one node (set_layout)
+  cudaStream_t stream;  // stream of the creating call; frees are ordered on it
+};
+
+struct pss_tree {
+  uint32_t k, p;
+  int item_bytes;
+  cudaStream_t stream;
+  std::vector<void*> mem;       // one set per level
+  std::vector<uint32_t> nodes;  // summaries per level
+};
+
+namespace {
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return PSS_OK;
+  if (e == cudaErrorMemoryAllocation) return PSS_ENOMEM;
+  return PSS_ECUDA;
+}
+
+// Keep freed stream-ordered memory in the pool (no return to the OS between
+// calls), once per device.
+std::mutex g_pool_mu;
+std::vector<int> g_pool_done;
+
+cudaError_t prepare_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  for (int d : g_pool_done)
+    if (d == dev) return cudaSuccess;
+  cudaMemPool_t pool;
+  e = cudaDeviceGetDefaultMemPool(&pool, dev);
+  if (e != cudaSuccess) return e;
+  uint64_t thr = ~0ull;
+  e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  if (e != cudaSuccess) return e;
+  g_pool_done.push_back(dev);
+  return cudaSuccess;
+}
+
+cudaError_t alloc_set(uint32_t nodes, uint32_t k, int w, cudaStream_t s, void** mem) {
+  SetLayout L = set_layout(nodes, k, w);
+  cudaError_t e = cudaMallocAsync(mem, L.total, s);
+  if (e != cudaSuccess) {
+    *mem = nullptr;
+    return e;
+  }
+  e = cudaMemsetAsync((char*)*mem + L.status, 0, 4, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(*mem, s);
+    *mem = nullptr;
+  }
+  return e;
+}
+
+size_t max_optin_smem() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return (size_t)v;
+}
+
+int check_k_width(uint32_t k, int w) {
+  if (w != 4 && w != 8) return PSS_EINVAL;
+  if (k < 2 || k > PSS_MAX_K) return PSS_EINVAL;
+  return PSS_OK;
+}
+
+// Level 0 (the block summaries, enqueued by `level0`) and the merge levels.
+template <typename ItemT, typename Level0>
+int run_tree(uint32_t k, uint32_t p, cudaStream_t s, bool keep, std::vector<void*>& mems,
+             std::vector<uint32_t>& nodes, Level0 level0) {
+  const int w = (int)sizeof(ItemT);
+  auto fail = [&](cudaError_t e) {
+    for (void* m : mems)
+      if (m) cudaFreeAsync(m, s);
+    mems.clear();
+    nodes.clear();
+    return from_cuda(e);
+  };
+  void* m0 = nullptr;
+  cudaError_t e = alloc_set(p, k, w, s, &m0);
+  if (e != cudaSuccess) return fail(e);
+  mems.push_back(m0);
+  nodes.push_back(p);
+  {
+    ProfScope prof(PROF_SUMMARIZE, s, 1);
+    e = level0(set_view<ItemT>(m0, p, k));
+  }
+  if (e != cudaSuccess) return fail(e);
+  uint32_t levels = 0;
+  for (uint32_t w2 = p; w2 > 1; w2 = (w2 + 1) / 2) ++levels;
+  ProfScope prof(PROF_MERGE, s, levels);
+  while (nodes.back() > 1) {
+    const uint32_t cur = nodes.back(), nxt = (cur + 1) / 2;
+    void* mm = nullptr;
+    e = alloc_set(nxt, k, w, s, &mm);
+    if (e != cudaSuccess) return fail(e);
+    e = launch_merge_level<ItemT>(set_view<ItemT>(mems.back(), cur, k), set_view<ItemT>(mm, nxt, k),
+                                  s);
+    count_launches(1);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(mm, s);
+      return fail(e);
+    }
+    if (!keep) {
+      cudaFreeAsync(mems.back(), s);
+      mems.back() = nullptr;
+    }
+    mems.push_back(mm);
+    nodes.push_back(nxt);
+  }
+  return PSS_OK;
+}
+
+template <typename ItemT>
+int run_tree_device(const void* d_items, uint64_t n, uint32_t k, uint32_t p, cudaStream_t s,
+                    bool keep, std::vector<void*>& mems, std::vector<uint32_t>& nodes) {
+  return run_tree<ItemT>(k, p, s, keep, mems, nodes, [&](SetView<ItemT> v0) {
+    count_launches(1);
+    return launch_summarize_blocks<ItemT>((const ItemT*)d_items, n, p, 0, p, v0, 0, s);
+  });
+}
+
+// One non-blocking copy stream per device for host-input calls.
+std::mutex g_copy_mu;
+std::vector<std::pair<int, cudaStream_t>> g_copy_streams;
+
+cudaError_t copy_stream(cudaStream_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_copy_mu);
+  for (auto& ds : g_copy_streams)
+    if (ds.first == dev) {
+      *out = ds.second;
+      return cudaSuccess;
+    }
+  cudaStream_t cs;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  g_copy_streams.push_back({dev, cs});
+  *out = cs;
+  return cudaSuccess;
+}
+
+// Host input: the blocks are copied in `groups` slabs on the copy stream;
+// the summarize kernel of slab g starts as soon as slab g has landed, so the
+// copy of slab g+1 overlaps it.
+template <typename ItemT>
+int run_tree_host(const void* h_items, uint64_t n, uint32_t k, uint32_t p, cudaStream_t s,
+                  std::vector<void*>& mems, std::vector<uint32_t>& nodes) {
+  const size_t w = sizeof(ItemT);
+  cudaStream_t cs;
+  cudaError_t e = copy_stream(&cs);
+  if (e != cudaSuccess) return from_cuda(e);
+  void* dbuf = nullptr;
+  if (n) {
+    e = cudaMallocAsync(&dbuf, n * w, s);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  const uint32_t groups = p < 16 ? p : 16;
+  std::vector<cudaEvent_t> evs;
+  auto make_event = [&](cudaEvent_t* ev) {
+    cudaError_t r = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (r == cudaSuccess) evs.push_back(*ev);
+    return r;
+  };
+  cudaEvent_t ready;
+  e = make_event(&ready);
+  if (e == cudaSuccess) e = cudaEventRecord(ready, s);        // dbuf allocated on s
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
+  int rc = from_cuda(e);
+  if (rc == PSS_OK) {
+    rc = run_tree<ItemT>(k, p, s, false, mems, nodes, [&](SetView<ItemT> v0) {
+      cudaError_t r = cudaSuccess;
+      for (uint32_t g = 0; g < groups && r == cudaSuccess; ++g) {
+        const uint32_t r0 = (uint32_t)((uint64_t)g * p / groups);
+        const uint32_t r1 = (uint32_t)((uint64_t)(g + 1) * p / groups);
+        const uint64_t lo = block_bound(r0, n, p), hi = block_bound(r1, n, p);
+        if (hi > lo) {
+          cudaEvent_t landed;
+          r = make_event(&landed);
+          if (r == cudaSuccess)
+            r = cudaMemcpyAsync((char*)dbuf + lo * w, (const char*)h_items + lo * w, (hi - lo) * w,
+                                cudaMemcpyHostToDevice, cs);
+          if (r == cudaSuccess) r = cudaEventRecord(landed, cs);
+          if (r == cudaSuccess) r = cudaStreamWaitEvent(s, landed, 0);
+        }
+        if (r == cudaSuccess && r1 > r0) {
+          count_launches(1);
+          r = launch_summarize_blocks<ItemT>((const ItemT*)dbuf, n, p, r0, r1 - r0, v0, r0, s);
+        }
+      }
+      return r;
+    });
+  }
+  if (dbuf) cudaFreeAsync(dbuf, s);
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+  return rc;
+}
+
+int validate_summarize(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p) {
+  int rc = check_k_width(k, w);
+  if (rc) return rc;
+  if (p == 0) return PSS_EINVAL;
+  if (n > 0 && d_items == nullptr) return PSS_EINVAL;
+  if ((n + p - 1) / p >= (1ull << 32)) return PSS_EINVAL;  // a block must be < 2^32 items
+  const size_t need = w == 4 ? ss_smem_bytes<uint32_t>(k) : ss_smem_bytes<u64>(k);
+  const size_t need_m = w == 4 ? merge_smem_bytes<uint32_t>(k) : merge_smem_bytes<u64>(k);
+  const size_t have = max_optin_smem();
+  if (need > have || need_m > have) return PSS_EINVAL;
+  return PSS_OK;
+}
+
+int tree_common(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p, cudaStream_t s,
+                bool keep, std::vector<void*>& mems, std::vector<uint32_t>& nodes) {
+  cudaError_t e = prepare_device();
+  if (e != cudaSuccess) return from_cuda(e);
+  int rc = validate_summarize(d_items, n, w, k, p);
+  if (rc) return rc;
+  return w == 4 ? run_tree_device<uint32_t>(d_items, n, k, p, s, keep, mems, nodes)
+                : run_tree_device<u64>(d_items, n, k, p, s, keep, mems, nodes);
+}
+
+// Canonical copy-out of one node; filter selects the query.
+int canon_out(void* set_mem, uint32_t nodes, uint32_t node, uint32_t k, int w, uint64_t n,
+              uint32_t kq, int filter, pss_entry* host_out, uint32_t cap, uint32_t* n_out,
+              cudaStream_t s) {
+  const size_t ebytes = (size_t)k * sizeof(pss_entry);
+  void* dmem = nullptr;
+  cudaError_t e = cudaMallocAsync(&dmem, ebytes + 16, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  pss_entry* d_out = (pss_entry*)dmem;
+  uint32_t* d_n = (uint32_t*)((char*)dmem + ebytes);
+  {
+  ProfScope prof(PROF_QUERY, s, 1);
+  count_launches(1);
+  e = (w == 4) ? launch_canon<uint32_t>(set_view<uint32_t>(set_mem, nodes, k), node, n, kq, filter,
+                                        d_out, d_n, s)
+               : launch_canon<u64>(set_view<u64>(set_mem, nodes, k), node, n, kq, filter, d_out,
+                                   d_n, s);
+  }
+  uint32_t hn[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hn, d_n, sizeof(hn), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int rc = from_cuda(e);
+  if (rc == PSS_OK && hn[1] != 0) rc = PSS_EDEVICE;
+  if (rc == PSS_OK && hn[0] > cap) rc = PSS_ERANGE;
+  if (rc == PSS_OK && hn[0] > 0) {
+    e = cudaMemcpyAsync(host_out, d_out, (size_t)hn[0] * sizeof(pss_entry), cudaMemcpyDeviceToHost,
+                        s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    rc = from_cuda(e);
+  }
+  cudaFreeAsync(dmem, s);
+  if (rc == PSS_OK && n_out) *n_out = hn[0];
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pss_strerror(int code) {
+  switch (code) {
+    case PSS_OK: return "success";
+    case PSS_EINVAL: return "invalid argument";
+    case PSS_EMISMATCH: return "summaries have different k or item width";
+    case PSS_ENOMEM: return "device memory allocation failed";
+    case PSS_ECUDA: return "CUDA runtime error";
+    case PSS_ETIMEOUT: return "bounded device wait expired";
+    case PSS_EDEVICE: return "a kernel recorded an error in the summary";
+    case PSS_ERANGE: return "output capacity too small";
+    default: return "unknown error";
+  }
+}
+
+int pss_abi_version(void) { return 1; }
+
+int pss_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
+                  void* stream, pss_summary** out) {
+  if (!out) return PSS_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<void*> mems;
+  std::vector<uint32_t> nodes;
+  int rc = tree_common(d_items, n, item_bytes, k, p, s, false, mems, nodes);
+  if (rc) return rc;
+  pss_summary* sm = new (std::nothrow) pss_summary;
+  if (!sm) {
+    cudaFreeAsync(mems.back(), s);
+    return PSS_ENOMEM;
+  }
+  sm->k = k;
+  sm->item_bytes = item_bytes;
+  sm->mem = mems.back();
+  sm->stream = s;
+  *out = sm;
+  return PSS_OK;
+}
+
+int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
+                       void* stream, pss_summary** out) {
+  if (!out) return PSS_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prepare_device();
+  if (e != cudaSuccess) return from_cuda(e);
+  int rc = validate_summarize(h_items, n, item_bytes, k, p);
+  if (rc) return rc;
+  std::vector<void*> mems;
+  std::vector<uint32_t> nodes;
+  rc = item_bytes == 4 ? run_tree_host<uint32_t>(h_items, n, k, p, s, mems, nodes)
+                       : run_tree_host<u64>(h_items, n, k, p, s, mems, nodes);
+  if (rc) return rc;
+  pss_summary* sm = new (std::nothrow) pss_summary;
+  if (!sm) {
+    cudaFreeAsync(mems.back(), s);
+    return PSS_ENOMEM;
+  }
+  sm->k = k;
+  sm->item_bytes = item_bytes;
+  sm->mem = mems.back();
+  sm->stream = s;
+  *out = sm;
+  return PSS_OK;
+}
+
+int pss_summarize_tree(const void* d_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
+                       void* stream, pss_tree** out) {
+  if (!out) return PSS_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  pss_tree* t = new (std::nothrow) pss_tree;
+  if (!t) return PSS_ENOMEM;
+  int rc = tree_common(d_items, n, item_bytes, k, p, s, true, t->mem, t->nodes);
+  if (rc) {
+    delete t;
+    return rc;
+  }
+  t->k = k;
+  t->p = p;
+  t->item_bytes = item_bytes;
+  t->stream = s;
+  *out = t;
+  return PSS_OK;
+}
+
+int pss_tree_levels(const pss_tree* tree, uint32_t* levels) {
+  if (!tree || !levels) return PSS_EINVAL;
+  *levels = (uint32_t)tree->nodes.size();
+  return PSS_OK;
+}
+
+int pss_tree_level_nodes(const pss_tree* tree, uint32_t level, uint32_t* nodes) {
+  if (!tree || !nodes || level >= tree->nodes.size()) return PSS_EINVAL;
+  *nodes = tree->nodes[level];
+  return PSS_OK;
+}
+
+int pss_tree_read_level(const pss_tree* tree, uint32_t level, uint64_t* items, uint64_t* counts,
+                        uint64_t* errs, uint32_t* sizes, uint64_t* m, uint64_t* n_covered,
+                        void* stream) {
+  if (!tree || level >= tree->nodes.size()) return PSS_EINVAL;
+  if (!items || !counts || !errs || !sizes || !m || !n_covered) return PSS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t nodes = tree->nodes[level], k = tree->k;
+  const int w = tree->item_bytes;
+  const SetLayout L = set_layout(nodes, k, w);
+  const char* base = (const char*)tree->mem[level];
+  const size_t e = (size_t)nodes * k;
+  std::vector<uint32_t> narrow;
+  uint32_t status = 0;
+  cudaError_t ce;
+  if (w == 4) {
+    narrow.resize(e);
+    ce = cudaMemcpyAsync(narrow.data(), base + L.item, e * 4, cudaMemcpyDeviceToHost, s);
+  } else {
+    ce = cudaMemcpyAsync(items, base + L.item, e * 8, cudaMemcpyDeviceToHost, s);
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(counts, base + L.count, e * 8, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(errs, base + L.err, e * 8, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(sizes, base + L.size, (size_t)nodes * 4, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(m, base + L.m, (size_t)nodes * 8, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(n_covered, base + L.ncov, (size_t)nodes * 8, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&status, base + L.status, 4, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return from_cuda(ce);
+  if (w == 4)
+    for (size_t i = 0; i < e; ++i) items[i] = narrow[i];
+  return status ? PSS_EDEVICE : PSS_OK;
+}
+
+int pss_tree_root(const pss_tree* tree, void* stream, pss_summary** out) {
+  if (!tree || !out) return PSS_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t k = tree->k;
+  const int w = tree->item_bytes;
+  const SetLayout L = set_layout(1, k, w);
+  void* mem = nullptr;
+  cudaError_t e = cudaMallocAsync(&mem, L.total, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = cudaMemcpyAsync(mem, tree->mem.back(), L.total, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(mem, s);
+    return from_cuda(e);
+  }
+  pss_summary* sm = new (std::nothrow) pss_summary;
+  if (!sm) {
+    cudaFreeAsync(mem, s);
+    return PSS_ENOMEM;
+  }
+  sm->k = k;
+  sm->item_bytes = w;
+  sm->mem = mem;
+  sm->stream = s;
+  *out = sm;
+  return PSS_OK;
+}
+
+void pss_tree_free(pss_tree* tree) {
+  if (!tree) return;
+  for (void* m : tree->mem)
+    if (m) cudaFreeAsync(m, tree->stream);
+  delete tree;
+}
+
+int pss_merge(const pss_summary* a, const pss_summary* b, void* stream, pss_summary** out) {
+  if (!a || !b || !out) return PSS_EINVAL;
+  *out = nullptr;
+  if (a->k != b->k || a->item_bytes != b->item_bytes) return PSS_EMISMATCH;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prepare_device();
+  if (e != cudaSuccess) return from_cuda(e);
+  const uint32_t k = a->k;
+  const int w = a->item_bytes;
+  void* mem = nullptr;
+  e = alloc_set(1, k, w, s, &mem);
+  if (e != cudaSuccess) return from_cuda(e);
+  ProfScope prof(PROF_MERGE, s, 1);
+  count_launches(1);
+  if (w == 4)
+    e = launch_merge_pair<uint32_t>(set_view<uint32_t>(a->mem, 1, k), 0,
+                                    set_view<uint32_t>(b->mem, 1, k), 0,
+                                    set_view<uint32_t>(mem, 1, k), s);
+  else
+    e = launch_merge_pair<u64>(set_view<u64>(a->mem, 1, k), 0, set_view<u64>(b->mem, 1, k), 0,
+                               set_view<u64>(mem, 1, k), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(mem, s);
+    return from_cuda(e);
+  }
+  pss_summary* sm = new (std::nothrow) pss_summary;
+  if (!sm) {
+    cudaFreeAsync(mem, s);
+    return PSS_ENOMEM;
+  }
+  sm->k = k;
+  sm->item_bytes = w;
+  sm->mem = mem;
+  sm->stream = s;
+  *out = sm;
+  return PSS_OK;
+}
+
+int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* host_out, uint32_t cap,
+              uint32_t* n_out, void* stream) {
+  if (!summary || !n_out || k < 2) return PSS_EINVAL;
+  if (cap > 0 && !host_out) return PSS_EINVAL;
+  return canon_out(summary->mem, 1, 0, summary->k, summary->item_bytes, n, k, 1, host_out, cap,
+                   n_out, (cudaStream_t)stream);
+}
+
+int pss_export(const pss_summary* summary, pss_entry* host_out, uint32_t cap, uint32_t* size,
+               uint64_t* m, uint64_t* n_covered, void* stream) {
+  if (!summary || !size) return PSS_EINVAL;
+  if (cap > 0 && !host_out) return PSS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = canon_out(summary->mem, 1, 0, summary->k, summary->item_bytes, 0, 1, 0, host_out, cap,
+                     size, s);
+  if (rc) return rc;
+  const SetLayout L = set_layout(1, summary->k, summary->item_bytes);
+  uint64_t hm = 0, hc = 0;
+  cudaError_t e = cudaMemcpyAsync(&hm, (char*)summary->mem + L.m, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, (char*)summary->mem + L.ncov, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (m) *m = hm;
+  if (n_covered) *n_covered = hc;
+  return PSS_OK;
+}
+
+int pss_summary_info(const pss_summary* summary, uint32_t* k, int* item_bytes) {
+  if (!summary) return PSS_EINVAL;
+  if (k) *k = summary->k;
+  if (item_bytes) *item_bytes = summary->item_bytes;
+  return PSS_OK;
+}
+
+void pss_free(pss_summary* summary) {
+  if (!summary) return;
+  if (summary->mem) cudaFreeAsync(summary->mem, summary->stream);
+  delete summary;
+}
+
+int pss_gen_zipf(void* d_out, uint64_t count, int item_bytes, uint64_t seed, uint32_t stream_id,
+                 uint64_t start, double s, int log2u, void* stream) {
+  if (item_bytes != 4 && item_bytes != 8) return PSS_EINVAL;
+  if (count > 0 && !d_out) return PSS_EINVAL;
+  if (log2u < 1 || log2u > 63 || (item_bytes == 4 && log2u > 32)) return PSS_EINVAL;
+  if (!(s > 0.0) || s > 64.0) return PSS_EINVAL;
+  if (count > 0) count_launches(1);
+  return from_cuda(launch_gen_zipf(d_out, count, item_bytes, seed, stream_id, start, s, log2u,
+                                   (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// pss_kernels.cuh — launch entry points of the device kernels (host side).
+#pragma once
+
+#include "pss_internal.cuh"
+
+namespace pss {
+
+constexpr int SS_BS = 256;     // threads per CTA of the summarize kernel (= window size)
+constexpr int MERGE_BS = 512;  // threads per CTA of the combine kernel
+constexpr int CANON_BS = 1024; // threads per CTA of the query/export kernel
+
+// Shared memory of one summarize CTA for k counters.
+template <typename ItemT>
+size_t ss_smem_bytes(uint32_t k);
+
+// Blocks r0 .. r0+count-1 of p (Algorithm 1 bounds over n items) into nodes
+// node0 .. node0+count-1 of `out`.
+template <typename ItemT>
+cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
+                                    uint32_t count, SetView<ItemT> out, uint32_t node0,
+                                    cudaStream_t stream);
+
+template <typename ItemT>
+size_t merge_smem_bytes(uint32_t k);
+
+// One level of the reduction tree: out node j = combine(in node 2j, in node
+// 2j+1), or a copy of in node 2j when it has no partner.
+template <typename ItemT>
+cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream);
+
+// Merge of two single summaries (node ia of a, node ib of b) into node 0 of out.
+template <typename ItemT>
+cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, uint32_t ib,
+                              SetView<ItemT> out, cudaStream_t stream);
+
+// Canonical export of node `node`: entries with (filter == 0) or
+// count * kq > n, sorted by (count desc, item asc), written to out[0..*out_n).
+template <typename ItemT>
+cudaError_t launch_canon(SetView<ItemT> in, uint32_t node, u64 n, uint32_t kq, int filter,
+                         pss_entry* out, uint32_t* out_n, cudaStream_t stream);
+
+template <typename ItemT>
+cudaError_t launch_copy_node(SetView<ItemT> in, uint32_t node, SetView<ItemT> out,
+                             uint32_t out_node, cudaStream_t stream);
+
+// Kernel-group timing (profile.cu): categories of ProfScope.
+enum ProfCat : int { PROF_SUMMARIZE = 0, PROF_MERGE = 1, PROF_QUERY = 2 };
+
+// Records CUDA events on `s` around its lifetime when profiling is enabled;
+// `units` is what the group counts as launches of its category.
+class ProfScope {
+ public:
+  ProfScope(int cat, cudaStream_t s, uint64_t units);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  int cat_;
+  cudaStream_t s_;
+  uint64_t units_;
+  cudaEvent_t start_ = nullptr, end_ = nullptr;
+  bool active_ = false;
+};
+
+// Adds n to the library's launch counter.
+void count_launches(uint64_t n);
+
+cudaError_t launch_gen_zipf(void* out, u64 count, int item_bytes, u64 seed, uint32_t stream_id,
+                            u64 start, double s, int log2u, cudaStream_t stream);
+
+}  // namespace pss

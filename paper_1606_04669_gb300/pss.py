@@ -1,0 +1,327 @@
+"""Python binding of libpss (include/pss.h): argument marshalling only.
+
+Every step of Parallel Space Saving runs in the library's CUDA kernels; this
+module turns torch tensors into device pointers, torch streams into
+cudaStream_t handles and PSS_E* codes into exceptions.  There is no CPU
+fallback: if libpss cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+PSS_OK = 0
+PSS_EINVAL = -1
+PSS_EMISMATCH = -2
+PSS_ENOMEM = -3
+PSS_ECUDA = -4
+PSS_ETIMEOUT = -5
+PSS_EDEVICE = -6
+PSS_ERANGE = -7
+PSS_MAX_K = 4096
+
+_lock = threading.Lock()
+_lib = None
+
+vp = ctypes.c_void_p
+u32 = ctypes.c_uint32
+u64 = ctypes.c_uint64
+u64p = ctypes.POINTER(ctypes.c_uint64)
+u32p = ctypes.POINTER(ctypes.c_uint32)
+
+
+class PssError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("summarize_calls", ctypes.c_uint64),
+                ("merge_levels", ctypes.c_uint64), ("query_calls", ctypes.c_uint64),
+                ("summarize_ms", ctypes.c_double), ("merge_ms", ctypes.c_double),
+                ("query_ms", ctypes.c_double)]
+
+
+class Entry(ctypes.Structure):
+    _fields_ = [("item", ctypes.c_uint64), ("count", ctypes.c_uint64), ("err", ctypes.c_uint64)]
+
+
+# Every function of include/pss.h: name -> (restype, argtypes).
+SIGNATURES = {
+    "pss_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pss_abi_version": (ctypes.c_int, []),
+    "pss_summarize": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, ctypes.POINTER(vp)]),
+    "pss_summarize_host": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, ctypes.POINTER(vp)]),
+    "pss_summarize_tree": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, ctypes.POINTER(vp)]),
+    "pss_tree_levels": (ctypes.c_int, [vp, u32p]),
+    "pss_tree_level_nodes": (ctypes.c_int, [vp, u32, u32p]),
+    "pss_tree_read_level": (ctypes.c_int, [vp, u32, u64p, u64p, u64p, u32p, u64p, u64p, vp]),
+    "pss_tree_root": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
+    "pss_tree_free": (None, [vp]),
+    "pss_merge": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
+    "pss_query": (ctypes.c_int, [vp, u64, u32, ctypes.POINTER(Entry), u32, u32p, vp]),
+    "pss_export": (ctypes.c_int, [vp, ctypes.POINTER(Entry), u32, u32p, u64p, u64p, vp]),
+    "pss_summary_info": (ctypes.c_int, [vp, u32p, ctypes.POINTER(ctypes.c_int)]),
+    "pss_free": (None, [vp]),
+    "pss_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "pss_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
+    "pss_gen_zipf": (ctypes.c_int, [vp, u64, ctypes.c_int, u64, u32, u64, ctypes.c_double,
+                                    ctypes.c_int, vp]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpss.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libpss.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().pss_strerror(code).decode()
+    except Exception:  # the library itself failed to load
+        return f"error {code}"
+
+
+def _check(rc: int, what: str):
+    if rc != PSS_OK:
+        raise PssError(rc, what)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _item_bytes(t) -> int:
+    import torch
+    if t.dtype in (torch.int32, torch.uint32):
+        return 4
+    if t.dtype in (torch.int64, torch.uint64):
+        return 8
+    raise TypeError(f"items must be a 4- or 8-byte integer tensor, got {t.dtype}")
+
+
+def _check_items(items):
+    if not items.is_cuda:
+        raise ValueError("items must be a CUDA tensor (the library has no CPU path)")
+    if not items.is_contiguous():
+        raise ValueError("items must be contiguous")
+    return _item_bytes(items)
+
+
+@dataclass
+class Exported:
+    """A summary in canonical order (count desc, item asc)."""
+    item: np.ndarray
+    count: np.ndarray
+    err: np.ndarray
+    m: int
+    n_covered: int
+
+    @property
+    def size(self) -> int:
+        return int(self.item.shape[0])
+
+
+def _entries_to_arrays(buf, n):
+    if not n:
+        z = np.zeros(0, np.uint64)
+        return z, z.copy(), z.copy()
+    raw = np.frombuffer(memoryview(buf), dtype=np.uint64, count=3 * n).reshape(n, 3)
+    return raw[:, 0].copy(), raw[:, 1].copy(), raw[:, 2].copy()
+
+
+class Summary:
+    """A device-resident summary owned by libpss (freed on close / GC)."""
+
+    def __init__(self, handle: int, stream=None):
+        self._h = vp(handle)
+        k = u32()
+        w = ctypes.c_int()
+        _check(load().pss_summary_info(self._h, ctypes.byref(k), ctypes.byref(w)), "pss_summary_info")
+        self.k = int(k.value)
+        self.item_bytes = int(w.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self, stream=None) -> Exported:
+        buf = (Entry * self.k)()
+        size = u32()
+        m = u64()
+        cov = u64()
+        _check(load().pss_export(self._h, buf, self.k, ctypes.byref(size), ctypes.byref(m),
+                                 ctypes.byref(cov), vp(_stream_handle(stream))), "pss_export")
+        it, ct, er = _entries_to_arrays(buf, size.value)
+        return Exported(it, ct, er, int(m.value), int(cov.value))
+
+    def query(self, n: int, k: int | None = None, stream=None) -> Exported:
+        kq = self.k if k is None else int(k)
+        buf = (Entry * self.k)()
+        nout = u32()
+        _check(load().pss_query(self._h, int(n), kq, buf, self.k, ctypes.byref(nout),
+                                vp(_stream_handle(stream))), "pss_query")
+        it, ct, er = _entries_to_arrays(buf, nout.value)
+        return Exported(it, ct, er, 0, int(n))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().pss_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tree:
+    """Every level of one reduction tree (level 0 = block summaries)."""
+
+    def __init__(self, handle: int):
+        self._h = vp(handle)
+        lv = u32()
+        _check(load().pss_tree_levels(self._h, ctypes.byref(lv)), "pss_tree_levels")
+        self.levels = int(lv.value)
+
+    def nodes(self, level: int) -> int:
+        n = u32()
+        _check(load().pss_tree_level_nodes(self._h, level, ctypes.byref(n)), "pss_tree_level_nodes")
+        return int(n.value)
+
+    def read_level(self, level: int, k: int, stream=None):
+        """Raw device layout of one level: list of (items, counts, errs, m, n_covered) per node,
+        entries sorted by item ascending."""
+        nodes = self.nodes(level)
+        it = np.zeros(nodes * k, np.uint64)
+        ct = np.zeros(nodes * k, np.uint64)
+        er = np.zeros(nodes * k, np.uint64)
+        sz = np.zeros(nodes, np.uint32)
+        m = np.zeros(nodes, np.uint64)
+        cov = np.zeros(nodes, np.uint64)
+        _check(load().pss_tree_read_level(
+            self._h, level, it.ctypes.data_as(u64p), ct.ctypes.data_as(u64p),
+            er.ctypes.data_as(u64p), sz.ctypes.data_as(u32p), m.ctypes.data_as(u64p),
+            cov.ctypes.data_as(u64p), vp(_stream_handle(stream))), "pss_tree_read_level")
+        out = []
+        for j in range(nodes):
+            b, s = j * k, int(sz[j])
+            out.append((it[b:b + s].copy(), ct[b:b + s].copy(), er[b:b + s].copy(), int(m[j]),
+                        int(cov[j])))
+        return out
+
+    def root(self, stream=None) -> Summary:
+        h = vp()
+        _check(load().pss_tree_root(self._h, vp(_stream_handle(stream)), ctypes.byref(h)),
+               "pss_tree_root")
+        return Summary(h.value)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().pss_tree_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def summarize(items, k: int, p: int, stream=None) -> Summary:
+    """pss_summarize: block summaries of p blocks merged by the binary tree."""
+    w = _check_items(items)
+    h = vp()
+    _check(load().pss_summarize(vp(items.data_ptr()), items.numel(), w, int(k), int(p),
+                                vp(_stream_handle(stream)), ctypes.byref(h)), "pss_summarize")
+    return Summary(h.value)
+
+
+def summarize_host(items, k: int, p: int, stream=None) -> Summary:
+    """pss_summarize_host: the same computation on a CPU tensor (pinned for overlap)."""
+    if items.is_cuda:
+        raise ValueError("summarize_host takes a CPU tensor")
+    if not items.is_contiguous():
+        raise ValueError("items must be contiguous")
+    w = _item_bytes(items)
+    h = vp()
+    _check(load().pss_summarize_host(vp(items.data_ptr()), items.numel(), w, int(k), int(p),
+                                     vp(_stream_handle(stream)), ctypes.byref(h)),
+           "pss_summarize_host")
+    return Summary(h.value)
+
+
+def summarize_tree(items, k: int, p: int, stream=None) -> Tree:
+    """pss_summarize_tree: as summarize, keeping every tree level."""
+    w = _check_items(items)
+    h = vp()
+    _check(load().pss_summarize_tree(vp(items.data_ptr()), items.numel(), w, int(k), int(p),
+                                     vp(_stream_handle(stream)), ctypes.byref(h)),
+           "pss_summarize_tree")
+    return Tree(h.value)
+
+
+def merge(a: Summary, b: Summary, stream=None) -> Summary:
+    """pss_merge: combine(a, b, k) of Algorithm 2."""
+    h = vp()
+    _check(load().pss_merge(a.handle, b.handle, vp(_stream_handle(stream)), ctypes.byref(h)),
+           "pss_merge")
+    return Summary(h.value)
+
+
+def gen_zipf(count: int, *, seed: int, s: float, log2u: int, item_bytes: int = 4,
+             stream_id: int = 0, start: int = 0, out=None, device=None, stream=None):
+    """pss_gen_zipf into a new (or the given) CUDA tensor of int32/int64 bit patterns."""
+    import torch
+    if out is None:
+        dt = torch.int32 if item_bytes == 4 else torch.int64
+        out = torch.empty(count, dtype=dt, device=device or "cuda")
+    else:
+        item_bytes = _check_items(out)
+        if out.numel() < count:
+            raise ValueError("out is too small")
+    _check(load().pss_gen_zipf(vp(out.data_ptr()), int(count), int(item_bytes), int(seed),
+                               int(stream_id), int(start), float(s), int(log2u),
+                               vp(_stream_handle(stream))), "pss_gen_zipf")
+    return out
+
+
+def profile_enable(on: bool = True):
+    """Time the library's kernel groups with CUDA events from now on."""
+    _check(load().pss_profile_enable(1 if on else 0), "pss_profile_enable")
+
+
+def profile_read(reset: bool = False) -> dict:
+    """Launch count and accumulated device times (waits for recorded events)."""
+    p = Profile()
+    _check(load().pss_profile_read(ctypes.byref(p), 1 if reset else 0), "pss_profile_read")
+    return {name: getattr(p, name) for name, _ in Profile._fields_}

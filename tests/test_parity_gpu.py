@@ -1,0 +1,203 @@
+"""GPU path vs the CPU oracle, through the C ABI (bit-exact: integer work).
+
+Every block summary, every node of every tree level, the root and the query
+are compared entry by entry on the same seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from tests._helpers import canonical, check_bounds, exact_counts, summary_entries
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1606_04669_gb300 as P  # noqa: E402
+
+
+def to_dev(x: np.ndarray):
+    if x.dtype == np.uint32:
+        return torch.from_numpy(x.view(np.int32)).cuda()
+    return torch.from_numpy(x.view(np.int64)).cuda()
+
+
+def node_entries(node):
+    it, ct, er, m, cov = node
+    return list(zip(it.tolist(), ct.tolist(), er.tolist())), m, cov
+
+
+def compare_tree(x: np.ndarray, k: int, p: int):
+    tree = P.summarize_tree(to_dev(x), k, p)
+    ref = oracle.pss_tree(x, k, p)
+    assert tree.levels == len(ref)
+    for lv, ref_level in enumerate(ref):
+        got = tree.read_level(lv, k)
+        assert len(got) == len(ref_level)
+        for j, (g, r) in enumerate(zip(got, ref_level)):
+            ent, m, cov = node_entries(g)
+            items = [e[0] for e in ent]
+            assert items == sorted(items), f"level {lv} node {j}: device layout not item-sorted"
+            assert canonical(ent) == summary_entries(r), f"level {lv} node {j}"
+            assert (m, cov) == (r.m, r.n_covered), f"level {lv} node {j}"
+    root = tree.root()
+    e = root.export()
+    r = ref[-1][0]
+    assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == summary_entries(r)
+    assert (e.m, e.n_covered) == (r.m, r.n_covered)
+    n = len(x)
+    q = root.query(n, k)
+    rq = oracle.query(r, n, k)
+    assert list(zip(q.item.tolist(), q.count.tolist(), q.err.tolist())) == summary_entries(rq)
+    tree.close()
+    return root
+
+
+def test_generator_device_matches_host():
+    for (s, log2u, w, start) in ((1.1, 20, 4, 0), (1.0, 32, 4, 12345), (0.5, 32, 8, 7),
+                                 (3.0, 24, 4, 1 << 33), (1.8, 32, 8, 999)):
+        host = oracle.gen_zipf(100_000, seed=42, s=s, log2u=log2u, width=w, start=start)
+        dev = P.gen_zipf(100_000, seed=42, s=s, log2u=log2u, item_bytes=w, start=start)
+        got = dev.cpu().numpy().view(np.uint32 if w == 4 else np.uint64)
+        assert np.array_equal(got, host), (s, log2u, w)
+
+
+def test_config1_full_tree():
+    # n = 2^20 u32 Zipf(1.1) over [0, 2^20), seed 1, k = 100, p = 8
+    x = oracle.gen_zipf(1 << 20, seed=1, s=1.1, log2u=20)
+    compare_tree(x, 100, 8)
+
+
+@pytest.mark.parametrize("n,k,p,w,s,log2u,seed", [
+    (50_000, 64, 4, 4, 1.1, 16, 101),
+    (123_457, 200, 13, 4, 0.8, 20, 102),     # odd p: carried nodes
+    (200_000, 500, 5, 4, 1.5, 32, 103),
+    (300_000, 1000, 3, 4, 1.0, 32, 104),
+    (100_000, 2000, 8, 8, 1.2, 32, 105),     # u64 items
+    (80_000, 4096, 2, 4, 0.9, 24, 106),      # the largest k
+    (80_000, 4096, 3, 8, 1.3, 40, 107),
+    (60_000, 2, 9, 4, 1.1, 12, 108),          # k = 2
+    (70_000, 333, 31, 4, 0.5, 32, 109),       # nearly every item misses
+    (150_000, 1024, 1, 8, 2.0, 32, 110),      # p = 1: plain sequential Space Saving
+    (262_144, 2000, 1, 4, 1.1, 24, 2),        # one block of the 2^30 stream's shape
+])
+def test_random_configs(n, k, p, w, s, log2u, seed):
+    x = oracle.gen_zipf(n, seed=seed, s=s, log2u=log2u, width=w)
+    compare_tree(x, k, p)
+
+
+def test_edge_empty_and_tiny():
+    compare_tree(np.zeros(0, np.uint32), 5, 4)            # n = 0
+    compare_tree(np.array([7, 7, 9], np.uint32), 4, 8)     # n < p: empty blocks
+    compare_tree(np.array([3, 1, 2], np.uint32), 16, 1)    # n < k
+    compare_tree(np.array([1, 2, 3, 1], np.uint32), 2, 1)  # the golden example
+    compare_tree(np.array([1, 2, 2, 1, 3], np.uint32), 2, 1)
+
+
+def test_edge_all_same_and_all_distinct():
+    compare_tree(np.full(100_000, 0xFFFFFFFF, np.uint32), 10, 7)   # sentinel-valued item
+    compare_tree(np.arange(100_000, dtype=np.uint32) * np.uint32(2654435761), 100, 4)
+    compare_tree(np.full(5000, np.uint64(2 ** 64 - 1)), 3, 2)
+
+
+def test_edge_hash_collisions():
+    # Items that are multiples of large powers of two collide in naive hashes.
+    rng = np.random.default_rng(5)
+    base = (np.arange(3000, dtype=np.uint64) << np.uint64(20)).astype(np.uint32)
+    x = base[rng.zipf(1.3, size=200_000) % 3000]
+    compare_tree(x, 512, 4)
+    x64 = (np.arange(5000, dtype=np.uint64) << np.uint64(40))[rng.zipf(1.2, 100_000) % 5000]
+    compare_tree(x64, 256, 3)
+
+
+def test_interleaved_hits_misses_windows():
+    # Periodic streams hit the window-prefix logic (conflicts between hits and
+    # evictions in one window, bucket exhaustion mid-window).
+    pat = np.concatenate([np.arange(40, dtype=np.uint32), np.arange(20, dtype=np.uint32)])
+    x = np.tile(pat, 3000)
+    compare_tree(x, 30, 3)
+    y = np.tile(np.arange(300, dtype=np.uint32), 800)
+    compare_tree(y, 256, 2)
+    z = np.repeat(np.arange(1000, dtype=np.uint32), 3)[np.random.default_rng(3).permutation(3000)]
+    compare_tree(np.tile(z, 50), 100, 5)
+
+
+def test_merge_api():
+    xa = oracle.gen_zipf(200_000, seed=7, s=1.1, log2u=20)
+    xb = oracle.gen_zipf(150_000, seed=8, s=1.3, log2u=20)
+    for k in (2, 100, 1000):
+        a = P.summarize(to_dev(xa), k, 4)
+        b = P.summarize(to_dev(xb), k, 3)
+        ra, _ = oracle.parallel_space_saving(xa, k, 4)
+        rb, _ = oracle.parallel_space_saving(xb, k, 3)
+        for (u, v, ru, rv) in ((a, b, ra, rb), (b, a, rb, ra)):
+            c = P.merge(u, v)
+            e = c.export()
+            rc = oracle.combine(ru, rv, k)
+            assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == \
+                summary_entries(rc)
+            assert (e.m, e.n_covered) == (rc.m, rc.n_covered)
+    a = P.summarize(to_dev(xa), 10, 2)
+    b = P.summarize(to_dev(xb), 11, 2)
+    with pytest.raises(P.PssError) as ei:
+        P.merge(a, b)
+    assert ei.value.code == P.PSS_EMISMATCH
+
+
+def test_argument_errors():
+    x = to_dev(np.arange(100, dtype=np.uint32))
+    for k, p in ((1, 4), (P.PSS_MAX_K + 1, 4), (10, 0)):
+        with pytest.raises(P.PssError) as ei:
+            P.summarize(x, k, p)
+        assert ei.value.code == P.PSS_EINVAL
+    s = P.summarize(x, 8, 2)
+    lib = P.load()
+    import ctypes
+    buf = (P.pss.Entry * 1)()
+    n = ctypes.c_uint32()
+    rc = lib.pss_export(s.handle, buf, 1, ctypes.byref(n), None, None,
+                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == P.PSS_ERANGE
+
+
+def test_config2_sampled_blocks_and_full_size_properties():
+    # n = 2^30 u32 Zipf(1.1) over [0, 2^24), seed 2, k = 2000, p = 4096.
+    n, k, p = 1 << 30, 2000, 4096
+    x = P.gen_zipf(n, seed=2, s=1.1, log2u=24)
+    tree = P.summarize_tree(x, k, p)
+    level0 = tree.read_level(0, k)
+    for r in (0, 1, 777, 2048, 4094, 4095):
+        lo, hi = oracle.block_bounds(n, p, r)
+        xr = oracle.gen_zipf(hi - lo, seed=2, s=1.1, log2u=24, start=lo)
+        ref = oracle.space_saving(xr, k)
+        ent, m, cov = node_entries(level0[r])
+        assert canonical(ent) == summary_entries(ref), r
+        assert (m, cov) == (ref.m, hi - lo)
+    # Root against exact frequencies of the whole stream (torch histogram).
+    root = tree.root()
+    e = root.export()
+    f = torch.bincount(x.view(torch.int32).to(torch.int64), minlength=1 << 24).cpu().numpy()
+    assert e.n_covered == n and e.size == k
+    assert np.all(e.count - e.err <= f[e.item.astype(np.int64)])
+    assert np.all(f[e.item.astype(np.int64)] <= e.count)
+    mask = np.ones(1 << 24, bool)
+    mask[e.item.astype(np.int64)] = False
+    assert f[mask].max() <= e.m
+    q = root.query(n, k)
+    truly = set(np.nonzero(f * k > n)[0].tolist())
+    assert truly <= set(q.item.tolist())  # 100% recall
+    tree.close()
+
+
+def test_host_input_path():
+    # pss_summarize_host: slab copies from pinned host memory overlapping the kernels.
+    for (n, k, p, w) in ((500_000, 300, 37, 4), (300_000, 1000, 16, 8), (1000, 50, 40, 4)):
+        x = oracle.gen_zipf(n, seed=21 + k, s=1.1, log2u=20, width=w)
+        h = torch.from_numpy(x.view(np.int32 if w == 4 else np.int64)).pin_memory()
+        e = P.summarize_host(h, k, p).export()
+        r, q = oracle.parallel_space_saving(x, k, p)
+        assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == summary_entries(r)
+        assert (e.m, e.n_covered) == (r.m, r.n_covered)
