@@ -39,6 +39,11 @@ WORKLOADS = {
         desc="plain single stream: n=2^30 uint32 Zipf(s=1.1) over [0,2^24), seed 2; k=2000; "
              "p=4096 equal blocks; binary merge tree; query n/k",
         n=1 << 30, w=4, s=1.1, log2u=24, seed=2, k=2000, p=4096),
+    "wave": dict(
+        desc="one wave of the plain workload's blocks: n=304*262144 uint32 Zipf(s=1.1) over "
+             "[0,2^24), seed 2; k=2000; p=304 blocks of 262144 items (the block shape of the "
+             "2^30 stream); binary merge tree; query n/k",
+        n=304 * 262144, w=4, s=1.1, log2u=24, seed=2, k=2000, p=304),
     "small": dict(
         desc="plain single stream: n=2^20 uint32 Zipf(s=1.1) over [0,2^20), seed 1; k=100; p=8; "
              "binary merge tree; query n/k",

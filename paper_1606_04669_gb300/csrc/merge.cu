@@ -281,6 +281,9 @@ cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream
   const size_t smem = merge_smem_bytes<ItemT>(in.k);
   auto kern = merge_level_kernel<ItemT, MERGE_BS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out);
   return cudaGetLastError();
@@ -292,6 +295,9 @@ cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, u
   const size_t smem = merge_smem_bytes<ItemT>(out.k);
   auto kern = merge_pair_kernel<ItemT, MERGE_BS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out);
   return cudaGetLastError();

@@ -2,30 +2,34 @@
 // SpaceSaving call on the block bounds of Algorithm 1), one CTA per block.
 //
 // The sequential rule, with k counters (item, count, err, touch):
-//   x monitored            -> count += 1, touch = t
-//   a counter is free      -> (x, 1, 0, t)
-//   else, victim v = argmin (count, touch) -> err = count, count += 1,
-//                                              item = x, touch = t
-// is reproduced exactly while the CTA consumes a window of BS items at once:
+//   x monitored          -> count += 1, touch = t
+//   a counter is free    -> (x, 1, 0, t)
+//   else victim v = argmin (count, touch) -> err = count, count += 1,
+//                                            item = x, touch = t
+// is reproduced exactly while the CTA consumes a window of W = BS * IPT items
+// per step.  Definitions for one window, all relative to its start state:
 //
-//   1. every thread looks its item up in a shared-memory open-addressing
-//      table (item -> counter slot); hits commute with one another, so a
-//      window of hits only is applied with atomics;
-//   2. missing items are de-duplicated inside the window (first occurrence by
-//      position), ranked by position, and the r-th one is given the r-th
-//      oldest counter of the minimum-count bucket.  That bucket is kept as a
-//      list sorted by touch (the FIFO of the counters that reached the
-//      minimum count, oldest first); entries invalidated by a later hit are
-//      skipped lazily (their count is no longer the minimum);
-//   3. the assignment is exact for the window prefix in which no hit lands on
-//      a counter that a miss of that prefix evicts, the bucket does not run
-//      out and the table does not fill up; the window is cut at the first
-//      position where one of these fails, the prefix is applied, and the next
-//      window starts there;
-//   4. when the bucket runs out, the next one is built from (a) the counters
-//      already at that count before the current epoch, sorted by touch, and
-//      (b) the log of counters that reached it during the epoch, which is
-//      already in time order.
+//   * bucket list: the counters of minimum count m ordered by touch (oldest
+//     first).  Evictions take them in that order; a counter leaves the bucket
+//     when it is hit.  The list is rebuilt when the bucket runs out (an
+//     "epoch" ends): from the older members, sorted by touch, followed by the
+//     log of counters that reached count m + 1 during the epoch, which is in
+//     time order by construction.
+//   * events: the first occurrence of each item missing from the table
+//     ("misses"), plus "conversions": the first occurrence of a bucket
+//     member's item after that member was evicted in this window.
+//   * event e (in time order) evicts the (e + s)-th bucket member, s being the
+//     number of members before it that were "skipped" (hit before their turn).
+//     Only members hit inside the window can be skipped or converted; one warp
+//     walks just those, in list order, deciding each with the time of the
+//     event that reaches it.  Every other assignment is arithmetic.
+//   * the window is cut only where the bucket runs out (or a fill or a
+//     per-window capacity ends): everything before the cut is exact, the rest
+//     is processed again from the new state.
+//
+// Table: item -> counter slot in buckets of four 32-bit cells (16-bit tag,
+// slot + 1) read with one 128-bit shared load; deletions clear the cell (no
+// tombstones); each home bucket records how far its items were displaced.
 //
 // Output: the block's summary sorted by item ascending, with size, minimum m
 // (the minimum count if k counters are in use, else 0) and the block length.
@@ -36,8 +40,9 @@ namespace pss {
 
 namespace {
 
-constexpr uint16_t CELL_EMPTY = 0;
-constexpr uint16_t CELL_TOMB = 0xFFFF;
+constexpr uint32_t NONE32 = 0xFFFFFFFFu;
+constexpr int HMAX = 256;     // skipped members tracked per window
+constexpr int CONVMAX = 32;   // conversions tracked per window (one per lane)
 
 template <typename ItemT>
 struct ItemOps;
@@ -67,83 +72,118 @@ struct SSState {
   uint32_t head;         // next unread index of the bucket list
   uint32_t list_len;
   uint32_t log_len;      // entries of the next-bucket log
-  uint32_t log_over;     // log overflowed: next rebuild scans everything
   uint32_t used;         // counters in use
   uint32_t full;         // used == k
-  uint32_t tombs;        // tombstones in the hash table
-  uint32_t tomb_reuse;   // tombstones re-used by this window's inserts
   uint32_t epoch_start;  // position at which the current bucket list was built
-  uint32_t P;            // exact prefix of the current window
-  uint32_t found, j0;    // victim gathering cursor
-  uint32_t need_rebuild; // 0 none, 1 incremental, 2 full scan
+  uint32_t nvalid, nhit, j0;  // candidate compaction
+  uint32_t nskip, nconv, astop;
+  uint32_t cut;          // exact prefix of the window
+  uint32_t amax;         // 1 + largest candidate index applied (0: none)
+  uint32_t exhausted;
+  uint32_t napplied;     // events applied in a filling window
+  uint32_t need;         // 0 none, 1 incremental list rebuild, 2 full
+  uint32_t maxdisp;      // largest bucket displacement since the last table rebuild
   uint32_t stall;
   uint32_t status;
-  uint32_t red;          // reduction scratch
 };
 
-template <typename ItemT, int BS>
+template <typename ItemT>
 struct SSSmem {
-  uint32_t C, cshift, WT, wshift, LOGCAP, SORTN;
-  u64* skey;
+  uint32_t NB, nbshift, WT, wshift, CMAX, SORTN;
+  // persistent state
   ItemT* item;
   uint32_t* cnt;
   uint32_t* err;
   uint32_t* touch;
-  ItemT* wkey;
-  uint32_t* wpos;
-  uint32_t* rankpos;
-  uint32_t* Vidx;
-  uint32_t* wsum;   // 2 * (BS/32 + 1)
-  uint16_t* cellof;
-  uint16_t* hash;
+  uint32_t* cell;     // NB * 4 cells: (tag << 16) | (slot + 1), 0 = empty
+  uint32_t* dmax;     // per home bucket: largest displacement of its items
+  uint32_t* hfirst;   // per slot: first hit position in the window (members only)
+  uint16_t* cellof;   // per slot: its cell
   uint16_t* list;
   uint16_t* logq;
-  uint16_t* vrank;
-  uint16_t* spay;
+  uint16_t* fate;     // per evicted member with a conversion: its new slot + 1
+  // window scratch (aliased by the rebuild sort)
+  ItemT* wkey;
+  uint32_t* wpos;
   uint16_t* wslot;
-  uint16_t* V;
+  uint16_t* rankpos;
+  uint16_t* logpos;
+  uint16_t* cand;
+  uint16_t* candidx;
+  uint16_t* hitc;
+  uint16_t* skipl;
+  uint16_t* convt;
+  uint16_t* convlo;
+  uint16_t* convsrc;
+  uint32_t* wsum;
+  uint32_t* rkey;     // rebuild sort (over the window scratch)
+  uint16_t* rpay;
+  u64* fkey;          // final sort (over everything after touch)
+  uint16_t* fpay;
 };
 
-__host__ __device__ inline uint32_t ilog2(uint32_t x) {
+__host__ __device__ inline uint32_t ilog2c(uint32_t x) {
   uint32_t r = 0;
   while ((1u << r) < x) ++r;
   return r;
 }
 
-template <typename ItemT, int BS>
-__host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSmem<ItemT, BS>* s) {
-  SSSmem<ItemT, BS> L;
-  L.C = next_pow2(2 * k < 64 ? 64 : 2 * k);
-  L.cshift = 32 - ilog2(L.C);
-  L.WT = 2 * BS;
-  L.wshift = 32 - ilog2(L.WT);
-  L.LOGCAP = 2 * k;
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename ItemT, int BS, int IPT>
+__host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSmem<ItemT>* out) {
+  constexpr uint32_t W = BS * IPT;
+  SSSmem<ItemT> L;
+  const uint32_t nbk = (k + 1) / 2;
+  L.NB = next_pow2(nbk < 16 ? 16 : nbk);
+  L.nbshift = 32 - ilog2c(L.NB);
+  L.WT = 2 * W;
+  L.wshift = 32 - ilog2c(L.WT);
+  L.CMAX = W + 2 * BS;
   L.SORTN = next_pow2(k);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
-    off = (off + bytes + 15) & ~(size_t)15;
+    off = align16(off + bytes);
     return base + o;
   };
-  L.skey = (u64*)take(8ull * L.SORTN);
   L.item = (ItemT*)take(sizeof(ItemT) * k);
   L.cnt = (uint32_t*)take(4ull * k);
   L.err = (uint32_t*)take(4ull * k);
   L.touch = (uint32_t*)take(4ull * k);
+  const size_t after_touch = off;
+  L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
+  L.cell = (uint32_t*)take(16ull * L.NB);
+  L.dmax = (uint32_t*)take(4ull * L.NB);
+  L.hfirst = (uint32_t*)take(4ull * k);
+  L.cellof = (uint16_t*)take(2ull * k);
+  L.list = (uint16_t*)take(2ull * k);
+  L.logq = (uint16_t*)take(2ull * k);
+  L.fate = (uint16_t*)take(2ull * k);
+  const size_t u0 = off;
   L.wkey = (ItemT*)take(sizeof(ItemT) * (L.WT + 1));
   L.wpos = (uint32_t*)take(4ull * (L.WT + 1));
-  L.rankpos = (uint32_t*)take(4ull * BS);
-  L.Vidx = (uint32_t*)take(4ull * BS);
-  L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
-  L.cellof = (uint16_t*)take(2ull * k);
-  L.hash = (uint16_t*)take(2ull * L.C);
-  L.list = (uint16_t*)take(2ull * k);
-  L.logq = (uint16_t*)take(2ull * L.LOGCAP);
-  L.vrank = (uint16_t*)take(2ull * k);
-  L.spay = (uint16_t*)take(2ull * L.SORTN);
   L.wslot = (uint16_t*)take(2ull * (L.WT + 1));
-  L.V = (uint16_t*)take(2ull * BS);
-  if (s) *s = L;
+  L.rankpos = (uint16_t*)take(2ull * W);
+  L.logpos = (uint16_t*)take(2ull * W);
+  L.cand = (uint16_t*)take(2ull * L.CMAX);
+  L.candidx = (uint16_t*)take(2ull * L.CMAX);
+  L.hitc = (uint16_t*)take(2ull * L.CMAX);
+  L.skipl = (uint16_t*)take(2ull * HMAX);
+  L.convt = (uint16_t*)take(2ull * CONVMAX);
+  L.convlo = (uint16_t*)take(2ull * CONVMAX);
+  L.convsrc = (uint16_t*)take(2ull * CONVMAX);
+  // The rebuild sort reuses the window scratch.
+  L.rkey = (uint32_t*)(base + u0);
+  L.rpay = (uint16_t*)(base + u0 + align16(4ull * L.SORTN));
+  const size_t sort_end = u0 + align16(4ull * L.SORTN) + align16(2ull * L.SORTN);
+  if (sort_end > off) off = sort_end;
+  // The final sort reuses everything after touch (the state is dead by then).
+  L.fkey = (u64*)(base + after_touch);
+  L.fpay = (uint16_t*)(base + after_touch + 8ull * L.SORTN);
+  const size_t final_end = align16(after_touch + 8ull * L.SORTN + 2ull * L.SORTN);
+  if (final_end > off) off = final_end;
+  if (out) *out = L;
   return off;
 }
 
@@ -160,128 +200,170 @@ __device__ __forceinline__ uint32_t block_min_u32(uint32_t v, uint32_t* scratch)
   return r;
 }
 
-template <typename ItemT, int BS>
+// Number of entries of the sorted arr[0..n) smaller than x (n <= 1024), by
+// one warp: a search over 32 segments, then inside the segment found.
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint16_t* arr, uint32_t n, uint32_t x) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t seg = (n + 31) / 32;
+  bool p = false;
+  if (seg && lane * seg < n) p = arr[min((lane + 1) * seg, n) - 1] < x;
+  const uint32_t nfull = __popc(__ballot_sync(0xffffffffu, p));
+  const uint32_t base = min(nfull * seg, n);  // the last segment may be partial
+  const uint32_t j = base + lane;
+  const bool q = lane < seg && j < n && arr[j] < x;
+  return base + __popc(__ballot_sync(0xffffffffu, q));
+}
+
+template <typename ItemT, int BS, int IPT>
 struct SSBlock {
-  SSSmem<ItemT, BS> s;
+  SSSmem<ItemT> s;
   SSState* S;
   uint32_t k;
-  uint32_t sb;  // scan scratch parity
+  uint32_t par;  // scan scratch parity
 
   __device__ __forceinline__ uint32_t scan(uint32_t v, uint32_t* total) {
-    uint32_t* buf = s.wsum + (sb ? (BS / 32 + 1) : 0);
-    sb ^= 1;
+    uint32_t* buf = s.wsum + (par ? (BS / 32 + 1) : 0);
+    par ^= 1;
     return block_exclusive_scan<BS>(v, buf, total);
   }
 
-  __device__ __forceinline__ int lookup(ItemT x, uint32_t& status) const {
-    uint32_t c = ItemOps<ItemT>::h1(x) >> s.cshift;
-    const uint32_t mask = s.C - 1;
-    for (uint32_t i = 0; i < s.C; ++i) {
-      uint16_t v = s.hash[c];
-      if (v == CELL_EMPTY) return -1;
-      if (v != CELL_TOMB && s.item[v - 1] == x) return (int)v - 1;
-      c = (c + 1) & mask;
+  __device__ __forceinline__ int lookup(ItemT x) const {
+    const uint32_t h = ItemOps<ItemT>::h1(x);
+    const uint32_t b = h >> s.nbshift, tag = h & 0xFFFFu, mask = s.NB - 1;
+    const uint32_t d = s.dmax[b];
+    for (uint32_t dd = 0; dd <= d; ++dd) {
+      const uint4 c = *(const uint4*)&s.cell[((b + dd) & mask) * 4];
+      const uint32_t cs[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (cs[i] && (cs[i] >> 16) == tag) {
+          const uint32_t q = (cs[i] & 0xFFFFu) - 1;
+          if (s.item[q] == x) return (int)q;
+        }
+      }
     }
-    status |= ST_PROBE;
     return -1;
   }
 
-  // Claim the first empty or tombstone cell of x's probe sequence for slot.
   __device__ __forceinline__ void insert(ItemT x, uint32_t slot, uint32_t& status) {
-    uint32_t c = ItemOps<ItemT>::h1(x) >> s.cshift;
-    const uint32_t mask = s.C - 1;
-    for (uint32_t i = 0; i < 4 * s.C; ++i) {
-      uint16_t v = s.hash[c];
-      if (v == CELL_EMPTY || v == CELL_TOMB) {
-        uint16_t old = atomicCAS(&s.hash[c], v, (uint16_t)(slot + 1));
-        if (old == v) {
-          if (v == CELL_TOMB) atomicAdd(&S->tomb_reuse, 1u);
-          s.cellof[slot] = (uint16_t)c;
+    const uint32_t h = ItemOps<ItemT>::h1(x);
+    const uint32_t b = h >> s.nbshift, mask = s.NB - 1;
+    const uint32_t val = ((h & 0xFFFFu) << 16) | (slot + 1);
+    for (uint32_t dd = 0; dd < s.NB; ++dd) {
+      const uint32_t bb = (b + dd) & mask;
+      for (int i = 0; i < 4; ++i) {
+        uint32_t* c = &s.cell[bb * 4 + i];
+        if (*c == 0u && atomicCAS(c, 0u, val) == 0u) {
+          s.cellof[slot] = (uint16_t)(bb * 4 + i);
+          if (dd) {
+            atomicMax(&s.dmax[b], dd);
+            atomicMax(&S->maxdisp, dd);
+          }
           return;
         }
-        continue;  // lost the race for this cell: look at it again
       }
-      c = (c + 1) & mask;
     }
     status |= ST_PROBE;
   }
 
-  // Window de-duplication table: returns the cell of x, and keeps in wpos
-  // the smallest position at which x missed.
-  __device__ __forceinline__ uint32_t wtab_insert(ItemT x, uint32_t t) {
+  __device__ __forceinline__ uint32_t wtab_insert(ItemT x, uint32_t rel) {
     uint32_t c;
     if (x == ItemOps<ItemT>::SENT) {
       c = s.WT;
     } else {
       c = ItemOps<ItemT>::h2(x) >> s.wshift;
       for (uint32_t i = 0; i < s.WT; ++i) {
-        ItemT prev = atomicCAS(&s.wkey[c], ItemOps<ItemT>::SENT, x);
+        const ItemT prev = atomicCAS(&s.wkey[c], ItemOps<ItemT>::SENT, x);
         if (prev == ItemOps<ItemT>::SENT || prev == x) break;
         c = (c + 1) & (s.WT - 1);
       }
     }
-    atomicMin(&s.wpos[c], t);
+    atomicMin(&s.wpos[c], rel);
     return c;
   }
 
-  __device__ void rebuild_hash(uint32_t& status) {
-    for (uint32_t c = threadIdx.x; c < s.C; c += BS) s.hash[c] = CELL_EMPTY;
+  // Window scratch that must start clear (the rebuild sort writes over it).
+  __device__ void reset_window_scratch() {
+    constexpr uint32_t W = BS * IPT;
+    for (uint32_t i = threadIdx.x; i <= s.WT; i += BS) {
+      s.wkey[i] = ItemOps<ItemT>::SENT;
+      s.wpos[i] = NONE32;
+    }
+    for (uint32_t i = threadIdx.x; i < W; i += BS) s.logpos[i] = 0;
+  }
+
+  __device__ void rebuild_table(uint32_t& status) {
+    for (uint32_t c = threadIdx.x; c < 4 * s.NB; c += BS) s.cell[c] = 0;
+    for (uint32_t b = threadIdx.x; b < s.NB; b += BS) s.dmax[b] = 0;
     __syncthreads();
     const uint32_t used = S->used;
     for (uint32_t i = threadIdx.x; i < used; i += BS) insert(s.item[i], i, status);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      S->tombs = 0;
-      S->tomb_reuse = 0;
-    }
+    if (threadIdx.x == 0) S->maxdisp = 0;
     __syncthreads();
   }
 
-  // Build the list of the minimum-count bucket in touch order.  now = the
-  // position of the next item to process.
+  // Build the bucket list of the minimum count, oldest touch first.  `now` is
+  // the position of the next item to process.
   __device__ void rebuild_list(bool full_scan, uint32_t now) {
     uint32_t mn = 0xFFFFFFFFu;
     for (uint32_t i = threadIdx.x; i < k; i += BS) mn = min(mn, s.cnt[i]);
     mn = block_min_u32<BS>(mn, s.wsum);
-    const bool incremental = !full_scan && !S->log_over && mn == S->m + 1;
+    const bool incremental = !full_scan && mn == S->m + 1;
     const uint32_t epoch = S->epoch_start;
-    // (a) counters at count mn to sort by touch
+    // (a) members to sort by touch: all of them, or those older than the epoch
     uint32_t n1 = 0;
     for (uint32_t base = 0; base < k; base += BS) {
       const uint32_t i = base + threadIdx.x;
       bool f = false;
       if (i < k) f = s.cnt[i] == mn && (!incremental || s.touch[i] < epoch);
       uint32_t tot;
-      uint32_t ex = scan(f ? 1u : 0u, &tot);
+      const uint32_t ex = scan(f ? 1u : 0u, &tot);
       if (f) {
-        s.skey[n1 + ex] = s.touch[i];
-        s.spay[n1 + ex] = (uint16_t)i;
+        s.rkey[n1 + ex] = s.touch[i];
+        s.rpay[n1 + ex] = (uint16_t)i;
       }
       n1 += tot;
     }
     const uint32_t n2p = next_pow2(n1 ? n1 : 1);
     for (uint32_t i = n1 + threadIdx.x; i < n2p; i += BS) {
-      s.skey[i] = ~0ull;
-      s.spay[i] = 0xFFFF;
+      s.rkey[i] = 0xFFFFFFFFu;
+      s.rpay[i] = 0xFFFF;
     }
     __syncthreads();
-    block_bitonic_sort<BS, uint16_t>(s.skey, s.spay, n2p);
-    for (uint32_t i = threadIdx.x; i < n1; i += BS) s.list[i] = s.spay[i];
-    // (b) the log of counters that reached count mn during the epoch
+    // ascending by (touch, slot); touches of distinct counters differ
+    for (uint32_t size = 2; size <= n2p; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t i = threadIdx.x; i < (n2p >> 1); i += BS) {
+          const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+          const bool asc = (lo & size) == 0;
+          const uint32_t a = s.rkey[lo], b = s.rkey[hi];
+          const uint16_t pa = s.rpay[lo], pb = s.rpay[hi];
+          const bool greater = (a > b) || (a == b && pa > pb);
+          if (greater == asc) {
+            s.rkey[lo] = b; s.rkey[hi] = a;
+            s.rpay[lo] = pb; s.rpay[hi] = pa;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t i = threadIdx.x; i < n1; i += BS) s.list[i] = s.rpay[i];
+    // (b) the log: members that reached count mn during the epoch, in time order
     uint32_t n = n1;
     if (incremental) {
       const uint32_t ll = S->log_len;
       for (uint32_t base = 0; base < ll; base += BS) {
         const uint32_t j = base + threadIdx.x;
         bool f = false;
-        uint16_t sl = 0;
+        uint16_t q = 0;
         if (j < ll) {
-          sl = s.logq[j];
-          f = s.cnt[sl] == mn;
+          q = s.logq[j];
+          f = s.cnt[q] == mn;
         }
         uint32_t tot;
-        uint32_t ex = scan(f ? 1u : 0u, &tot);
-        if (f && n + ex < k) s.list[n + ex] = sl;
+        const uint32_t ex = scan(f ? 1u : 0u, &tot);
+        if (f && n + ex < k) s.list[n + ex] = q;
         n += tot;
       }
     }
@@ -291,27 +373,28 @@ struct SSBlock {
       S->head = 0;
       S->list_len = n < k ? n : k;
       S->log_len = 0;
-      S->log_over = 0;
       S->epoch_start = now;
     }
     __syncthreads();
   }
 };
 
-template <typename ItemT, int BS>
+template <typename ItemT, int BS, int IPT>
 __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ items, u64 n,
                                                       uint32_t p, uint32_t r0,
                                                       SetView<ItemT> out, uint32_t node0) {
+  constexpr uint32_t W = BS * IPT;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SSState S_;
-  SSBlock<ItemT, BS> B;
+  SSBlock<ItemT, BS, IPT> B;
   B.k = out.k;
   B.S = &S_;
-  B.sb = 0;
-  ss_carve<ItemT, BS>(B.k, smem, &B.s);
+  B.par = 0;
+  ss_carve<ItemT, BS, IPT>(B.k, smem, &B.s);
   SSState& S = S_;
+  auto& s = B.s;
   const uint32_t k = B.k;
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t r = r0 + blockIdx.x;
   const uint32_t node = node0 + blockIdx.x;
   const u64 left = block_bound(r, n, p), right = block_bound((u64)r + 1, n, p);
@@ -327,178 +410,378 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
   }
   const uint32_t len = (uint32_t)(right - left);
   const ItemT* __restrict__ xs = items + left;
-  auto& s = B.s;
   uint32_t status = 0;
 
-  for (uint32_t i = tid; i < s.C; i += BS) s.hash[i] = CELL_EMPTY;
-  for (uint32_t i = tid; i <= s.WT; i += BS) {
-    s.wkey[i] = ItemOps<ItemT>::SENT;
-    s.wpos[i] = 0xFFFFFFFFu;
+  for (uint32_t i = tid; i < 4 * s.NB; i += BS) s.cell[i] = 0;
+  for (uint32_t i = tid; i < s.NB; i += BS) s.dmax[i] = 0;
+  for (uint32_t i = tid; i < k; i += BS) {
+    s.hfirst[i] = NONE32;
+    s.fate[i] = 0;
   }
-  for (uint32_t i = tid; i < k; i += BS) s.vrank[i] = 0;
+  B.reset_window_scratch();
   if (tid == 0) {
-    S.m = 0; S.head = 0; S.list_len = 0; S.log_len = 0; S.log_over = 0;
-    S.used = 0; S.full = 0; S.tombs = 0; S.tomb_reuse = 0; S.epoch_start = 0;
-    S.P = 0; S.found = 0; S.j0 = 0; S.need_rebuild = 0; S.stall = 0; S.status = 0;
+    S.m = 0; S.head = 0; S.list_len = 0; S.log_len = 0; S.used = 0; S.full = 0;
+    S.epoch_start = 0; S.maxdisp = 0; S.stall = 0; S.status = 0; S.need = 0;
   }
   __syncthreads();
 
-  const uint32_t hash_limit = s.C / 4 * 3;
+  ItemT nx[IPT];
+  bool have_next = false;
   uint32_t t0 = 0;
   while (t0 < len) {
-    const uint32_t nw = min((uint32_t)BS, len - t0);
-    const uint32_t t = t0 + tid;
-    const bool act = tid < nw;
-    const ItemT x = act ? xs[t] : (ItemT)0;
-    const int slot = act ? B.lookup(x, status) : -1;
-    const uint32_t full = S.full, m = S.m;
-    const bool hit = slot >= 0;
-    const bool miss = act && !hit;
-    const uint32_t pre = hit ? s.cnt[slot] : 0u;
-    const bool lfhit = full && hit && pre == m;
-
-    if (!__syncthreads_or(miss || lfhit)) {
-      // Hits only: they commute.
-      if (hit) {
-        atomicAdd(&s.cnt[slot], 1u);
-        atomicMax(&s.touch[slot], t);
+    const uint32_t nact = min(W, len - t0);
+    ItemT x[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t rel = tid * IPT + j;
+      x[j] = have_next ? nx[j] : (rel < nact ? xs[t0 + rel] : (ItemT)0);
+    }
+    // Prefetch the next window on the assumption that this one is not cut.
+    have_next = t0 + W < len;
+    if (have_next) {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t t = t0 + W + tid * IPT + j;
+        nx[j] = t < len ? xs[t] : (ItemT)0;
       }
-      __syncthreads();
-      t0 += nw;
-      continue;
     }
+    const uint32_t full = S.full, m = S.m;
 
-    if (tid == 0) {
-      S.P = nw;
-      S.found = 0;
-      S.j0 = S.head;
+    // ---- P1: look up; first hit of bucket members; misses into the window table
+    int sl[IPT];
+    uint32_t wc[IPT];
+    uint32_t miss = 0, mhit = 0;  // bit j: item j missed / hit a bucket member
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t rel = tid * IPT + j;
+      sl[j] = -1;
+      wc[j] = 0;
+      if (rel < nact) {
+        sl[j] = B.lookup(x[j]);
+        if (sl[j] < 0) {
+          miss |= 1u << j;
+          wc[j] = B.wtab_insert(x[j], rel);
+        } else if (full && s.cnt[sl[j]] == m) {
+          mhit |= 1u << j;
+          atomicMin(&s.hfirst[sl[j]], rel);
+        }
+      }
     }
-    uint32_t wc = 0;
-    if (miss) wc = B.wtab_insert(x, t);
     __syncthreads();
-    const bool first = miss && s.wpos[wc] == t;
-    const bool lf = lfhit || (full && first);
-    uint32_t tot;
-    const uint32_t ex = B.scan((first ? 1u : 0u) | (lf ? 0x10000u : 0u), &tot);
-    const uint32_t rnk = ex & 0xFFFFu, lrk = ex >> 16, M = tot & 0xFFFFu;
-    if (first) s.rankpos[rnk] = t;
 
-    // Victims: the first M counters of the bucket list still at count m.
-    uint32_t Lv = 0;
+    // ---- P2: first occurrences of the misses, ranked by position
+    uint32_t first = 0, nf = 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j)
+      if ((miss >> j & 1) && s.wpos[wc[j]] == tid * IPT + j) {
+        first |= 1u << j;
+        ++nf;
+      }
+    uint32_t M;
+    const uint32_t rbase = B.scan(nf, &M);
+    uint32_t rank[IPT];
+    {
+      uint32_t rr = rbase;
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        rank[j] = rr;
+        if (first >> j & 1) s.rankpos[rr++] = (uint16_t)(tid * IPT + j);
+      }
+    }
+    if (tid == 0) {
+      S.cut = nact;
+      S.amax = 0;
+      S.exhausted = 0;
+      S.napplied = 0;
+      S.nvalid = 0;
+      S.nhit = 0;
+      S.j0 = S.head;
+      S.nskip = 0;
+      S.nconv = 0;
+      S.astop = NONE32;
+      S.need = 0;
+    }
+    __syncthreads();
+
+    // ---- P3: the bucket members still at count m, in list order
+    bool list_end = false;
     if (full && M > 0) {
       for (;;) {
-        const uint32_t found = S.found, j0 = S.j0, ll = S.list_len;
-        if (found >= M || j0 >= ll) break;
-        const uint32_t j = j0 + tid;
-        uint16_t sl = 0;
-        bool valid = false;
-        if (j < ll) {
-          sl = s.list[j];
-          valid = s.cnt[sl] == m;
+        const uint32_t nv = S.nvalid, nh = S.nhit, j0 = S.j0, ll = S.list_len;
+        if (nv >= M + 2 * nh + 1) break;
+        if (j0 >= ll) {
+          list_end = true;
+          break;
         }
-        uint32_t vt;
-        const uint32_t ve = B.scan(valid ? 1u : 0u, &vt);
-        if (valid && found + ve < M) {
-          s.V[found + ve] = sl;
-          s.Vidx[found + ve] = j;
+        if (nv + BS > s.CMAX) break;
+        const uint32_t j = j0 + tid;
+        bool valid = false, hit = false;
+        uint16_t q = 0;
+        if (j < ll) {
+          q = s.list[j];
+          valid = s.cnt[q] == m;
+          hit = valid && s.hfirst[q] != NONE32;
+        }
+        uint32_t tt;
+        const uint32_t ex = B.scan((valid ? 1u : 0u) | (hit ? 0x10000u : 0u), &tt);
+        if (valid) {
+          const uint32_t a = nv + (ex & 0xFFFFu);
+          s.cand[a] = q;
+          s.candidx[a] = (uint16_t)j;
+          if (hit) s.hitc[nh + (ex >> 16)] = (uint16_t)a;
         }
         if (tid == 0) {
-          S.found = found + vt;
+          S.nvalid = nv + (tt & 0xFFFFu);
+          S.nhit = nh + (tt >> 16);
           S.j0 = j0 + BS;
         }
         __syncthreads();
       }
-      Lv = min(S.found, M);
-      if (tid < Lv) s.vrank[s.V[tid]] = (uint16_t)(tid + 1);
     }
-    __syncthreads();
 
-    // Cut the window at the first position where the assignment stops being exact.
-    if (full && hit) {
-      const uint32_t vr = s.vrank[slot];
-      if (vr) atomicMin(&S.P, max(t, s.rankpos[vr - 1]) - t0);
-    }
-    if (tid == 0) {
-      if (!full) {
-        const uint32_t F = k - S.used;
-        if (M > F) atomicMin(&S.P, s.rankpos[F] - t0);
-      } else if (Lv < M) {
-        atomicMin(&S.P, s.rankpos[Lv] - t0);
+    // ---- P4: one warp walks the members hit in this window (skips, conversions)
+    if (full && M > 0 && warp == 0) {
+      const uint32_t nv = S.nvalid, nh = S.nhit;
+      uint32_t nskip = 0, nconv = 0, astop = nv;
+      uint32_t ct = NONE32, clo = 0, cs = 0;  // conversion held by this lane, sorted by time
+      for (uint32_t hi = 0; hi < nh; ++hi) {
+        const uint32_t a = s.hitc[hi];
+        const uint32_t hq = s.hfirst[s.cand[a]];
+        const uint32_t e = a - nskip;  // the event that reaches this member
+        const uint32_t mi = lane < nconv ? lane + clo : NONE32;
+        const unsigned bc = __ballot_sync(0xffffffffu, mi == e);
+        uint32_t tau;
+        if (bc) {
+          tau = __shfl_sync(0xffffffffu, ct, __ffs(bc) - 1);
+        } else {
+          const uint32_t nb = __popc(__ballot_sync(0xffffffffu, mi < e));
+          const uint32_t i = e - nb;
+          if (i >= M) break;  // no event reaches this member, nor any later one
+          tau = s.rankpos[i];
+        }
+        if (hq < tau) {  // hit before its turn: it leaves the bucket
+          if (nskip == HMAX) {
+            astop = a;
+            break;
+          }
+          if (lane == 0) s.skipl[nskip] = (uint16_t)a;
+          ++nskip;
+        } else {  // evicted at tau; its item comes back at hq
+          if (nconv == CONVMAX) {
+            astop = a;
+            break;
+          }
+          const uint32_t lo = warp_lower_bound(s.rankpos, M, hq);
+          const uint32_t pos = __popc(__ballot_sync(0xffffffffu, lane < nconv && ct < hq));
+          const uint32_t pct = __shfl_up_sync(0xffffffffu, ct, 1);
+          const uint32_t pclo = __shfl_up_sync(0xffffffffu, clo, 1);
+          const uint32_t pcs = __shfl_up_sync(0xffffffffu, cs, 1);
+          if (lane > pos && lane <= nconv) {
+            ct = pct;
+            clo = pclo;
+            cs = pcs;
+          }
+          if (lane == pos) {
+            ct = hq;
+            clo = lo;
+            cs = a;
+          }
+          ++nconv;
+        }
+      }
+      if (lane < nconv) {
+        s.convt[lane] = (uint16_t)ct;
+        s.convlo[lane] = (uint16_t)clo;
+        s.convsrc[lane] = (uint16_t)cs;
+      }
+      if (lane == 0) {
+        S.nskip = nskip;
+        S.nconv = nconv;
+        S.astop = astop;
       }
     }
     __syncthreads();
-    const uint32_t P = S.P, lim = t0 + P;
-    const bool applyF = first && t < lim;
-    const bool applyL = lf && t < lim;
-    const uint32_t MP = (uint32_t)__syncthreads_count(applyF);
 
-    // Evictions: remove the victims' items from the table.
-    if (applyF && full) s.hash[s.cellof[s.V[rnk]]] = CELL_TOMB;
-    __syncthreads();
-    if (applyF) {
-      const uint32_t v = full ? (uint32_t)s.V[rnk] : S.used + rnk;
-      B.insert(x, v, status);
-      s.item[v] = x;
-      s.cnt[v] = full ? m + 1 : 1u;
-      s.err[v] = full ? m : 0u;
-      s.touch[v] = t;
-      s.wslot[wc] = (uint16_t)v;
-    }
-    if (applyL) {
-      const uint32_t idx = S.log_len + lrk;
-      if (idx < s.LOGCAP) s.logq[idx] = first ? s.V[rnk] : (uint16_t)slot;
-    }
-    const uint32_t LGP = (uint32_t)__syncthreads_count(applyL);
-
-    if (t < lim) {
-      if (hit) {
-        atomicAdd(&s.cnt[slot], 1u);
-        atomicMax(&s.touch[slot], t);
-      } else if (miss && !first) {
-        const uint32_t v = s.wslot[wc];
-        atomicAdd(&s.cnt[v], 1u);
-        atomicMax(&s.touch[v], t);
+    // ---- P5: every event's victim (or the cut)
+    const uint32_t nconv = S.nconv, nskip = S.nskip;
+    const uint32_t limit = full ? min(S.nvalid, S.astop) : 0u;
+    const bool can_exhaust = full && list_end && S.astop >= S.nvalid;
+    const uint32_t nfree = full ? 0u : k - S.used;
+    const uint32_t used0 = S.used;
+    auto assign = [&](uint32_t e) {
+      uint32_t a = e;
+      for (uint32_t i = 0; i < nskip; ++i) {
+        if (s.skipl[i] <= a) ++a;
+        else break;
       }
-    }
-    if (full && tid < Lv) s.vrank[s.V[tid]] = 0;
-    if (tid == 0) {
+      return a;
+    };
+    uint32_t vict[IPT];
+    uint32_t va[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      vict[j] = 0;
+      va[j] = NONE32;
+      if (!(first >> j & 1)) continue;
+      const uint32_t rel = tid * IPT + j;
       if (!full) {
-        S.used += MP;
+        if (rank[j] < nfree) vict[j] = used0 + rank[j];
+        else atomicMin(&S.cut, rel);
+        continue;
+      }
+      uint32_t e = rank[j];
+      for (uint32_t c = 0; c < nconv; ++c) e += s.convlo[c] <= rank[j] ? 1u : 0u;
+      const uint32_t a = assign(e);
+      if (a < limit) {
+        vict[j] = s.cand[a];
+        va[j] = a;
       } else {
-        if (MP) S.head = s.Vidx[MP - 1] + 1;
-        S.tombs += MP;
+        atomicMin(&S.cut, rel);
+        if (can_exhaust) S.exhausted = 1;
       }
-      uint32_t nl = S.log_len + LGP;
-      if (nl > s.LOGCAP) {
-        S.log_over = 1;
-        nl = s.LOGCAP;
+    }
+    // conversion events: thread c handles conversion c
+    uint32_t cvict = 0, cva = NONE32, ctime = NONE32, csrc = 0;
+    ItemT citem = (ItemT)0;
+    if (tid < nconv) {
+      ctime = s.convt[tid];
+      csrc = s.cand[s.convsrc[tid]];
+      citem = s.item[csrc];
+      const uint32_t a = assign(tid + s.convlo[tid]);
+      if (a < limit) {
+        cvict = s.cand[a];
+        cva = a;
+      } else {
+        atomicMin(&S.cut, ctime);
+        if (can_exhaust) S.exhausted = 1;
       }
-      S.log_len = nl;
-      S.tombs -= S.tomb_reuse;
-      S.tomb_reuse = 0;
-      S.need_rebuild = 0;
-      if (!full && S.used == k) {
-        S.full = 1;
-        S.need_rebuild = 2;
-      } else if (full && Lv < M && MP == Lv) {
-        S.need_rebuild = 1;
-      }
-      S.stall = P ? 0 : S.stall + 1;
     }
     __syncthreads();
-    if (first) {
-      if (wc != s.WT) s.wkey[wc] = ItemOps<ItemT>::SENT;
-      s.wpos[wc] = 0xFFFFFFFFu;
+    const uint32_t cut = S.cut;
+
+    // ---- P6: evictions take the victims' items out of the table
+    if (full) {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j)
+        if ((first >> j & 1) && tid * IPT + j < cut) s.cell[s.cellof[vict[j]]] = 0u;
+      if (tid < nconv && ctime < cut) s.cell[s.cellof[cvict]] = 0u;
     }
-    const uint32_t nr = S.need_rebuild;
-    if (nr) B.rebuild_list(nr == 2, lim);
-    if (S.used + S.tombs > hash_limit) B.rebuild_hash(status);
+    __syncthreads();
+
+    // ---- P7: insertions; new counters start at m (their occurrences are added next)
+    uint32_t napp = 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t rel = tid * IPT + j;
+      if (!(first >> j & 1) || rel >= cut) continue;
+      const uint32_t v = vict[j];
+      B.insert(x[j], v, status);
+      s.item[v] = x[j];
+      s.cnt[v] = full ? m : 0u;
+      s.err[v] = full ? m : 0u;
+      s.touch[v] = 0;
+      s.wslot[wc[j]] = (uint16_t)v;
+      if (full) {
+        s.logpos[rel] = (uint16_t)(v + 1);
+        atomicMax(&S.amax, va[j] + 1u);
+      } else {
+        ++napp;
+      }
+    }
+    if (tid < nconv && ctime < cut) {
+      B.insert(citem, cvict, status);
+      s.item[cvict] = citem;
+      s.cnt[cvict] = m;
+      s.err[cvict] = m;
+      s.touch[cvict] = 0;
+      s.fate[csrc] = (uint16_t)(cvict + 1);
+      s.logpos[ctime] = (uint16_t)(cvict + 1);
+      atomicMax(&S.amax, cva + 1u);
+    }
+    if (!full && napp) atomicAdd(&S.napplied, napp);
+    __syncthreads();
+
+    // ---- P8: every occurrence before the cut adds one to its counter
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t rel = tid * IPT + j;
+      if (rel >= cut) continue;
+      uint32_t tgt;
+      if (miss >> j & 1) {
+        tgt = s.wslot[wc[j]];
+      } else {
+        tgt = (uint32_t)sl[j];
+        if (mhit >> j & 1) {
+          const uint32_t f = s.fate[tgt];
+          if (f) tgt = f - 1;  // the member was evicted: its item was re-inserted
+          else if (s.hfirst[tgt] == rel) s.logpos[rel] = (uint16_t)(tgt + 1);  // m -> m + 1
+        }
+      }
+      atomicAdd(&s.cnt[tgt], 1u);
+      atomicMax(&s.touch[tgt], t0 + rel);
+    }
+    __syncthreads();
+
+    // ---- P9: log in time order, reset the window scratch, advance
+    uint32_t nl = 0;
+    uint16_t lg[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t rel = tid * IPT + j;
+      lg[j] = s.logpos[rel];
+      if (lg[j] && rel < cut) ++nl;
+      s.logpos[rel] = 0;
+    }
+    uint32_t ltot;
+    const uint32_t lbase = B.scan(nl, &ltot);
+    {
+      uint32_t o = S.log_len + lbase;
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        if (lg[j] && tid * IPT + j < cut) {
+          if (o < k) s.logq[o] = (uint16_t)(lg[j] - 1);
+          ++o;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      if (mhit >> j & 1) s.hfirst[sl[j]] = NONE32;
+      if (first >> j & 1) {
+        if (wc[j] != s.WT) s.wkey[wc[j]] = ItemOps<ItemT>::SENT;
+        s.wpos[wc[j]] = NONE32;
+      }
+    }
+    if (tid < nconv) s.fate[csrc] = 0;
+    if (tid == 0) {
+      const uint32_t nlog = S.log_len + ltot;
+      S.log_len = nlog < k ? nlog : k;
+      if (full) {
+        if (S.amax) S.head = s.candidx[S.amax - 1u] + 1u;
+        if (S.exhausted && cut < nact) S.need = 1;
+      } else {
+        S.used += S.napplied;
+        if (S.used == k) {
+          S.full = 1;
+          S.need = 2;
+        }
+      }
+      S.stall = cut ? 0u : S.stall + 1u;
+    }
+    __syncthreads();
+    const uint32_t need = S.need;
+    if (need) {
+      B.rebuild_list(need == 2, t0 + cut);
+      if (S.maxdisp > 2) B.rebuild_table(status);
+      B.reset_window_scratch();
+    }
     if (S.stall >= 3) {
       status |= ST_NOPROGRESS;
       break;
     }
     __syncthreads();
-    t0 = lim;
+    if (cut < W) have_next = false;
+    t0 += cut;
   }
 
   // ---- output: the summary sorted by item ascending
@@ -507,24 +790,24 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
   const uint32_t used = S.used;
   uint32_t mn = 0xFFFFFFFFu;
   for (uint32_t i = tid; i < used; i += BS) mn = min(mn, s.cnt[i]);
-  mn = block_min_u32<BS>(mn, s.wsum);
+  mn = block_min_u32<BS>(mn, s.wsum);  // before the sort keys overwrite wsum
   const uint32_t n2p = next_pow2(used ? used : 1);
   for (uint32_t i = tid; i < n2p; i += BS) {
     if (i < used) {
-      s.skey[i] = ItemOps<ItemT>::sort_key(s.item[i], i);
-      s.spay[i] = (uint16_t)i;
+      s.fkey[i] = ItemOps<ItemT>::sort_key(s.item[i], i);
+      s.fpay[i] = (uint16_t)i;
     } else {
-      s.skey[i] = ~0ull;
-      s.spay[i] = 0xFFFF;
+      s.fkey[i] = ~0ull;
+      s.fpay[i] = 0xFFFF;
     }
   }
   __syncthreads();
-  block_bitonic_sort<BS, uint16_t>(s.skey, s.spay, n2p);
+  block_bitonic_sort<BS, uint16_t>(s.fkey, s.fpay, n2p);
   for (uint32_t i = tid; i < used; i += BS) {
-    const uint32_t sl = s.spay[i];
-    out.item[obase + i] = s.item[sl];
-    out.count[obase + i] = s.cnt[sl];
-    out.err[obase + i] = s.err[sl];
+    const uint32_t q = s.fpay[i];
+    out.item[obase + i] = s.item[q];
+    out.count[obase + i] = s.cnt[q];
+    out.err[obase + i] = s.err[q];
   }
   if (tid == 0) {
     out.size[node] = used;
@@ -538,7 +821,7 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
 
 template <typename ItemT>
 size_t ss_smem_bytes(uint32_t k) {
-  return ss_carve<ItemT, SS_BS>(k, nullptr, nullptr);
+  return ss_carve<ItemT, SS_BS, SS_IPT>(k, nullptr, nullptr);
 }
 
 template <typename ItemT>
@@ -546,8 +829,11 @@ cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint3
                                     uint32_t count, SetView<ItemT> out, uint32_t node0,
                                     cudaStream_t stream) {
   const size_t smem = ss_smem_bytes<ItemT>(out.k);
-  auto kern = ss_block_kernel<ItemT, SS_BS>;
+  auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   if (count == 0) return cudaSuccess;
   kern<<<count, SS_BS, smem, stream>>>(items, n, p, r0, out, node0);

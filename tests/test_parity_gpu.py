@@ -201,3 +201,21 @@ def test_host_input_path():
         r, q = oracle.parallel_space_saving(x, k, p)
         assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == summary_entries(r)
         assert (e.m, e.n_covered) == (r.m, r.n_covered)
+
+
+def test_fuzz_small_universes():
+    # Many skips, conversions and in-window epoch ends: small k, small
+    # universes, skewed draws, windows cut at every kind of boundary.
+    rng = np.random.default_rng(20261203)
+    for trial in range(60):
+        k = int(rng.integers(2, 300))
+        n = int(rng.integers(0, 60_000))
+        p = int(rng.integers(1, 9))
+        u = int(rng.integers(2, 4 * k + 50))
+        a = 1.05 + 1.5 * rng.random()
+        ranks = np.minimum(rng.zipf(a, size=n), u) - 1
+        perm = rng.permutation(u).astype(np.uint64)
+        w = 8 if trial % 3 == 0 else 4
+        vals = perm[ranks] * np.uint64(2654435761 if w == 4 else 0x9E3779B97F4A7C15 >> 1)
+        x = vals.astype(np.uint32) if w == 4 else vals.astype(np.uint64)
+        compare_tree(x, k, p)
