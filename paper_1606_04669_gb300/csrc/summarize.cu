@@ -78,9 +78,7 @@ struct SSState {
   uint32_t nvalid, nhit, j0;  // candidate compaction
   uint32_t nskip, nconv, astop;
   uint32_t cut;          // exact prefix of the window
-  uint32_t amax;         // 1 + largest candidate index applied (0: none)
   uint32_t exhausted;
-  uint32_t napplied;     // events applied in a filling window
   uint32_t need;         // 0 none, 1 incremental list rebuild, 2 full
   uint32_t maxdisp;      // largest bucket displacement since the last table rebuild
   uint32_t stall;
@@ -304,68 +302,83 @@ struct SSBlock {
   }
 
   // Build the bucket list of the minimum count, oldest touch first.  `now` is
-  // the position of the next item to process.
-  __device__ void rebuild_list(bool full_scan, uint32_t now) {
+  // the position of the next item to process.  Returns true when the large
+  // sort wrote over the window scratch (which must then be reset).
+  __device__ bool rebuild_list(bool full_scan, uint32_t now) {
+    // thread-contiguous ranges of counters: [c0, c1)
+    const uint32_t per = (k + BS - 1) / BS;
+    const uint32_t c0 = min(threadIdx.x * per, k), c1 = min(c0 + per, k);
     uint32_t mn = 0xFFFFFFFFu;
-    for (uint32_t i = threadIdx.x; i < k; i += BS) mn = min(mn, s.cnt[i]);
+    for (uint32_t i = c0; i < c1; ++i) mn = min(mn, s.cnt[i]);
     mn = block_min_u32<BS>(mn, s.wsum);
     const bool incremental = !full_scan && mn == S->m + 1;
     const uint32_t epoch = S->epoch_start;
     // (a) members to sort by touch: all of them, or those older than the epoch
-    uint32_t n1 = 0;
-    for (uint32_t base = 0; base < k; base += BS) {
-      const uint32_t i = base + threadIdx.x;
-      bool f = false;
-      if (i < k) f = s.cnt[i] == mn && (!incremental || s.touch[i] < epoch);
-      uint32_t tot;
-      const uint32_t ex = scan(f ? 1u : 0u, &tot);
-      if (f) {
-        s.rkey[n1 + ex] = s.touch[i];
-        s.rpay[n1 + ex] = (uint16_t)i;
+    uint32_t nloc = 0;
+    for (uint32_t i = c0; i < c1; ++i)
+      nloc += (s.cnt[i] == mn && (!incremental || s.touch[i] < epoch)) ? 1u : 0u;
+    uint32_t n1;
+    uint32_t o = scan(nloc, &n1);
+    const bool small = n1 <= (uint32_t)BS;
+    uint32_t* key = small ? (uint32_t*)s.cand : s.rkey;   // cand holds >= 2 * BS u16 = BS u32
+    uint16_t* pay = small ? s.candidx : s.rpay;
+    for (uint32_t i = c0; i < c1; ++i) {
+      if (s.cnt[i] == mn && (!incremental || s.touch[i] < epoch)) {
+        key[o] = s.touch[i];
+        pay[o] = (uint16_t)i;
+        ++o;
       }
-      n1 += tot;
-    }
-    const uint32_t n2p = next_pow2(n1 ? n1 : 1);
-    for (uint32_t i = n1 + threadIdx.x; i < n2p; i += BS) {
-      s.rkey[i] = 0xFFFFFFFFu;
-      s.rpay[i] = 0xFFFF;
     }
     __syncthreads();
-    // ascending by (touch, slot); touches of distinct counters differ
-    for (uint32_t size = 2; size <= n2p; size <<= 1) {
-      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t i = threadIdx.x; i < (n2p >> 1); i += BS) {
-          const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
-          const bool asc = (lo & size) == 0;
-          const uint32_t a = s.rkey[lo], b = s.rkey[hi];
-          const uint16_t pa = s.rpay[lo], pb = s.rpay[hi];
-          const bool greater = (a > b) || (a == b && pa > pb);
-          if (greater == asc) {
-            s.rkey[lo] = b; s.rkey[hi] = a;
-            s.rpay[lo] = pb; s.rpay[hi] = pa;
-          }
-        }
-        __syncthreads();
+    if (small) {
+      // touches of distinct counters differ: rank = number of smaller keys
+      if (threadIdx.x < n1) {
+        const uint32_t my = key[threadIdx.x];
+        uint32_t rk = 0;
+        for (uint32_t j = 0; j < n1; ++j) rk += key[j] < my ? 1u : 0u;
+        s.list[rk] = pay[threadIdx.x];
       }
+    } else {
+      const uint32_t n2p = next_pow2(n1);
+      for (uint32_t i = n1 + threadIdx.x; i < n2p; i += BS) {
+        key[i] = 0xFFFFFFFFu;
+        pay[i] = 0xFFFF;
+      }
+      __syncthreads();
+      for (uint32_t size = 2; size <= n2p; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t i = threadIdx.x; i < (n2p >> 1); i += BS) {
+            const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+            const bool asc = (lo & size) == 0;
+            const uint32_t a = key[lo], b = key[hi];
+            if ((a > b) == asc) {
+              key[lo] = b; key[hi] = a;
+              const uint16_t t = pay[lo]; pay[lo] = pay[hi]; pay[hi] = t;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (uint32_t i = threadIdx.x; i < n1; i += BS) s.list[i] = pay[i];
     }
-    for (uint32_t i = threadIdx.x; i < n1; i += BS) s.list[i] = s.rpay[i];
     // (b) the log: members that reached count mn during the epoch, in time order
     uint32_t n = n1;
     if (incremental) {
       const uint32_t ll = S->log_len;
-      for (uint32_t base = 0; base < ll; base += BS) {
-        const uint32_t j = base + threadIdx.x;
-        bool f = false;
-        uint16_t q = 0;
-        if (j < ll) {
-          q = s.logq[j];
-          f = s.cnt[q] == mn;
+      const uint32_t lper = (ll + BS - 1) / BS;
+      const uint32_t l0 = min(threadIdx.x * lper, ll), l1 = min(l0 + lper, ll);
+      uint32_t lc = 0;
+      for (uint32_t j = l0; j < l1; ++j) lc += s.cnt[s.logq[j]] == mn ? 1u : 0u;
+      uint32_t tot;
+      uint32_t lo = n1 + scan(lc, &tot);
+      for (uint32_t j = l0; j < l1; ++j) {
+        const uint16_t q = s.logq[j];
+        if (s.cnt[q] == mn) {
+          if (lo < k) s.list[lo] = q;
+          ++lo;
         }
-        uint32_t tot;
-        const uint32_t ex = scan(f ? 1u : 0u, &tot);
-        if (f && n + ex < k) s.list[n + ex] = q;
-        n += tot;
       }
+      n += tot;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -376,6 +389,7 @@ struct SSBlock {
       S->epoch_start = now;
     }
     __syncthreads();
+    return !small;
   }
 };
 
@@ -451,13 +465,42 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
     int sl[IPT];
     uint32_t wc[IPT];
     uint32_t miss = 0, mhit = 0;  // bit j: item j missed / hit a bucket member
+    {
+      // home buckets of all items first (independent loads), then resolve
+      uint4 hc[IPT];
+      uint32_t hd[IPT], tg[IPT];
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t h = ItemOps<ItemT>::h1(x[j]);
+        const uint32_t b = h >> s.nbshift;
+        tg[j] = h & 0xFFFFu;
+        hc[j] = *(const uint4*)&s.cell[b * 4];
+        hd[j] = s.dmax[b];
+      }
+      int q1[IPT];
+      ItemT it1[IPT];
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t cs[4] = {hc[j].x, hc[j].y, hc[j].z, hc[j].w};
+        q1[j] = -1;
+#pragma unroll
+        for (int i = 3; i >= 0; --i)
+          if (cs[i] && (cs[i] >> 16) == tg[j]) q1[j] = (int)(cs[i] & 0xFFFFu) - 1;
+        it1[j] = q1[j] >= 0 ? s.item[q1[j]] : (ItemT)0;
+      }
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        if (q1[j] >= 0 && it1[j] == x[j]) sl[j] = q1[j];
+        else if (q1[j] < 0 && hd[j] == 0) sl[j] = -1;
+        else sl[j] = B.lookup(x[j]);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const uint32_t rel = tid * IPT + j;
-      sl[j] = -1;
       wc[j] = 0;
+      if (rel >= nact) sl[j] = -1;
       if (rel < nact) {
-        sl[j] = B.lookup(x[j]);
         if (sl[j] < 0) {
           miss |= 1u << j;
           wc[j] = B.wtab_insert(x[j], rel);
@@ -490,9 +533,7 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
     }
     if (tid == 0) {
       S.cut = nact;
-      S.amax = 0;
       S.exhausted = 0;
-      S.napplied = 0;
       S.nvalid = 0;
       S.nhit = 0;
       S.j0 = S.head;
@@ -544,9 +585,18 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
       const uint32_t nv = S.nvalid, nh = S.nhit;
       uint32_t nskip = 0, nconv = 0, astop = nv;
       uint32_t ct = NONE32, clo = 0, cs = 0;  // conversion held by this lane, sorted by time
-      for (uint32_t hi = 0; hi < nh; ++hi) {
-        const uint32_t a = s.hitc[hi];
-        const uint32_t hq = s.hfirst[s.cand[a]];
+      bool done = false;
+      for (uint32_t hb = 0; hb < nh && !done; hb += 32) {
+       // this batch's hit members, one per lane
+       uint32_t a_l = 0, hq_l = 0;
+       if (hb + lane < nh) {
+         a_l = s.hitc[hb + lane];
+         hq_l = s.hfirst[s.cand[a_l]];
+       }
+       const uint32_t nb_ = min(32u, nh - hb);
+       for (uint32_t ii = 0; ii < nb_; ++ii) {
+        const uint32_t a = __shfl_sync(0xffffffffu, a_l, ii);
+        const uint32_t hq = __shfl_sync(0xffffffffu, hq_l, ii);
         const uint32_t e = a - nskip;  // the event that reaches this member
         const uint32_t mi = lane < nconv ? lane + clo : NONE32;
         const unsigned bc = __ballot_sync(0xffffffffu, mi == e);
@@ -556,12 +606,16 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
         } else {
           const uint32_t nb = __popc(__ballot_sync(0xffffffffu, mi < e));
           const uint32_t i = e - nb;
-          if (i >= M) break;  // no event reaches this member, nor any later one
+          if (i >= M) {  // no event reaches this member, nor any later one
+            done = true;
+            break;
+          }
           tau = s.rankpos[i];
         }
         if (hq < tau) {  // hit before its turn: it leaves the bucket
           if (nskip == HMAX) {
             astop = a;
+            done = true;
             break;
           }
           if (lane == 0) s.skipl[nskip] = (uint16_t)a;
@@ -569,6 +623,7 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
         } else {  // evicted at tau; its item comes back at hq
           if (nconv == CONVMAX) {
             astop = a;
+            done = true;
             break;
           }
           const uint32_t lo = warp_lower_bound(s.rankpos, M, hq);
@@ -588,6 +643,7 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
           }
           ++nconv;
         }
+       }
       }
       if (lane < nconv) {
         s.convt[lane] = (uint16_t)ct;
@@ -608,12 +664,10 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
     const bool can_exhaust = full && list_end && S.astop >= S.nvalid;
     const uint32_t nfree = full ? 0u : k - S.used;
     const uint32_t used0 = S.used;
+    // event e passes skipped member i iff e >= skipl[i] - i
     auto assign = [&](uint32_t e) {
       uint32_t a = e;
-      for (uint32_t i = 0; i < nskip; ++i) {
-        if (s.skipl[i] <= a) ++a;
-        else break;
-      }
+      for (uint32_t i = 0; i < nskip; ++i) a += (s.skipl[i] - i <= e) ? 1u : 0u;
       return a;
     };
     uint32_t vict[IPT];
@@ -669,7 +723,6 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
     __syncthreads();
 
     // ---- P7: insertions; new counters start at m (their occurrences are added next)
-    uint32_t napp = 0;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const uint32_t rel = tid * IPT + j;
@@ -681,12 +734,7 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
       s.err[v] = full ? m : 0u;
       s.touch[v] = 0;
       s.wslot[wc[j]] = (uint16_t)v;
-      if (full) {
-        s.logpos[rel] = (uint16_t)(v + 1);
-        atomicMax(&S.amax, va[j] + 1u);
-      } else {
-        ++napp;
-      }
+      if (full) s.logpos[rel] = (uint16_t)(v + 1);
     }
     if (tid < nconv && ctime < cut) {
       B.insert(citem, cvict, status);
@@ -696,9 +744,7 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
       s.touch[cvict] = 0;
       s.fate[csrc] = (uint16_t)(cvict + 1);
       s.logpos[ctime] = (uint16_t)(cvict + 1);
-      atomicMax(&S.amax, cva + 1u);
     }
-    if (!full && napp) atomicAdd(&S.napplied, napp);
     __syncthreads();
 
     // ---- P8: every occurrence before the cut adds one to its counter
@@ -753,27 +799,33 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
       }
     }
     if (tid < nconv) s.fate[csrc] = 0;
-    if (tid == 0) {
-      const uint32_t nlog = S.log_len + ltot;
-      S.log_len = nlog < k ? nlog : k;
-      if (full) {
-        if (S.amax) S.head = s.candidx[S.amax - 1u] + 1u;
-        if (S.exhausted && cut < nact) S.need = 1;
-      } else {
-        S.used += S.napplied;
-        if (S.used == k) {
-          S.full = 1;
-          S.need = 2;
+    if (warp == 0) {
+      // the applied events are the prefix of the merged sequence before the cut
+      const uint32_t norig = warp_lower_bound(s.rankpos, M, cut);
+      const uint32_t nc = __popc(__ballot_sync(0xffffffffu, lane < nconv && s.convt[lane] < cut));
+      const uint32_t nev = norig + nc;
+      if (lane == 0) {
+        const uint32_t nlog = S.log_len + ltot;
+        S.log_len = nlog < k ? nlog : k;
+        if (full) {
+          if (nev) S.head = s.candidx[assign(nev - 1)] + 1u;
+          if (S.exhausted && cut < nact) S.need = 1;
+        } else {
+          S.used += norig;
+          if (S.used == k) {
+            S.full = 1;
+            S.need = 2;
+          }
         }
+        S.stall = cut ? 0u : S.stall + 1u;
       }
-      S.stall = cut ? 0u : S.stall + 1u;
     }
     __syncthreads();
     const uint32_t need = S.need;
     if (need) {
-      B.rebuild_list(need == 2, t0 + cut);
+      const bool clobbered = B.rebuild_list(need == 2, t0 + cut);
       if (S.maxdisp > 2) B.rebuild_table(status);
-      B.reset_window_scratch();
+      if (clobbered) B.reset_window_scratch();
     }
     if (S.stall >= 3) {
       status |= ST_NOPROGRESS;
