@@ -102,6 +102,39 @@ int pss_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k, u
 int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
                        void* stream, pss_summary** out);
 
+/* Size of the fixed device array pss_summarize_noalloc works in (32 MiB). */
+#define PSS_NOALLOC_SCRATCH_BYTES (32ull << 20)
+
+/*
+ * pss_summarize_noalloc — the computation of pss_summarize for callers that
+ * cannot allocate device memory: processes that own all device memory
+ * through their own allocator, or that run under a fixed budget and must not
+ * allocate once started (a serving process, for instance).  The paper has no
+ * counterpart; this is a deployment variant of the same kernels.
+ *   - It calls no cudaMalloc, cudaFree or stream-ordered allocation.  The
+ *     block summaries and the reduction tree live in one fixed array of
+ *     PSS_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that
+ *     loads the library holds that array until the process exits.
+ *   - Limit: the p block summaries plus ceil(p/2) merged summaries must fit
+ *     in the array (about 1.5 p k (item_bytes + 16) bytes; e.g. p = 8,
+ *     k = 2000 fits, p = 4096, k = 2000 does not); otherwise PSS_ERANGE and
+ *     nothing is enqueued.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call uses the same array and leaves its contents there: calls
+ *     whose work overlaps on the GPU (other streams, other host threads) race
+ *     and must be serialized by the caller.
+ *   - Outputs, in caller-owned device memory: d_out_items (k items of
+ *     item_bytes), d_out_counts and d_out_errs (k values) receive the root
+ *     summary sorted by item ascending; d_out_header[4] = {size, m,
+ *     n_covered, status}, status != 0 meaning a kernel recorded an error.
+ * Arguments otherwise as pss_summarize.  Asynchronous on stream.
+ */
+int pss_summarize_noalloc(const void* d_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
+                          void* d_out_items, uint64_t* d_out_counts, uint64_t* d_out_errs,
+                          uint64_t* d_out_header, void* stream);
+
 /*
  * pss_summarize_tree — the same computation as pss_summarize, keeping every
  * level of the reduction tree (level 0 = the p block summaries, last level =

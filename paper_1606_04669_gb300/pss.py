@@ -59,6 +59,8 @@ SIGNATURES = {
     "pss_abi_version": (ctypes.c_int, []),
     "pss_summarize": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, ctypes.POINTER(vp)]),
     "pss_summarize_host": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, ctypes.POINTER(vp)]),
+    "pss_summarize_noalloc": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, u64p, u64p, u64p,
+                                             vp]),
     "pss_summarize_tree": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, ctypes.POINTER(vp)]),
     "pss_tree_levels": (ctypes.c_int, [vp, u32p]),
     "pss_tree_level_nodes": (ctypes.c_int, [vp, u32, u32p]),
