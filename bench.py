@@ -51,6 +51,30 @@ WORKLOADS = {
 }
 
 
+# DRAM traffic of the summarize kernel from one ncu capture (profiles/
+# ss_block_kernel_wave_k2000.md: 304 blocks of 262144 u32 items, k = 2000 ->
+# 318.92 MB read + 3.39 MB written).  Traffic grows with the number of blocks,
+# so a launch of p such blocks moves p times the per-block bytes.  The figure
+# is only valid for the kernel source it was measured on.
+TRAFFIC = {"summarize_sha1": "a9c764559b351332b73475f8825f5c394c13d7b6",
+           "bytes_per_block": (318.92e6 + 3.39e6) / 304, "block_items": 262144, "k": 2000, "w": 4}
+
+
+def traffic_per_launch(wl):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1606_04669_gb300", "csrc", "summarize.cu")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    t = TRAFFIC
+    if sha != t["summarize_sha1"] or wl["k"] != t["k"] or wl["w"] != t["w"]:
+        return None
+    if wl["n"] // wl["p"] != t["block_items"]:
+        return None
+    return t["bytes_per_block"] * wl["p"]
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -120,22 +144,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(wl, budget_s: float, max_blocks: int = 64):
+def cpu_baseline(wl, budget_s: float, seed_offset: int = 0):
     """The oracle, single-threaded on a host core, over the first B blocks of
     the workload (block summaries + their combine tree + query); B is sized so
-    the oracle works about budget_s seconds.  Input generation is not timed."""
-    import numpy as np
-
+    the oracle works about budget_s seconds.  Input generation (threaded) is
+    not timed."""
     import oracle
     n, k, p, w = wl["n"], wl["k"], wl["p"], wl["w"]
+    threads = os.cpu_count() or 1
     lo0, hi0 = oracle.block_bounds(n, p, 0)
-    x0 = oracle.gen_zipf(hi0 - lo0, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w)
+    x0 = oracle.gen_zipf(hi0 - lo0, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w,
+                         stream=seed_offset, threads=threads)
     t = time.perf_counter()
     oracle.space_saving(x0, k)
     per_block = max(time.perf_counter() - t, 1e-6)
-    blocks = int(max(2, min(max_blocks, p, budget_s / per_block)))
+    blocks = int(max(2, min(p, budget_s / per_block)))
     hi = oracle.block_bounds(n, p, blocks - 1)[1]
-    x = oracle.gen_zipf(hi, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w)
+    x = oracle.gen_zipf(hi, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w,
+                        stream=seed_offset, threads=threads)
     t = time.perf_counter()
     levels = oracle.pss_tree(x, k, blocks)
     oracle.query(levels[-1][0], hi, k)
@@ -184,17 +210,82 @@ def run_reference(args, wl, rank):
     return 0
 
 
+SWEEP_S = (0.5, 1.0, 1.5, 2.0, 3.0)
+SWEEP_K = (500, 1000, 2000, 4000)
+
+
+def run_sweep(args):
+    """Skew x k sweep of the plain path: n = 2^30 uint32 over [0, 2^32),
+    p = 4096, seed = 10 + 4 * i_s + i_k; one JSON line per point."""
+    import torch
+
+    import paper_1606_04669_gb300 as P
+    hbm, peak_kind = peaks()
+    n, p, w = 1 << 30, 4096, 4
+    stream = torch.cuda.current_stream()
+    x = torch.empty(n, dtype=torch.int32, device="cuda")
+    for i_s, zs in enumerate(SWEEP_S):
+        for i_k, k in enumerate(SWEEP_K):
+            if args.points and f"{zs}:{k}" not in args.points.split(","):
+                continue
+            seed = 10 + 4 * i_s + i_k
+            P.gen_zipf(n, seed=seed, s=zs, log2u=32, out=x)
+            torch.cuda.synchronize()
+
+            def step():
+                sm = P.summarize(x, k, p, stream=stream)
+                q = sm.query(n, k, stream=stream)
+                sm.close()
+                return q
+
+            for _ in range(max(args.warmup, 1)):
+                q = step()
+            torch.cuda.synchronize()
+            P.profile_read(reset=True)
+            P.profile_enable(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                q = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof = P.profile_read(reset=True)
+            P.profile_enable(False)
+            ms = e0.elapsed_time(e1) / args.steps
+            sum_ms = prof["summarize_ms"] / max(prof["summarize_calls"], 1)
+            alg = n * w + p * k * (w + 16) + p * 24
+            line = {
+                "metric": METRIC, "workload": "sweep", "zipf_s": zs, "k": k, "seed": seed,
+                "value": n / (ms / 1e3), "unit": "items/s", "ms_per_step": ms,
+                "input_gbs": n * w / (ms / 1e3) / 1e9, "hbm_frac": n * w / (ms / 1e3) / 1e9 / hbm,
+                "summarize_ms": sum_ms, "merge_tree_ms": prof["merge_ms"] / args.steps,
+                "roofline": {"bound": "hbm", "achieved": alg / (sum_ms / 1e3) / 1e9, "peak": hbm,
+                             "peak_kind": peak_kind, "unit": "GB/s",
+                             "frac": alg / (sum_ms / 1e3) / 1e9 / hbm},
+                "frequent_items": int(q.size), "steps": args.steps, "warmup": args.warmup,
+                "config": {"n": n, "p": p, "universe": "2^32", "item_bytes": w},
+            }
+            print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["sweep"], default="plain")
+    ap.add_argument("--points", default="", help="sweep points to run, e.g. 0.5:500,1.1:2000")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
+    if args.workload == "sweep":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        return run_sweep(args)
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -321,7 +412,8 @@ def main():
             "hbm_frac_nominal_8tbs": input_gbs / 8000.0,
             "roofline": {"bound": "hbm", "kernel": "ss_block_kernel (block summaries)",
                          "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
-                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": traffic_per_launch(wl),
                          "avg_launch_ms": sum_ms, "algorithmic_bytes": alg_bytes},
             "breakdown": {"summarize_ms": sum_ms, "merge_tree_ms": merge_ms,
                           "query_ms": query_ms,

@@ -168,6 +168,60 @@ int pss_tree_root(const pss_tree* tree, void* stream, pss_summary** out);
 void pss_tree_free(pss_tree* tree);
 
 /*
+ * Batched form: many independent streams, each with its own k and p, in one
+ * launch graph.  For every distinct k one persistent summarize kernel takes
+ * (stream, block) tasks from a work list, longest blocks first; one combine
+ * launch per tree level covers that level of every stream; one launch
+ * answers every stream's query.  Each stream's result is exactly that of
+ * pss_summarize + pss_query with the same k and p (Algorithm 1 and 2 are
+ * applied per stream; batching changes only the launch structure).
+ */
+typedef struct pss_batch pss_batch;
+
+typedef struct {
+  uint32_t nstreams;
+  int item_bytes;                /* 4 or 8, the same for every stream */
+  const void* const* d_items;    /* nstreams device pointers */
+  const uint64_t* n;             /* nstreams lengths */
+  const uint32_t* k;             /* nstreams counter counts, 2 <= k <= PSS_MAX_K */
+  const uint32_t* p;             /* nstreams block counts; NULL or 0 entries: pss_plan_blocks */
+  const double* skew_hint;       /* optional per-stream skew for the planner (NULL: unknown) */
+} pss_batch_desc;
+
+/* The planner's block count for a stream of n items with k counters: a pure
+ * function of its arguments (never of load), so a result can be replayed. */
+uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint);
+
+/* Plan and allocate a batch (device memory for every stream's tree, task
+ * lists, results).  The streams' item buffers are borrowed for the batch's
+ * lifetime.  Synchronizes stream. */
+int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out);
+
+/* The block count used for each stream (nstreams values). */
+int pss_batch_plan(const pss_batch* batch, uint32_t* p);
+
+/* Counts of a batch (any pointer may be NULL). */
+int pss_batch_info(const pss_batch* batch, uint32_t* nstreams, uint64_t* total_items,
+                   uint64_t* total_k, uint32_t* k_classes);
+
+/* Enqueue the whole batch on stream.  use_graph != 0: captured as a CUDA
+ * graph on the first call (stream must not be capturing) and replayed
+ * afterwards.  Asynchronous. */
+int pss_batch_run(pss_batch* batch, int use_graph, void* stream);
+
+/* Every stream's query result: stream i's entries are at host_out + (sum of
+ * k over streams before i), host_counts[i] of them.  Synchronizes stream;
+ * PSS_EDEVICE if a kernel recorded an error in any stream. */
+int pss_batch_results(pss_batch* batch, pss_entry* host_out, uint32_t* host_counts, void* stream);
+
+/* Canonical export of stream `index`'s root summary (as pss_export). */
+int pss_batch_export(pss_batch* batch, uint32_t index, pss_entry* host_out, uint32_t cap,
+                     uint32_t* size, uint64_t* m, uint64_t* n_covered, void* stream);
+
+/* Release a batch (stream-ordered on the stream that created it). */
+void pss_batch_free(pss_batch* batch);
+
+/*
  * pss_merge — combine(S1, S2, k) of Algorithm 2: union of the items; an item
  * in both gets count1 + count2 (err1 + err2); an item in one only gets the
  * other summary's minimum added to its count and to its err; Prune(k) keeps

@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           "-o", tmp, _SRC]
+           "-pthread", "-o", tmp, _SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -79,6 +79,10 @@ def _load():
         lib.oracle_gen_zipf.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                         ctypes.c_double, ctypes.c_int]
+        lib.oracle_gen_zipf_mt.restype = None
+        lib.oracle_gen_zipf_mt.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int]
         lib.oracle_gen_zipf_ranks.restype = None
         lib.oracle_gen_zipf_ranks.argtypes = [u64p, ctypes.c_uint64, ctypes.c_uint64,
                                               ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
@@ -235,12 +239,16 @@ def philox4x32_10(counter, key):
 
 
 def gen_zipf(count: int, *, seed: int, s: float, log2u: int, width: int = 4, stream: int = 0,
-             start: int = 0) -> np.ndarray:
+             start: int = 0, threads: int = 1) -> np.ndarray:
     """Items [start, start+count) of the seeded Zipf stream (host side)."""
     lib = _load()
     out = np.empty(count, np.uint32 if width == 4 else np.uint64)
-    lib.oracle_gen_zipf(out.ctypes.data_as(ctypes.c_void_p), start, count, width, seed, stream,
-                        float(s), log2u)
+    if threads > 1:
+        lib.oracle_gen_zipf_mt(out.ctypes.data_as(ctypes.c_void_p), start, count, width, seed,
+                               stream, float(s), log2u, threads)
+    else:
+        lib.oracle_gen_zipf(out.ctypes.data_as(ctypes.c_void_p), start, count, width, seed,
+                            stream, float(s), log2u)
     return out
 
 

@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <thread>
 #include <cstring>
 #include <unordered_map>
 #include <vector>
@@ -359,6 +360,22 @@ void oracle_gen_zipf(void* out, uint64_t start, uint64_t count, int width, uint6
     else
       ((uint64_t*)out)[i] = x;
   }
+}
+
+// The same items, generated by `threads` host threads (input preparation for
+// large oracle runs; the oracle's own computation stays single-threaded).
+void oracle_gen_zipf_mt(void* out, uint64_t start, uint64_t count, int width, uint64_t seed,
+                        uint32_t stream, double s, int log2u, int threads) {
+  if (threads < 1) threads = 1;
+  std::vector<std::thread> pool;
+  const uint64_t per = (count + threads - 1) / threads;
+  for (int t = 0; t < threads; ++t) {
+    const uint64_t lo = per * t, hi = std::min(count, lo + per);
+    if (lo >= hi) break;
+    char* base = (char*)out + lo * (uint64_t)width;
+    pool.emplace_back(oracle_gen_zipf, (void*)base, start + lo, hi - lo, width, seed, stream, s, log2u);
+  }
+  for (auto& th : pool) th.join();
 }
 
 // Ranks only (no bijection), for distribution tests of the generator.

@@ -1,0 +1,471 @@
+// batch.cu — many independent streams, each summarized with its own k and p,
+// in one launch graph: for every distinct k a persistent summarize kernel
+// takes (stream, block) tasks from a work list (longest blocks first), then
+// one combine launch per tree level covers that level of every stream, then
+// one launch answers every stream's query.  The k classes run on forked
+// streams; the whole sequence can be captured once as a CUDA graph and
+// replayed.  Each stream's result is exactly pss_summarize + pss_query with
+// the same k and p (the tree of Algorithm 1 and the combine of Algorithm 2 are
+// per stream; batching only changes the launch structure).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pss_internal.cuh"
+#include "pss_kernels.cuh"
+
+using namespace pss;
+
+namespace {
+
+struct StreamPlan {
+  const void* items;
+  uint64_t n;
+  uint32_t k, p;
+  std::vector<size_t> level_off;     // arena offset of each level's set
+  std::vector<uint32_t> level_nodes;
+  uint32_t out_off;                  // first result entry of this stream
+};
+
+struct LevelLaunch {
+  size_t descs_off, tasks_off;
+  uint32_t ntasks;
+};
+
+struct KClass {
+  uint32_t k = 0;
+  std::vector<uint32_t> sids;
+  size_t tasks_off = 0, counter_off = 0, qids_off = 0;
+  uint32_t ntasks = 0, grid = 0;
+  std::vector<LevelLaunch> levels;
+  cudaStream_t side = nullptr;
+  cudaEvent_t join = nullptr;
+};
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return PSS_OK;
+  if (e == cudaErrorMemoryAllocation) return PSS_ENOMEM;
+  return PSS_ECUDA;
+}
+
+__global__ void zero_words_kernel(char* arena, const size_t* offs, uint32_t count) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    *(uint32_t*)(arena + offs[i]) = 0u;
+}
+
+}  // namespace
+
+struct pss_batch {
+  uint32_t nstreams = 0;
+  int w = 4;
+  std::vector<StreamPlan> s;
+  std::vector<KClass> kc;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  size_t streams_off = 0, qdesc_off = 0, results_off = 0, nout_off = 0, status_offs_off = 0;
+  uint32_t nstatus = 0;
+  uint64_t total_k = 0;
+  uint64_t total_items = 0;
+  cudaStream_t owner = nullptr;
+  cudaStream_t capture = nullptr;  // the graph is captured here, launched on the caller's stream
+  uint64_t graph_launches = 0;     // kernels per graph launch
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint) {
+  (void)item_bytes;
+  (void)skew_hint;
+  // Block length: long enough that the per-block fixed work (table fill,
+  // final sort, summary write of up to k entries) stays small next to the
+  // block's items, short enough to give every SM several blocks.
+  const uint64_t len = k <= 256 ? (1ull << 17) : (k <= 1024 ? (1ull << 18) : (1ull << 19));
+  uint64_t p = (n + len - 1) / len;
+  if (p == 0) p = 1;
+  while ((n + p - 1) / p >= (1ull << 32)) ++p;
+  if (p > 0x7FFFFFFFull) p = 0x7FFFFFFFull;
+  return (uint32_t)p;
+}
+
+namespace {
+
+template <typename ItemT>
+int enqueue(pss_batch* b, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->fork, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  // status words of every set start clear (a set's status collects kernel errors)
+  e = cudaStreamWaitEvent(b->kc[0].side, b->fork, 0);
+  if (e != cudaSuccess) return from_cuda(e);
+  count_launches(1);
+  zero_words_kernel<<<64, 256, 0, b->kc[0].side>>>(
+      b->arena, (const size_t*)(b->arena + b->status_offs_off), b->nstatus);
+  if ((e = cudaGetLastError()) != cudaSuccess) return from_cuda(e);
+  e = cudaEventRecord(b->kc[0].join, b->kc[0].side);
+  if (e != cudaSuccess) return from_cuda(e);
+  for (KClass& c : b->kc) {
+    e = cudaStreamWaitEvent(c.side, b->kc[0].join, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = cudaMemsetAsync(b->arena + c.counter_off, 0, 4, c.side);
+    if (e != cudaSuccess) return from_cuda(e);
+    {
+      ProfScope prof(PROF_SUMMARIZE, c.side, 1);
+      count_launches(1);
+      e = launch_summarize_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
+                                        (const BatchTask*)(b->arena + c.tasks_off), c.ntasks,
+                                        (uint32_t*)(b->arena + c.counter_off), c.k, c.grid, c.side);
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    {
+      ProfScope prof(PROF_MERGE, c.side, c.levels.size());
+      for (const LevelLaunch& L : c.levels) {
+        count_launches(1);
+        e = launch_merge_tasks<ItemT>((const MergeDesc*)(b->arena + L.descs_off),
+                                      (const BatchTask*)(b->arena + L.tasks_off), L.ntasks, c.k,
+                                      c.side);
+        if (e != cudaSuccess) return from_cuda(e);
+      }
+    }
+    {
+      ProfScope prof(PROF_QUERY, c.side, 1);
+      count_launches(1);
+      e = launch_query_batch<ItemT>((const QueryDesc*)(b->arena + b->qdesc_off),
+                                    (const uint32_t*)(b->arena + c.qids_off),
+                                    (uint32_t)c.sids.size(), c.k,
+                                    (pss_entry*)(b->arena + b->results_off),
+                                    (uint32_t*)(b->arena + b->nout_off), c.side);
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    e = cudaEventRecord(c.join, c.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c.join, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return PSS_OK;
+}
+
+void destroy(pss_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->arena) cudaFreeAsync(b->arena, b->owner);
+  for (KClass& c : b->kc) {
+    if (c.side) {
+      cudaStreamSynchronize(c.side);
+      cudaStreamDestroy(c.side);
+    }
+    if (c.join) cudaEventDestroy(c.join);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->capture) {
+    cudaStreamSynchronize(b->capture);
+    cudaStreamDestroy(b->capture);
+  }
+  delete b;
+}
+
+}  // namespace
+
+extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out) {
+  if (!desc || !out) return PSS_EINVAL;
+  *out = nullptr;
+  const uint32_t ns = desc->nstreams;
+  const int w = desc->item_bytes;
+  if (ns == 0 || (w != 4 && w != 8) || !desc->d_items || !desc->n || !desc->k) return PSS_EINVAL;
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return PSS_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  pss_batch* b = new (std::nothrow) pss_batch;
+  if (!b) return PSS_ENOMEM;
+  b->nstreams = ns;
+  b->w = w;
+  b->owner = s;
+  b->s.resize(ns);
+  // ---- plan every stream and lay out its tree levels
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = align_up(off, 256);
+    off = o + bytes;
+    return o;
+  };
+  std::vector<uint32_t> kvals;
+  for (uint32_t i = 0; i < ns; ++i) {
+    StreamPlan& sp = b->s[i];
+    sp.items = desc->d_items[i];
+    sp.n = desc->n[i];
+    sp.k = desc->k[i];
+    const double skew = desc->skew_hint ? desc->skew_hint[i] : 0.0;
+    sp.p = (desc->p && desc->p[i]) ? desc->p[i] : pss_plan_blocks(sp.n, sp.k, w, skew);
+    if (sp.k < 2 || sp.k > PSS_MAX_K || sp.p == 0 || (sp.n > 0 && !sp.items) ||
+        (sp.n + sp.p - 1) / sp.p >= (1ull << 32)) {
+      destroy(b);
+      return PSS_EINVAL;
+    }
+    const size_t need = w == 4 ? ss_smem_bytes<uint32_t>(sp.k) : ss_smem_bytes<u64>(sp.k);
+    const size_t need_m = w == 4 ? merge_smem_bytes<uint32_t>(sp.k) : merge_smem_bytes<u64>(sp.k);
+    if (need > (size_t)optin || need_m > (size_t)optin) {
+      destroy(b);
+      return PSS_EINVAL;
+    }
+    for (uint32_t nodes = sp.p;; nodes = (nodes + 1) / 2) {
+      sp.level_nodes.push_back(nodes);
+      sp.level_off.push_back(take(set_layout(nodes, sp.k, w).total));
+      if (nodes == 1) break;
+    }
+    sp.out_off = (uint32_t)b->total_k;
+    b->total_k += sp.k;
+    b->total_items += sp.n;
+    if (std::find(kvals.begin(), kvals.end(), sp.k) == kvals.end()) kvals.push_back(sp.k);
+  }
+  std::sort(kvals.begin(), kvals.end());
+  b->streams_off = take(sizeof(BatchStream) * ns);
+  b->qdesc_off = take(sizeof(QueryDesc) * ns);
+  b->results_off = take(sizeof(pss_entry) * b->total_k);
+  b->nout_off = take(sizeof(uint32_t) * 2 * ns);
+  // ---- per k class: tasks (longest blocks first), merge levels, query ids
+  std::vector<char> host;  // image of the descriptor part of the arena, filled below
+  struct Pending {
+    size_t off;
+    std::vector<char> bytes;
+  };
+  std::vector<Pending> uploads;
+  auto upload = [&](size_t o, const void* src, size_t bytes) {
+    Pending pd;
+    pd.off = o;
+    pd.bytes.assign((const char*)src, (const char*)src + bytes);
+    uploads.push_back(std::move(pd));
+  };
+  b->kc.resize(kvals.size());
+  for (size_t ci = 0; ci < kvals.size(); ++ci) {
+    KClass& c = b->kc[ci];
+    c.k = kvals[ci];
+    for (uint32_t i = 0; i < ns; ++i)
+      if (b->s[i].k == c.k) c.sids.push_back(i);
+    std::vector<BatchTask> tasks;
+    std::vector<uint64_t> lens;
+    for (uint32_t i : c.sids)
+      for (uint32_t r = 0; r < b->s[i].p; ++r) tasks.push_back(BatchTask{i, r});
+    std::vector<uint64_t> key(tasks.size());
+    for (size_t t = 0; t < tasks.size(); ++t) {
+      const StreamPlan& sp = b->s[tasks[t].stream];
+      key[t] = block_bound(tasks[t].index + 1ull, sp.n, sp.p) - block_bound(tasks[t].index, sp.n, sp.p);
+    }
+    std::vector<size_t> order(tasks.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t bb) { return key[a] > key[bb]; });
+    std::vector<BatchTask> sorted(tasks.size());
+    for (size_t t = 0; t < order.size(); ++t) sorted[t] = tasks[order[t]];
+    c.ntasks = (uint32_t)sorted.size();
+    c.tasks_off = take(sizeof(BatchTask) * (sorted.size() ? sorted.size() : 1));
+    upload(c.tasks_off, sorted.data(), sizeof(BatchTask) * sorted.size());
+    c.counter_off = take(4);
+    const int per_sm = w == 4 ? summarize_ctas_per_sm<uint32_t>(c.k) : summarize_ctas_per_sm<u64>(c.k);
+    if (per_sm <= 0) {
+      destroy(b);
+      return PSS_EINVAL;
+    }
+    c.grid = (uint32_t)std::min<uint64_t>((uint64_t)sms * per_sm, c.ntasks);
+    // merge levels: level l -> l + 1 for every stream of the class that has it
+    for (uint32_t l = 0;; ++l) {
+      std::vector<MergeDesc> descs;
+      std::vector<BatchTask> mt;
+      for (uint32_t i : c.sids) {
+        const StreamPlan& sp = b->s[i];
+        if (l + 1 >= sp.level_nodes.size()) continue;
+        const uint32_t d = (uint32_t)descs.size();
+        descs.push_back(MergeDesc{nullptr, nullptr, sp.level_nodes[l], sp.k});
+        // pointers are fixed once the arena exists; record offsets for now
+        descs.back().in = (void*)(uintptr_t)sp.level_off[l];
+        descs.back().out = (void*)(uintptr_t)sp.level_off[l + 1];
+        for (uint32_t j = 0; j < sp.level_nodes[l + 1]; ++j) mt.push_back(BatchTask{d, j});
+      }
+      if (descs.empty()) break;
+      LevelLaunch L;
+      L.descs_off = take(sizeof(MergeDesc) * descs.size());
+      L.tasks_off = take(sizeof(BatchTask) * mt.size());
+      L.ntasks = (uint32_t)mt.size();
+      upload(L.descs_off, descs.data(), sizeof(MergeDesc) * descs.size());
+      upload(L.tasks_off, mt.data(), sizeof(BatchTask) * mt.size());
+      c.levels.push_back(L);
+    }
+    c.qids_off = take(sizeof(uint32_t) * c.sids.size());
+    upload(c.qids_off, c.sids.data(), sizeof(uint32_t) * c.sids.size());
+  }
+  // status words of every set
+  std::vector<size_t> status_offs;
+  for (const StreamPlan& sp : b->s)
+    for (size_t l = 0; l < sp.level_off.size(); ++l)
+      status_offs.push_back(sp.level_off[l] + set_layout(sp.level_nodes[l], sp.k, w).status);
+  b->nstatus = (uint32_t)status_offs.size();
+  b->status_offs_off = take(sizeof(size_t) * status_offs.size());
+  b->arena_bytes = align_up(off, 256);
+  // ---- device memory and descriptors
+  cudaError_t e = cudaMallocAsync((void**)&b->arena, b->arena_bytes, s);
+  if (e != cudaSuccess) {
+    b->arena = nullptr;
+    destroy(b);
+    return from_cuda(e);
+  }
+  e = cudaStreamSynchronize(s);
+  std::vector<BatchStream> bs(ns);
+  std::vector<QueryDesc> qd(ns);
+  for (uint32_t i = 0; i < ns && e == cudaSuccess; ++i) {
+    const StreamPlan& sp = b->s[i];
+    bs[i] = BatchStream{sp.items, sp.n, sp.p, sp.k, b->arena + sp.level_off[0]};
+    qd[i] = QueryDesc{b->arena + sp.level_off.back(), sp.n, sp.k, sp.out_off};
+  }
+  for (Pending& pd : uploads) {  // merge descriptors: offsets -> pointers
+    for (KClass& c : b->kc)
+      for (LevelLaunch& L : c.levels)
+        if (pd.off == L.descs_off) {
+          MergeDesc* md = (MergeDesc*)pd.bytes.data();
+          const size_t cnt = pd.bytes.size() / sizeof(MergeDesc);
+          for (size_t t = 0; t < cnt; ++t) {
+            md[t].in = b->arena + (uintptr_t)md[t].in;
+            md[t].out = b->arena + (uintptr_t)md[t].out;
+          }
+        }
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(b->arena + b->streams_off, bs.data(), sizeof(BatchStream) * ns, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->arena + b->qdesc_off, qd.data(), sizeof(QueryDesc) * ns, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !status_offs.empty())
+    e = cudaMemcpy(b->arena + b->status_offs_off, status_offs.data(), sizeof(size_t) * status_offs.size(), cudaMemcpyHostToDevice);
+  for (Pending& pd : uploads)
+    if (e == cudaSuccess && !pd.bytes.empty())
+      e = cudaMemcpy(b->arena + pd.off, pd.bytes.data(), pd.bytes.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  for (KClass& c : b->kc) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming);
+    // set kernel attributes outside any capture
+    if (e == cudaSuccess)
+      e = w == 4 ? launch_merge_tasks<uint32_t>(nullptr, nullptr, 0, c.k, c.side)
+                 : launch_merge_tasks<u64>(nullptr, nullptr, 0, c.k, c.side);
+    if (e == cudaSuccess)
+      e = w == 4 ? launch_query_batch<uint32_t>(nullptr, nullptr, 0, c.k, nullptr, nullptr, c.side)
+                 : launch_query_batch<u64>(nullptr, nullptr, 0, c.k, nullptr, nullptr, c.side);
+  }
+  if (e != cudaSuccess) {
+    destroy(b);
+    return from_cuda(e);
+  }
+  *out = b;
+  return PSS_OK;
+}
+
+extern "C" int pss_batch_plan(const pss_batch* b, uint32_t* p) {
+  if (!b || !p) return PSS_EINVAL;
+  for (uint32_t i = 0; i < b->nstreams; ++i) p[i] = b->s[i].p;
+  return PSS_OK;
+}
+
+extern "C" int pss_batch_run(pss_batch* b, int use_graph, void* stream) {
+  if (!b) return PSS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!use_graph) return b->w == 4 ? enqueue<uint32_t>(b, s) : enqueue<u64>(b, s);
+  if (!b->exec) {
+    // Capture on the batch's own stream (the caller's may be the legacy
+    // default stream, which cannot be captured); launches are counted per
+    // replay, not at capture.
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return from_cuda(e);
+    const uint64_t before = launch_count();
+    const int rc = b->w == 4 ? enqueue<uint32_t>(b, b->capture) : enqueue<u64>(b, b->capture);
+    b->graph_launches = launch_count() - before;
+    count_launches(0 - b->graph_launches);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->capture, &g);
+    if (rc != PSS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      return from_cuda(e);
+    }
+  }
+  count_launches(b->graph_launches);
+  return from_cuda(cudaGraphLaunch(b->exec, s));
+}
+
+extern "C" int pss_batch_results(pss_batch* b, pss_entry* host_out, uint32_t* host_counts,
+                                 void* stream) {
+  if (!b || !host_out || !host_counts) return PSS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<uint32_t> nout(2 * (size_t)b->nstreams);
+  std::vector<pss_entry> all(b->total_k);
+  cudaError_t e = cudaMemcpyAsync(all.data(), b->arena + b->results_off, sizeof(pss_entry) * b->total_k,
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(nout.data(), b->arena + b->nout_off, sizeof(uint32_t) * nout.size(),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  int rc = PSS_OK;
+  for (uint32_t i = 0; i < b->nstreams; ++i) {
+    const StreamPlan& sp = b->s[i];
+    host_counts[i] = nout[2 * i];
+    if (nout[2 * i + 1]) rc = PSS_EDEVICE;
+    memcpy(host_out + sp.out_off, all.data() + sp.out_off, sizeof(pss_entry) * nout[2 * i]);
+  }
+  return rc;
+}
+
+extern "C" int pss_batch_export(pss_batch* b, uint32_t index, pss_entry* host_out, uint32_t cap,
+                                uint32_t* size, uint64_t* m, uint64_t* n_covered, void* stream) {
+  if (!b || index >= b->nstreams || !size) return PSS_EINVAL;
+  if (cap > 0 && !host_out) return PSS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const StreamPlan& sp = b->s[index];
+  void* root = b->arena + sp.level_off.back();
+  const uint32_t k = sp.k;
+  void* dmem = nullptr;
+  cudaError_t e = cudaMallocAsync(&dmem, sizeof(pss_entry) * k + 16, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  pss_entry* d_out = (pss_entry*)dmem;
+  uint32_t* d_n = (uint32_t*)((char*)dmem + sizeof(pss_entry) * k);
+  count_launches(1);
+  e = b->w == 4 ? launch_canon<uint32_t>(set_view<uint32_t>(root, 1, k), 0, 0, 1, 0, d_out, d_n, s)
+                : launch_canon<u64>(set_view<u64>(root, 1, k), 0, 0, 1, 0, d_out, d_n, s);
+  uint32_t hn[2] = {0, 0};
+  const SetLayout L = set_layout(1, k, b->w);
+  uint64_t hm = 0, hc = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hn, d_n, sizeof(hn), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, (char*)root + L.m, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, (char*)root + L.ncov, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int rc = from_cuda(e);
+  if (rc == PSS_OK && hn[1]) rc = PSS_EDEVICE;
+  if (rc == PSS_OK && hn[0] > cap) rc = PSS_ERANGE;
+  if (rc == PSS_OK && hn[0]) {
+    e = cudaMemcpyAsync(host_out, d_out, sizeof(pss_entry) * hn[0], cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    rc = from_cuda(e);
+  }
+  cudaFreeAsync(dmem, s);
+  if (rc == PSS_OK) {
+    *size = hn[0];
+    if (m) *m = hm;
+    if (n_covered) *n_covered = hc;
+  }
+  return rc;
+}
+
+extern "C" int pss_batch_info(const pss_batch* b, uint32_t* nstreams, uint64_t* total_items,
+                              uint64_t* total_k, uint32_t* k_classes) {
+  if (!b) return PSS_EINVAL;
+  if (nstreams) *nstreams = b->nstreams;
+  if (total_items) *total_items = b->total_items;
+  if (total_k) *total_k = b->total_k;
+  if (k_classes) *k_classes = (uint32_t)b->kc.size();
+  return PSS_OK;
+}
+
+extern "C" void pss_batch_free(pss_batch* b) { destroy(b); }

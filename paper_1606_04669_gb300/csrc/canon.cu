@@ -51,10 +51,8 @@ __host__ __device__ inline size_t canon_carve(uint32_t k, unsigned char* base, u
 }
 
 template <typename ItemT, int BS>
-__global__ void __launch_bounds__(BS) canon_kernel(SetView<ItemT> in, uint32_t node, u64 n,
-                                                   uint32_t kq, int filter, pss_entry* out,
-                                                   uint32_t* out_n) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ void canon_node(const SetView<ItemT>& in, uint32_t node, u64 n, uint32_t kq, int filter,
+                           pss_entry* out, uint32_t* out_n, unsigned char* smem) {
   u64 *k1, *k2;
   uint16_t* pay;
   uint32_t* wsum;
@@ -103,6 +101,28 @@ __global__ void __launch_bounds__(BS) canon_kernel(SetView<ItemT> in, uint32_t n
   }
 }
 
+template <typename ItemT, int BS>
+__global__ void __launch_bounds__(BS) canon_kernel(SetView<ItemT> in, uint32_t node, u64 n,
+                                                   uint32_t kq, int filter, pss_entry* out,
+                                                   uint32_t* out_n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  canon_node<ItemT, BS>(in, node, n, kq, filter, out, out_n, smem);
+}
+
+// Batch form: CTA d answers the query of descriptor d (its root is node 0 of
+// a one-node set); results at out + out_off, counts at out_n[2 d], status at
+// out_n[2 d + 1].
+template <typename ItemT, int BS>
+__global__ void __launch_bounds__(BS) query_batch_kernel(const QueryDesc* __restrict__ descs,
+                                                         pss_entry* out, uint32_t* out_n,
+                                                         const uint32_t* __restrict__ ids) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t id = ids[blockIdx.x];
+  const QueryDesc d = descs[id];
+  const SetView<ItemT> root = set_view_dev<ItemT>(d.root, 1, d.k);
+  canon_node<ItemT, BS>(root, 0, d.n, d.k, 1, out + d.out_off, out_n + 2 * id, smem);
+}
+
 }  // namespace
 
 template <typename ItemT>
@@ -110,12 +130,28 @@ cudaError_t launch_canon(SetView<ItemT> in, uint32_t node, u64 n, uint32_t kq, i
                          pss_entry* out, uint32_t* out_n, cudaStream_t stream) {
   const size_t smem = canon_carve(in.k, nullptr, nullptr, nullptr, nullptr, nullptr);
   auto kern = canon_kernel<ItemT, CANON_BS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   kern<<<1, CANON_BS, smem, stream>>>(in, node, n, kq, filter, out, out_n);
   return cudaGetLastError();
 }
 
+template <typename ItemT>
+cudaError_t launch_query_batch(const QueryDesc* descs, const uint32_t* ids, uint32_t count,
+                               uint32_t k, pss_entry* out, uint32_t* out_n, cudaStream_t stream) {
+  const size_t smem = canon_carve(k, nullptr, nullptr, nullptr, nullptr, nullptr);
+  auto kern = query_batch_kernel<ItemT, CANON_BS>;
+  cudaError_t e = ensure_kernel_attrs((const void*)kern);
+  if (e != cudaSuccess) return e;
+  if (count == 0) return cudaSuccess;
+  kern<<<count, CANON_BS, smem, stream>>>(descs, out, out_n, ids);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_query_batch<uint32_t>(const QueryDesc*, const uint32_t*, uint32_t,
+                                                  uint32_t, pss_entry*, uint32_t*, cudaStream_t);
+template cudaError_t launch_query_batch<u64>(const QueryDesc*, const uint32_t*, uint32_t, uint32_t,
+                                             pss_entry*, uint32_t*, cudaStream_t);
 template cudaError_t launch_canon<uint32_t>(SetView<uint32_t>, uint32_t, u64, uint32_t, int,
                                             pss_entry*, uint32_t*, cudaStream_t);
 template cudaError_t launch_canon<u64>(SetView<u64>, uint32_t, u64, uint32_t, int, pss_entry*,

@@ -263,6 +263,23 @@ __global__ void __launch_bounds__(BS) merge_pair_kernel(SetView<ItemT> a, uint32
   merge_nodes<ItemT, BS>(a, ia, b, ib, out, 0, smem);
 }
 
+// Batch form: task (d, j) builds node j of the next level of descriptor d.
+template <typename ItemT, int BS>
+__global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __restrict__ descs,
+                                                         const BatchTask* __restrict__ tasks) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BatchTask t = tasks[blockIdx.x];
+  const MergeDesc d = descs[t.stream];
+  const SetView<ItemT> in = set_view_dev<ItemT>(d.in, d.in_nodes, d.k);
+  const SetView<ItemT> out = set_view_dev<ItemT>(d.out, (d.in_nodes + 1) / 2, d.k);
+  const uint32_t j = t.index;
+  if (2 * j + 1 >= d.in_nodes) {
+    copy_node<ItemT, BS>(in, 2 * j, out, j);
+    return;
+  }
+  merge_nodes<ItemT, BS>(in, 2 * j, in, 2 * j + 1, out, j, smem);
+}
+
 template <typename ItemT, int BS>
 __global__ void __launch_bounds__(BS) copy_node_kernel(SetView<ItemT> in, uint32_t ni,
                                                        SetView<ItemT> out, uint32_t no) {
@@ -280,10 +297,7 @@ template <typename ItemT>
 cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream) {
   const size_t smem = merge_smem_bytes<ItemT>(in.k);
   auto kern = merge_level_kernel<ItemT, MERGE_BS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+  cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out);
   return cudaGetLastError();
@@ -294,10 +308,7 @@ cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, u
                               SetView<ItemT> out, cudaStream_t stream) {
   const size_t smem = merge_smem_bytes<ItemT>(out.k);
   auto kern = merge_pair_kernel<ItemT, MERGE_BS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+  cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out);
   return cudaGetLastError();
@@ -310,6 +321,22 @@ cudaError_t launch_copy_node(SetView<ItemT> in, uint32_t node, SetView<ItemT> ou
   return cudaGetLastError();
 }
 
+template <typename ItemT>
+cudaError_t launch_merge_tasks(const MergeDesc* descs, const BatchTask* tasks, uint32_t ntasks,
+                               uint32_t k, cudaStream_t stream) {
+  const size_t smem = merge_smem_bytes<ItemT>(k);
+  auto kern = merge_tasks_kernel<ItemT, MERGE_BS>;
+  cudaError_t e = ensure_kernel_attrs((const void*)kern);
+  if (e != cudaSuccess) return e;
+  if (ntasks == 0) return cudaSuccess;
+  kern<<<ntasks, MERGE_BS, smem, stream>>>(descs, tasks);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_merge_tasks<uint32_t>(const MergeDesc*, const BatchTask*, uint32_t,
+                                                  uint32_t, cudaStream_t);
+template cudaError_t launch_merge_tasks<u64>(const MergeDesc*, const BatchTask*, uint32_t, uint32_t,
+                                             cudaStream_t);
 template size_t merge_smem_bytes<uint32_t>(uint32_t);
 template size_t merge_smem_bytes<u64>(uint32_t);
 template cudaError_t launch_merge_level<uint32_t>(SetView<uint32_t>, SetView<uint32_t>, cudaStream_t);

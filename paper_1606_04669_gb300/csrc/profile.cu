@@ -41,8 +41,12 @@ cudaEvent_t get_event() {
 
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 ProfScope::ProfScope(int cat, cudaStream_t s, uint64_t units) : cat_(cat), s_(s), units_(units) {
   if (!g_enabled.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   std::lock_guard<std::mutex> lock(g_mu);
   start_ = get_event();
   end_ = get_event();

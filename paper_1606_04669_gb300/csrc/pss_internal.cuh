@@ -73,6 +73,55 @@ inline SetView<ItemT> set_view(void* base, uint32_t nodes, uint32_t k) {
   return v;
 }
 
+// Device-side view of a set allocation (same layout as set_layout).
+template <typename ItemT>
+__device__ __forceinline__ SetView<ItemT> set_view_dev(void* base, uint32_t nodes, uint32_t k) {
+  const size_t e = (size_t)nodes * k;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  char* b = (char*)base;
+  size_t off = 0;
+  SetView<ItemT> v;
+  v.item = (ItemT*)(b + off);    off = up(off + e * sizeof(ItemT));
+  v.count = (u64*)(b + off);     off = up(off + e * 8);
+  v.err = (u64*)(b + off);       off = up(off + e * 8);
+  v.size = (uint32_t*)(b + off); off = up(off + (size_t)nodes * 4);
+  v.m = (u64*)(b + off);         off = up(off + (size_t)nodes * 8);
+  v.ncov = (u64*)(b + off);      off = up(off + (size_t)nodes * 8);
+  v.status = (uint32_t*)(b + off);
+  v.nodes = nodes;
+  v.k = k;
+  return v;
+}
+
+// One stream of a batch (device-resident descriptor).
+struct BatchStream {
+  const void* items;  // device items of the stream
+  u64 n;              // its length
+  uint32_t p, k;      // blocks and counters
+  void* level0;       // set of p block summaries (set_layout(p, k, w))
+};
+
+// One unit of work of a batch: block `index` of stream `stream`, or (merge)
+// node `index` of the next level of stream `stream`.
+struct BatchTask {
+  uint32_t stream, index;
+};
+
+// One stream's step of the reduction tree in a batch: level `in` (in_nodes
+// summaries) into level `out` (ceil(in_nodes / 2) summaries).
+struct MergeDesc {
+  void* in;
+  void* out;
+  uint32_t in_nodes, k;
+};
+
+// One stream's query in a batch: Pruned(root, n, kq) written at out_off.
+struct QueryDesc {
+  void* root;
+  u64 n;
+  uint32_t k, out_off;
+};
+
 // floor(r * n / p) without overflow (r <= p, p < 2^32): 128-bit product,
 // long division by 32-bit digits.  Algorithm 1's block bound.
 __host__ __device__ inline u64 block_bound(u64 r, u64 n, uint32_t p) {

@@ -1,9 +1,39 @@
 // pss_kernels.cuh — launch entry points of the device kernels (host side).
 #pragma once
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "pss_internal.cuh"
 
 namespace pss {
+
+// Allow a kernel the device's largest opt-in shared memory and prefer shared
+// memory over L1, once per kernel (keyed by its address; instantiations with
+// the same signature are different kernels), so that later launches, and
+// stream captures, do not set attributes.
+inline cudaError_t ensure_kernel_attrs(const void* kern) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, cudaError_t>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& kd : done)
+    if (kd.first == kern) return kd.second;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  // dynamic + static shared memory may not exceed the opt-in limit
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  done.push_back({kern, e});
+  return e;
+}
 
 constexpr int SS_BS = 256;     // threads per CTA of the summarize kernel
 constexpr int SS_IPT = 4;      // items per thread per window (window = SS_BS * SS_IPT)
@@ -44,6 +74,26 @@ template <typename ItemT>
 cudaError_t launch_copy_node(SetView<ItemT> in, uint32_t node, SetView<ItemT> out,
                              uint32_t out_node, cudaStream_t stream);
 
+// Batch forms (batch.cu).  Persistent block summaries over a task list.
+template <typename ItemT>
+cudaError_t launch_summarize_batch(const BatchStream* streams, const BatchTask* tasks,
+                                   uint32_t ntasks, uint32_t* counter, uint32_t k, uint32_t grid,
+                                   cudaStream_t stream);
+
+// Resident summarize CTAs per SM for k counters (0 if it cannot run).
+template <typename ItemT>
+int summarize_ctas_per_sm(uint32_t k);
+
+// One CTA per task: node task.index of the next level of descriptor task.stream.
+template <typename ItemT>
+cudaError_t launch_merge_tasks(const MergeDesc* descs, const BatchTask* tasks, uint32_t ntasks,
+                               uint32_t k, cudaStream_t stream);
+
+// One CTA per id: the query of descs[ids[i]].
+template <typename ItemT>
+cudaError_t launch_query_batch(const QueryDesc* descs, const uint32_t* ids, uint32_t count,
+                               uint32_t k, pss_entry* out, uint32_t* out_n, cudaStream_t stream);
+
 // Kernel-group timing (profile.cu): categories of ProfScope.
 enum ProfCat : int { PROF_SUMMARIZE = 0, PROF_MERGE = 1, PROF_QUERY = 2 };
 
@@ -64,8 +114,9 @@ class ProfScope {
   bool active_ = false;
 };
 
-// Adds n to the library's launch counter.
+// Adds n (modulo 2^64) to the library's launch counter; launch_count reads it.
 void count_launches(uint64_t n);
+uint64_t launch_count();
 
 cudaError_t launch_gen_zipf(void* out, u64 count, int item_bytes, u64 seed, uint32_t stream_id,
                             u64 start, double s, int log2u, cudaStream_t stream);

@@ -393,13 +393,13 @@ struct SSBlock {
   }
 };
 
+// The summary of block r of p (Algorithm 1 bounds over n items) into node
+// `node` of `out`; called by all threads of the CTA.
 template <typename ItemT, int BS, int IPT>
-__global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ items, u64 n,
-                                                      uint32_t p, uint32_t r0,
-                                                      SetView<ItemT> out, uint32_t node0) {
+__device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t p, uint32_t r,
+                                const SetView<ItemT>& out, uint32_t node, unsigned char* smem,
+                                SSState& S_) {
   constexpr uint32_t W = BS * IPT;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ SSState S_;
   SSBlock<ItemT, BS, IPT> B;
   B.k = out.k;
   B.S = &S_;
@@ -409,8 +409,6 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
   auto& s = B.s;
   const uint32_t k = B.k;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t r = r0 + blockIdx.x;
-  const uint32_t node = node0 + blockIdx.x;
   const u64 left = block_bound(r, n, p), right = block_bound((u64)r + 1, n, p);
   const size_t obase = (size_t)node * k;
   if (right - left >= (1ull << 32)) {
@@ -869,6 +867,40 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
   }
 }
 
+template <typename ItemT, int BS, int IPT>
+__global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ items, u64 n,
+                                                      uint32_t p, uint32_t r0,
+                                                      SetView<ItemT> out, uint32_t node0) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SSState S;
+  summarize_block<ItemT, BS, IPT>(items, n, p, r0 + blockIdx.x, out, node0 + blockIdx.x, smem, S);
+}
+
+// Persistent form for many streams: each CTA takes (stream, block) tasks from
+// a shared counter until the list is exhausted.  Tasks are listed longest
+// block first so that the last wave is short.
+template <typename ItemT, int BS, int IPT>
+__global__ void __launch_bounds__(BS) ss_batch_kernel(const BatchStream* __restrict__ streams,
+                                                      const BatchTask* __restrict__ tasks,
+                                                      uint32_t ntasks, uint32_t* counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SSState S;
+  __shared__ uint32_t next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t t = next;
+    __syncthreads();
+    if (t >= ntasks) break;
+    const BatchTask task = tasks[t];
+    const BatchStream st = streams[task.stream];
+    const SetView<ItemT> out = set_view_dev<ItemT>(st.level0, st.p, st.k);
+    summarize_block<ItemT, BS, IPT>((const ItemT*)st.items, st.n, st.p, task.index, out,
+                                    task.index, smem, S);
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 template <typename ItemT>
@@ -882,16 +914,43 @@ cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint3
                                     cudaStream_t stream) {
   const size_t smem = ss_smem_bytes<ItemT>(out.k);
   auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+  cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   if (count == 0) return cudaSuccess;
   kern<<<count, SS_BS, smem, stream>>>(items, n, p, r0, out, node0);
   return cudaGetLastError();
 }
 
+template <typename ItemT>
+cudaError_t launch_summarize_batch(const BatchStream* streams, const BatchTask* tasks,
+                                   uint32_t ntasks, uint32_t* counter, uint32_t k, uint32_t grid,
+                                   cudaStream_t stream) {
+  const size_t smem = ss_smem_bytes<ItemT>(k);
+  auto kern = ss_batch_kernel<ItemT, SS_BS, SS_IPT>;
+  cudaError_t e = ensure_kernel_attrs((const void*)kern);
+  if (e != cudaSuccess) return e;
+  if (ntasks == 0 || grid == 0) return cudaSuccess;
+  kern<<<grid, SS_BS, smem, stream>>>(streams, tasks, ntasks, counter);
+  return cudaGetLastError();
+}
+
+template <typename ItemT>
+int summarize_ctas_per_sm(uint32_t k) {
+  const size_t smem = ss_smem_bytes<ItemT>(k);
+  auto kern = ss_batch_kernel<ItemT, SS_BS, SS_IPT>;
+  if (ensure_kernel_attrs((const void*)kern) != cudaSuccess) return 0;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, SS_BS, smem) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+template cudaError_t launch_summarize_batch<uint32_t>(const BatchStream*, const BatchTask*, uint32_t,
+                                                      uint32_t*, uint32_t, uint32_t, cudaStream_t);
+template cudaError_t launch_summarize_batch<u64>(const BatchStream*, const BatchTask*, uint32_t,
+                                                 uint32_t*, uint32_t, uint32_t, cudaStream_t);
+template int summarize_ctas_per_sm<uint32_t>(uint32_t);
+template int summarize_ctas_per_sm<u64>(uint32_t);
 template size_t ss_smem_bytes<uint32_t>(uint32_t);
 template size_t ss_smem_bytes<u64>(uint32_t);
 template cudaError_t launch_summarize_blocks<uint32_t>(const uint32_t*, u64, uint32_t, uint32_t,

@@ -53,6 +53,13 @@ class Entry(ctypes.Structure):
     _fields_ = [("item", ctypes.c_uint64), ("count", ctypes.c_uint64), ("err", ctypes.c_uint64)]
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("nstreams", ctypes.c_uint32), ("item_bytes", ctypes.c_int),
+                ("d_items", ctypes.POINTER(ctypes.c_void_p)), ("n", ctypes.POINTER(ctypes.c_uint64)),
+                ("k", ctypes.POINTER(ctypes.c_uint32)), ("p", ctypes.POINTER(ctypes.c_uint32)),
+                ("skew_hint", ctypes.POINTER(ctypes.c_double))]
+
+
 # Every function of include/pss.h: name -> (restype, argtypes).
 SIGNATURES = {
     "pss_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -72,6 +79,14 @@ SIGNATURES = {
     "pss_export": (ctypes.c_int, [vp, ctypes.POINTER(Entry), u32, u32p, u64p, u64p, vp]),
     "pss_summary_info": (ctypes.c_int, [vp, u32p, ctypes.POINTER(ctypes.c_int)]),
     "pss_free": (None, [vp]),
+    "pss_plan_blocks": (ctypes.c_uint32, [u64, u32, ctypes.c_int, ctypes.c_double]),
+    "pss_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp, ctypes.POINTER(vp)]),
+    "pss_batch_plan": (ctypes.c_int, [vp, u32p]),
+    "pss_batch_info": (ctypes.c_int, [vp, u32p, u64p, u64p, u32p]),
+    "pss_batch_run": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+    "pss_batch_results": (ctypes.c_int, [vp, ctypes.POINTER(Entry), u32p, vp]),
+    "pss_batch_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p, u64p, vp]),
+    "pss_batch_free": (None, [vp]),
     "pss_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
     "pss_gen_zipf": (ctypes.c_int, [vp, u64, ctypes.c_int, u64, u32, u64, ctypes.c_double,
@@ -327,3 +342,85 @@ def profile_read(reset: bool = False) -> dict:
     p = Profile()
     _check(load().pss_profile_read(ctypes.byref(p), 1 if reset else 0), "pss_profile_read")
     return {name: getattr(p, name) for name, _ in Profile._fields_}
+
+
+def plan_blocks(n: int, k: int, item_bytes: int = 4, skew_hint: float = 0.0) -> int:
+    """The library's default block count for a stream (pss_plan_blocks)."""
+    return int(load().pss_plan_blocks(int(n), int(k), int(item_bytes), float(skew_hint)))
+
+
+class Batch:
+    """Many independent streams summarized in one launch graph (pss_batch_*).
+
+    items: CUDA tensors of one item width (borrowed for the batch's life);
+    ks: counters per stream; ps: blocks per stream (None / 0 = planned)."""
+
+    def __init__(self, items, ks, ps=None, skews=None, stream=None):
+        if not items:
+            raise ValueError("a batch needs at least one stream")
+        widths = {_check_items(t) for t in items}
+        if len(widths) != 1:
+            raise ValueError("every stream of a batch must have the same item width")
+        self._items = list(items)
+        ns = len(items)
+        self.item_bytes = widths.pop()
+        self._ptrs = (ctypes.c_void_p * ns)(*[t.data_ptr() for t in items])
+        self._n = (ctypes.c_uint64 * ns)(*[t.numel() for t in items])
+        self._k = (ctypes.c_uint32 * ns)(*[int(k) for k in ks])
+        self._p = (ctypes.c_uint32 * ns)(*[int(p or 0) for p in (ps or [0] * ns)])
+        self._skew = (ctypes.c_double * ns)(*[float(x or 0.0) for x in (skews or [0.0] * ns)])
+        d = BatchDesc(ns, self.item_bytes, self._ptrs, self._n, self._k, self._p, self._skew)
+        h = vp()
+        _check(load().pss_batch_create(ctypes.byref(d), vp(_stream_handle(stream)), ctypes.byref(h)),
+               "pss_batch_create")
+        self._h = h
+        self.nstreams = ns
+        self.ks = [int(k) for k in ks]
+
+    def plan(self) -> list[int]:
+        out = (ctypes.c_uint32 * self.nstreams)()
+        _check(load().pss_batch_plan(self._h, out), "pss_batch_plan")
+        return list(out)
+
+    def run(self, use_graph: bool = True, stream=None):
+        _check(load().pss_batch_run(self._h, 1 if use_graph else 0, vp(_stream_handle(stream))),
+               "pss_batch_run")
+
+    def results(self, stream=None) -> list[Exported]:
+        total = sum(self.ks)
+        buf = (Entry * total)()
+        counts = (ctypes.c_uint32 * self.nstreams)()
+        _check(load().pss_batch_results(self._h, buf, counts, vp(_stream_handle(stream))),
+               "pss_batch_results")
+        raw = np.frombuffer(memoryview(buf), dtype=np.uint64).reshape(total, 3)
+        out, off = [], 0
+        for i in range(self.nstreams):
+            c = int(counts[i])
+            r = raw[off:off + c]
+            out.append(Exported(r[:, 0].copy(), r[:, 1].copy(), r[:, 2].copy(), 0,
+                                int(self._n[i])))
+            off += self.ks[i]
+        return out
+
+    def export(self, index: int, stream=None) -> Exported:
+        k = self.ks[index]
+        buf = (Entry * k)()
+        size = u32()
+        m = u64()
+        cov = u64()
+        _check(load().pss_batch_export(self._h, int(index), buf, k, ctypes.byref(size),
+                                       ctypes.byref(m), ctypes.byref(cov),
+                                       vp(_stream_handle(stream))), "pss_batch_export")
+        it, ct, er = _entries_to_arrays(buf, size.value)
+        return Exported(it, ct, er, int(m.value), int(cov.value))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().pss_batch_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

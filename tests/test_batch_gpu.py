@@ -1,0 +1,79 @@
+"""Batched form (pss_batch_*): every stream's result equals the plain path
+with the same k and p, and the oracle's on streams small enough to replay."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1606_04669_gb300.gen import workloads as W
+from tests._helpers import summary_entries
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1606_04669_gb300 as P  # noqa: E402
+
+
+def ents(e):
+    return list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist()))
+
+
+def make_streams(width, seed):
+    rng = np.random.default_rng(seed)
+    lens = [0, 7, 999, 50_000, 123_457, 300_000, 700_001, 2_000_000]
+    ks = [2, 64, 256, 1024, 4096, 300]
+    specs = []
+    for i in range(22):
+        specs.append(dict(n=int(lens[i % len(lens)]), k=int(ks[(3 * i) % len(ks)]),
+                          s=float(0.8 + 1.2 * rng.random()), stream=i))
+    items = [P.gen_zipf(sp["n"], seed=seed, s=sp["s"], log2u=32, item_bytes=width,
+                        stream_id=sp["stream"]) for sp in specs]
+    return specs, items
+
+
+@pytest.mark.parametrize("width", [8, 4])
+def test_batch_equals_plain_and_oracle(width):
+    specs, items = make_streams(width, 3 if width == 8 else 5)
+    batch = P.Batch(items, [sp["k"] for sp in specs])
+    plan = batch.plan()
+    assert plan == [P.plan_blocks(sp["n"], sp["k"], width) for sp in specs]
+    batch.run(use_graph=False)
+    res = batch.results()
+    for i, sp in enumerate(specs):
+        plain = P.summarize(items[i], sp["k"], plan[i])
+        q = plain.query(sp["n"], sp["k"])
+        assert ents(res[i]) == ents(q), i
+        e = batch.export(i)
+        pe = plain.export()
+        assert ents(e) == ents(pe) and (e.m, e.n_covered) == (pe.m, pe.n_covered), i
+        if sp["n"] <= 300_000:
+            x = oracle.gen_zipf(sp["n"], seed=3 if width == 8 else 5, s=sp["s"], log2u=32,
+                                width=width, stream=sp["stream"])
+            root, rq = oracle.parallel_space_saving(x, sp["k"], plan[i])
+            assert ents(e) == summary_entries(root) and e.m == root.m, i
+            assert ents(res[i]) == summary_entries(rq), i
+    # the graph form, replayed twice, gives the same results
+    for _ in range(2):
+        batch.run(use_graph=True)
+        res2 = batch.results()
+        assert all(ents(a) == ents(b) for a, b in zip(res, res2))
+    batch.close()
+
+
+def test_batch_explicit_plan_and_workload_params():
+    specs = W.batched_streams(seed=3, nstreams=16, lo=1e3, hi=3e5)
+    items = [P.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, item_bytes=sp.item_bytes,
+                        stream_id=sp.index) for sp in specs]
+    ps = [1 + (i % 5) for i in range(len(specs))]
+    batch = P.Batch(items, [sp.k for sp in specs], ps=ps)
+    assert batch.plan() == ps
+    batch.run(use_graph=True)
+    res = batch.results()
+    for i, sp in enumerate(specs):
+        x = oracle.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, width=8, stream=sp.index)
+        root, rq = oracle.parallel_space_saving(x, sp.k, ps[i])
+        assert ents(res[i]) == summary_entries(rq), i
