@@ -258,6 +258,83 @@ int pss_summary_info(const pss_summary* summary, uint32_t* k, int* item_bytes);
 void pss_free(pss_summary* summary);
 
 /*
+ * Served form: a request loop with continuous batching.  Each request is a
+ * segment of one tenant's stream; the server keeps every tenant's summary
+ * resident on the device and merges each new segment into it with combine
+ * (Algorithm 2), strictly in arrival order per tenant, then answers two
+ * queries (Algorithm 1, Pruned): the segment's own and the tenant's running
+ * one.  Requests are released at their scheduled arrival times (open loop);
+ * a scheduler thread admits them while the device-memory budget and the
+ * per-tick limit allow, so requests that arrive while others are on the GPU
+ * join the next tick, and ticks overlap on the device (segment work on
+ * alternating streams, tenant merges in order on one stream).  Results are
+ * independent of the mix: a request's results equal those of running its
+ * tenant's requests alone, in order.
+ */
+typedef struct pss_server pss_server;
+
+typedef struct {
+  uint32_t tenants;        /* tenant summaries kept resident */
+  uint32_t k;              /* counters of every segment and tenant summary */
+  uint64_t budget_bytes;   /* device memory admitted requests may hold at once */
+  uint32_t max_batch;      /* requests admitted per scheduling tick */
+  uint32_t max_inflight;   /* admitted, not yet completed requests (host result slots) */
+} pss_server_config;
+
+typedef struct {
+  uint64_t id;             /* caller's request id (unique) */
+  double arrival;          /* scheduled arrival, seconds after pss_server_start */
+  uint32_t tenant;         /* < tenants */
+  uint64_t n;              /* segment length (items) */
+  const void* d_items;     /* segment items (uint32, device); NULL: generate them */
+  double s;                /* generated segments: Zipf skew, universe 2^log2u */
+  int log2u;
+  uint64_t seed;           /* generated segments: seed and stream id */
+  uint32_t stream_id;
+  uint32_t p;              /* blocks for the segment; 0 = pss_plan_blocks */
+} pss_request;
+
+typedef struct {
+  uint64_t id;
+  uint32_t tenant;
+  uint32_t p;              /* blocks used for the segment */
+  double arrival, admitted, completed;  /* seconds after start */
+  uint32_t n_segment;      /* entries of the segment query */
+  uint32_t n_tenant;       /* entries of the tenant query */
+  uint64_t tenant_items;   /* items merged into the tenant, this segment included */
+  int status;              /* PSS_OK or an error code */
+} pss_completion;
+
+int pss_server_create(const pss_server_config* config, pss_server** out);
+
+/* Queue requests (any order; each is released at its arrival time).  May be
+ * called before or after pss_server_start. */
+int pss_server_submit(pss_server* server, const pss_request* requests, uint32_t count);
+
+/* Start the clock and the scheduler thread. */
+int pss_server_start(pss_server* server);
+
+/* Wait until every submitted request has completed (timeout in seconds;
+ * PSS_ETIMEOUT if it expires). */
+int pss_server_wait(pss_server* server, double timeout_s);
+
+/* Drain up to cap completions (in completion order). */
+int pss_server_poll(pss_server* server, pss_completion* out, uint32_t cap, uint32_t* n_out);
+
+/* The two query results of a completed request (count desc, item asc);
+ * each array holds k entries.  The result is released once read. */
+int pss_server_result(pss_server* server, uint64_t id, pss_entry* segment_out, uint32_t* n_segment,
+                      pss_entry* tenant_out, uint32_t* n_tenant);
+
+/* Canonical export of a tenant's resident summary (waits for the server's
+ * tenant work enqueued so far). */
+int pss_server_tenant_export(pss_server* server, uint32_t tenant, pss_entry* host_out, uint32_t cap,
+                             uint32_t* size, uint64_t* m, uint64_t* n_covered);
+
+/* Stop the scheduler (after the current tick) and release everything. */
+void pss_server_destroy(pss_server* server);
+
+/*
  * Profiling.  The paper reports run time and the "fractional overhead" of
  * the reduction relative to the computation (Section 4.1); the library can
  * time its own kernel groups with CUDA events on the launching stream.

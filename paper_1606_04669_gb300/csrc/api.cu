@@ -281,6 +281,23 @@ int canon_out(void* set_mem, uint32_t nodes, uint32_t node, uint32_t k, int w, u
 
 }  // namespace
 
+namespace pss {
+
+// The root set (one node) of the path over d_items, allocated stream-ordered
+// on s (release with cudaFreeAsync); used by the serving runtime.
+int summarize_to_set(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p,
+                     cudaStream_t s, void** root) {
+  std::vector<void*> mems;
+  std::vector<uint32_t> nodes;
+  *root = nullptr;
+  int rc = tree_common(d_items, n, w, k, p, s, false, mems, nodes);
+  if (rc) return rc;
+  *root = mems.back();
+  return PSS_OK;
+}
+
+}  // namespace pss
+
 extern "C" {
 
 const char* pss_strerror(int code) {

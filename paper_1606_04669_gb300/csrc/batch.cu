@@ -469,3 +469,14 @@ extern "C" int pss_batch_info(const pss_batch* b, uint32_t* nstreams, uint64_t* 
 }
 
 extern "C" void pss_batch_free(pss_batch* b) { destroy(b); }
+
+namespace pss {
+
+void* batch_root(pss_batch* b, uint32_t i) { return b->arena + b->s[i].level_off.back(); }
+
+void batch_query_device(pss_batch* b, uint32_t i, pss_entry** entries, uint32_t** counts) {
+  *entries = (pss_entry*)(b->arena + b->results_off) + b->s[i].out_off;
+  *counts = (uint32_t*)(b->arena + b->nout_off) + 2 * i;
+}
+
+}  // namespace pss

@@ -94,6 +94,15 @@ template <typename ItemT>
 cudaError_t launch_query_batch(const QueryDesc* descs, const uint32_t* ids, uint32_t count,
                                uint32_t k, pss_entry* out, uint32_t* out_n, cudaStream_t stream);
 
+// Host-side: the root set of the whole path (api.cu), stream-ordered on s.
+int summarize_to_set(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p,
+                     cudaStream_t s, void** root);
+
+// Host-side accessors of a batch (batch.cu): stream i's root set (one node),
+// and its query result (entries, then {count, status}) on the device.
+void* batch_root(pss_batch* b, uint32_t i);
+void batch_query_device(pss_batch* b, uint32_t i, pss_entry** entries, uint32_t** counts);
+
 // Kernel-group timing (profile.cu): categories of ProfScope.
 enum ProfCat : int { PROF_SUMMARIZE = 0, PROF_MERGE = 1, PROF_QUERY = 2 };
 

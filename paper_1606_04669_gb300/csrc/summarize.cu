@@ -264,6 +264,20 @@ struct SSBlock {
     status |= ST_PROBE;
   }
 
+  // One occurrence at position t for counter tgt (NONE32: none); lanes of the
+  // warp with the same counter add theirs with one atomic (frequent items
+  // would otherwise serialize on their counter).  All lanes call it.
+  __device__ __forceinline__ void add_occurrence(uint32_t tgt, uint32_t t) {
+    const unsigned grp = __match_any_sync(0xffffffffu, tgt);
+    if (tgt != NONE32) {
+      const uint32_t mx = __reduce_max_sync(grp, t);
+      if ((threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1)) {
+        atomicAdd(&s.cnt[tgt], (uint32_t)__popc(grp));
+        atomicMax(&s.touch[tgt], mx);
+      }
+    }
+  }
+
   __device__ __forceinline__ uint32_t wtab_insert(ItemT x, uint32_t rel) {
     uint32_t c;
     if (x == ItemOps<ItemT>::SENT) {
@@ -508,7 +522,19 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
         }
       }
     }
-    __syncthreads();
+    // Hits on counters outside the minimum bucket commute with everything:
+    // a window of those only just adds its occurrences.
+    if (!__syncthreads_or((miss | mhit) != 0)) {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t rel = tid * IPT + j;
+        B.add_occurrence(rel < nact ? (uint32_t)sl[j] : NONE32, t0 + rel);
+      }
+      __syncthreads();
+      t0 += nact;
+      if (nact < W) have_next = false;
+      continue;
+    }
 
     // ---- P2: first occurrences of the misses, ranked by position
     uint32_t first = 0, nf = 0;
@@ -749,20 +775,20 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const uint32_t rel = tid * IPT + j;
-      if (rel >= cut) continue;
-      uint32_t tgt;
-      if (miss >> j & 1) {
-        tgt = s.wslot[wc[j]];
-      } else {
-        tgt = (uint32_t)sl[j];
-        if (mhit >> j & 1) {
-          const uint32_t f = s.fate[tgt];
-          if (f) tgt = f - 1;  // the member was evicted: its item was re-inserted
-          else if (s.hfirst[tgt] == rel) s.logpos[rel] = (uint16_t)(tgt + 1);  // m -> m + 1
+      uint32_t tgt = NONE32;
+      if (rel < cut) {
+        if (miss >> j & 1) {
+          tgt = s.wslot[wc[j]];
+        } else {
+          tgt = (uint32_t)sl[j];
+          if (mhit >> j & 1) {
+            const uint32_t f = s.fate[tgt];
+            if (f) tgt = f - 1;  // the member was evicted: its item was re-inserted
+            else if (s.hfirst[tgt] == rel) s.logpos[rel] = (uint16_t)(tgt + 1);  // m -> m + 1
+          }
         }
       }
-      atomicAdd(&s.cnt[tgt], 1u);
-      atomicMax(&s.touch[tgt], t0 + rel);
+      B.add_occurrence(tgt, t0 + rel);
     }
     __syncthreads();
 

@@ -14,8 +14,8 @@
  *   - Zipf_{s,U}: P(rank = r) proportional to r^-s for r in [1, U], drawn by
  *     rejection-inversion (W. Hormann and G. Derflinger, "Rejection-inversion
  *     to generate variates from monotone discrete distributions", ACM TOMACS
- *     6(3), 1996).  Attempt a of item i consumes one uniform from the
- *     counter-based generator below.
+ *     6(3), 1996), with its quick-acceptance bound.  Attempt a of item i
+ *     consumes one uniform from the counter-based generator below.
  *   - Uniforms: Philox4x32-10 (J. Salmon, M. Moraes, R. Dror, D. Shaw,
  *     "Parallel random numbers: as easy as 1, 2, 3", SC 2011), key =
  *     (seed low word, seed high word), counter = (i low word, i high word,
@@ -26,15 +26,17 @@
  *     scattered over the universe instead of being 0, 1, 2, ...
  *
  * Bit-exact reproducibility: all floating point is IEEE double with
- * operations +, -, *, / only (each correctly rounded), and never contracted
- * into fused multiply-adds: device code goes through the __d*_rn intrinsics,
- * host code must be compiled with -ffp-contract=off.  log and exp are this
+ * operations +, -, *, / and explicit fused multiply-add (each correctly
+ * rounded), and nothing else is contracted: device code goes through the
+ * __d*_rn / __fma_rn intrinsics, host code uses C's fma and must be compiled
+ * with -ffp-contract=off.  log and exp are this
  * file's own (range reduction plus series from the mathematics), so that no
  * platform libm enters the result.
  */
 #ifndef PSS_ZIPF_H_
 #define PSS_ZIPF_H_
 
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -48,11 +50,13 @@
 #endif
 
 #if defined(__CUDA_ARCH__)
+#define PSSG_FMA(a, b, c) __fma_rn((a), (b), (c))
 #define PSSG_MUL(a, b) __dmul_rn((a), (b))
 #define PSSG_ADD(a, b) __dadd_rn((a), (b))
 #define PSSG_SUB(a, b) __dsub_rn((a), (b))
 #define PSSG_DIV(a, b) __ddiv_rn((a), (b))
 #else
+#define PSSG_FMA(a, b, c) fma((a), (b), (c))
 #define PSSG_MUL(a, b) ((a) * (b))
 #define PSSG_ADD(a, b) ((a) + (b))
 #define PSSG_SUB(a, b) ((a) - (b))
@@ -106,7 +110,8 @@ PSSG_FN double pssg_pow2(int e) { return pssg_from_bits((uint64_t)(e + 1023) << 
 #define PSSG_SQRT2 0x1.6a09e667f3bcdp+0
 
 /* Natural log for positive normal x: x = 2^e f with f in (sqrt(1/2), sqrt 2],
- * log f = 2 atanh(z), z = (f-1)/(f+1), |z| < 0.172, atanh series to z^25. */
+ * log f = 2 atanh(z), z = (f-1)/(f+1), |z| < 0.172, atanh series to z^21
+ * (the next term is below 1e-18 relative). */
 PSSG_FN double pssg_log(double x) {
   uint64_t b = pssg_bits(x);
   int e = (int)((b >> 52) & 0x7FF) - 1023;
@@ -114,48 +119,42 @@ PSSG_FN double pssg_log(double x) {
   if (f > PSSG_SQRT2) { f = PSSG_MUL(f, 0.5); e += 1; }
   double z = PSSG_DIV(PSSG_SUB(f, 1.0), PSSG_ADD(f, 1.0));
   double z2 = PSSG_MUL(z, z);
-  double q = 1.0 / 25.0;
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 23.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 21.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 19.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 17.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 15.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 13.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 11.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 9.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 7.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 5.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0 / 3.0);
-  q = PSSG_ADD(PSSG_MUL(q, z2), 1.0);
+  double q = 1.0 / 21.0;
+  q = PSSG_FMA(q, z2, 1.0 / 19.0);
+  q = PSSG_FMA(q, z2, 1.0 / 17.0);
+  q = PSSG_FMA(q, z2, 1.0 / 15.0);
+  q = PSSG_FMA(q, z2, 1.0 / 13.0);
+  q = PSSG_FMA(q, z2, 1.0 / 11.0);
+  q = PSSG_FMA(q, z2, 1.0 / 9.0);
+  q = PSSG_FMA(q, z2, 1.0 / 7.0);
+  q = PSSG_FMA(q, z2, 1.0 / 5.0);
+  q = PSSG_FMA(q, z2, 1.0 / 3.0);
+  q = PSSG_FMA(q, z2, 1.0);
   double lf = PSSG_MUL(PSSG_MUL(2.0, z), q);
   double de = (double)e;
-  return PSSG_ADD(PSSG_MUL(de, PSSG_LN2_HI), PSSG_ADD(PSSG_MUL(de, PSSG_LN2_LO), lf));
+  return PSSG_FMA(de, PSSG_LN2_HI, PSSG_ADD(PSSG_MUL(de, PSSG_LN2_LO), lf));
 }
 
 /* exp(x) for |x| < 700: x = n ln2 + r, |r| <= ln2/2, Taylor series of e^r to
- * r^18/18! (truncation below 1e-19 relative), then scale by 2^n. */
+ * r^14/14! (truncation below 4e-18 relative), then scale by 2^n. */
 PSSG_FN double pssg_exp(double x) {
-  double nd = pssg_floor(PSSG_ADD(PSSG_MUL(x, PSSG_INV_LN2), 0.5));
+  double nd = pssg_floor(PSSG_FMA(x, PSSG_INV_LN2, 0.5));
   double r = PSSG_SUB(PSSG_SUB(x, PSSG_MUL(nd, PSSG_LN2_HI)), PSSG_MUL(nd, PSSG_LN2_LO));
-  double p = 1.0 / 6402373705728000.0; /* 1/18! */
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 355687428096000.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 20922789888000.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 1307674368000.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 87178291200.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 6227020800.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 479001600.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 39916800.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 3628800.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 362880.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 40320.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 5040.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 720.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 120.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 24.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0 / 6.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 0.5);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0);
-  p = PSSG_ADD(PSSG_MUL(p, r), 1.0);
+  double p = 1.0 / 87178291200.0; /* 1/14! */
+  p = PSSG_FMA(p, r, 1.0 / 6227020800.0);
+  p = PSSG_FMA(p, r, 1.0 / 479001600.0);
+  p = PSSG_FMA(p, r, 1.0 / 39916800.0);
+  p = PSSG_FMA(p, r, 1.0 / 3628800.0);
+  p = PSSG_FMA(p, r, 1.0 / 362880.0);
+  p = PSSG_FMA(p, r, 1.0 / 40320.0);
+  p = PSSG_FMA(p, r, 1.0 / 5040.0);
+  p = PSSG_FMA(p, r, 1.0 / 720.0);
+  p = PSSG_FMA(p, r, 1.0 / 120.0);
+  p = PSSG_FMA(p, r, 1.0 / 24.0);
+  p = PSSG_FMA(p, r, 1.0 / 6.0);
+  p = PSSG_FMA(p, r, 0.5);
+  p = PSSG_FMA(p, r, 1.0);
+  p = PSSG_FMA(p, r, 1.0);
   return PSSG_MUL(p, pssg_pow2((int)nd));
 }
 
@@ -164,25 +163,25 @@ PSSG_FN double pssg_expm1_over(double t) {
   if (t > -0.5 && t < 0.5) {
     /* sum_{j>=0} t^j / (j+1)!, to t^19/20! */
     double p = 1.0 / 2432902008176640000.0; /* 1/20! */
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 121645100408832000.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 6402373705728000.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 355687428096000.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 20922789888000.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 1307674368000.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 87178291200.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 6227020800.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 479001600.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 39916800.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 3628800.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 362880.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 40320.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 5040.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 720.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 120.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 24.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 6.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 0.5);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0);
+    p = PSSG_FMA(p, t, 1.0 / 121645100408832000.0);
+    p = PSSG_FMA(p, t, 1.0 / 6402373705728000.0);
+    p = PSSG_FMA(p, t, 1.0 / 355687428096000.0);
+    p = PSSG_FMA(p, t, 1.0 / 20922789888000.0);
+    p = PSSG_FMA(p, t, 1.0 / 1307674368000.0);
+    p = PSSG_FMA(p, t, 1.0 / 87178291200.0);
+    p = PSSG_FMA(p, t, 1.0 / 6227020800.0);
+    p = PSSG_FMA(p, t, 1.0 / 479001600.0);
+    p = PSSG_FMA(p, t, 1.0 / 39916800.0);
+    p = PSSG_FMA(p, t, 1.0 / 3628800.0);
+    p = PSSG_FMA(p, t, 1.0 / 362880.0);
+    p = PSSG_FMA(p, t, 1.0 / 40320.0);
+    p = PSSG_FMA(p, t, 1.0 / 5040.0);
+    p = PSSG_FMA(p, t, 1.0 / 720.0);
+    p = PSSG_FMA(p, t, 1.0 / 120.0);
+    p = PSSG_FMA(p, t, 1.0 / 24.0);
+    p = PSSG_FMA(p, t, 1.0 / 6.0);
+    p = PSSG_FMA(p, t, 0.5);
+    p = PSSG_FMA(p, t, 1.0);
     return p;
   }
   return PSSG_DIV(PSSG_SUB(pssg_exp(t), 1.0), t);
@@ -193,15 +192,15 @@ PSSG_FN double pssg_log1p_over(double t) {
   if (t > -0.01 && t < 0.01) {
     /* sum_{j>=0} (-t)^j / (j+1), to t^9/10 */
     double p = -1.0 / 10.0;
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 9.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), -1.0 / 8.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 7.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), -1.0 / 6.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 5.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), -1.0 / 4.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0 / 3.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), -1.0 / 2.0);
-    p = PSSG_ADD(PSSG_MUL(p, t), 1.0);
+    p = PSSG_FMA(p, t, 1.0 / 9.0);
+    p = PSSG_FMA(p, t, -1.0 / 8.0);
+    p = PSSG_FMA(p, t, 1.0 / 7.0);
+    p = PSSG_FMA(p, t, -1.0 / 6.0);
+    p = PSSG_FMA(p, t, 1.0 / 5.0);
+    p = PSSG_FMA(p, t, -1.0 / 4.0);
+    p = PSSG_FMA(p, t, 1.0 / 3.0);
+    p = PSSG_FMA(p, t, -1.0 / 2.0);
+    p = PSSG_FMA(p, t, 1.0);
     return p;
   }
   /* log1p(t) = log(u) - ((u - 1) - t) / u with u = 1 + t (Goldberg 1991). */
@@ -217,6 +216,7 @@ typedef struct {
   double one_m_s;  /* 1 - s */
   double h_x1;     /* H(3/2) - h(1): left end of the sampled interval */
   double h_n;      /* H(N + 1/2): right end */
+  double squeeze;  /* k - x <= squeeze accepts without evaluating H and h */
   uint64_t n;      /* number of ranks N = U */
 } pssg_zipf;
 
@@ -236,12 +236,16 @@ PSSG_FN double pssg_zipf_h(const pssg_zipf* z, double x) {
   return pssg_exp(PSSG_MUL(-z->s, pssg_log(x)));
 }
 
+PSSG_FN double pssg_zipf_Hinv(const pssg_zipf* z, double y);
+
 PSSG_FN void pssg_zipf_init(pssg_zipf* z, double s, uint64_t n) {
   z->s = s;
   z->one_m_s = PSSG_SUB(1.0, s);
   z->n = n;
   z->h_x1 = PSSG_SUB(pssg_zipf_H(z, 1.5), 1.0);
   z->h_n = pssg_zipf_H(z, PSSG_ADD((double)n, 0.5));
+  /* the quick acceptance bound of rejection-inversion: 2 - H^-1(H(5/2) - h(2)) */
+  z->squeeze = PSSG_SUB(2.0, pssg_zipf_Hinv(z, PSSG_SUB(pssg_zipf_H(z, 2.5), pssg_zipf_h(z, 2.0))));
 }
 
 /* One rejection-inversion attempt with uniform u; returns 0 on rejection,
@@ -255,6 +259,7 @@ PSSG_FN uint64_t pssg_zipf_try(const pssg_zipf* z, double u) {
   if (kd > (double)z->n) kd = (double)z->n;
   uint64_t k = (uint64_t)kd;
   double kk = (double)k;
+  if (PSSG_SUB(kk, x) <= z->squeeze) return k;
   if (y >= PSSG_SUB(pssg_zipf_H(z, PSSG_ADD(kk, 0.5)), pssg_zipf_h(z, kk))) return k;
   return 0;
 }

@@ -60,6 +60,27 @@ class BatchDesc(ctypes.Structure):
                 ("skew_hint", ctypes.POINTER(ctypes.c_double))]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("tenants", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("arrival", ctypes.c_double), ("tenant", ctypes.c_uint32),
+                ("n", ctypes.c_uint64), ("d_items", ctypes.c_void_p), ("s", ctypes.c_double),
+                ("log2u", ctypes.c_int), ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
+                ("p", ctypes.c_uint32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tenant", ctypes.c_uint32), ("p", ctypes.c_uint32),
+                ("arrival", ctypes.c_double), ("admitted", ctypes.c_double),
+                ("completed", ctypes.c_double), ("n_segment", ctypes.c_uint32),
+                ("n_tenant", ctypes.c_uint32), ("tenant_items", ctypes.c_uint64),
+                ("status", ctypes.c_int)]
+
+
 # Every function of include/pss.h: name -> (restype, argtypes).
 SIGNATURES = {
     "pss_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -87,6 +108,16 @@ SIGNATURES = {
     "pss_batch_results": (ctypes.c_int, [vp, ctypes.POINTER(Entry), u32p, vp]),
     "pss_batch_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p, u64p, vp]),
     "pss_batch_free": (None, [vp]),
+    "pss_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+    "pss_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(Request), u32]),
+    "pss_server_start": (ctypes.c_int, [vp]),
+    "pss_server_wait": (ctypes.c_int, [vp, ctypes.c_double]),
+    "pss_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), u32, u32p]),
+    "pss_server_result": (ctypes.c_int, [vp, u64, ctypes.POINTER(Entry), u32p, ctypes.POINTER(Entry),
+                                         u32p]),
+    "pss_server_tenant_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p,
+                                                u64p]),
+    "pss_server_destroy": (None, [vp]),
     "pss_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
     "pss_gen_zipf": (ctypes.c_int, [vp, u64, ctypes.c_int, u64, u32, u64, ctypes.c_double,
@@ -418,6 +449,91 @@ class Batch:
         if getattr(self, "_h", None) is not None and self._h.value:
             load().pss_batch_free(self._h)
         self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop with continuous batching over resident tenant summaries
+    (pss_server_*).  Requests carry scheduled arrival times (open loop)."""
+
+    def __init__(self, tenants: int, k: int, budget_bytes: int = 16 << 30, max_batch: int = 256,
+                 max_inflight: int = 2048):
+        cfg = ServerConfig(int(tenants), int(k), int(budget_bytes), int(max_batch), int(max_inflight))
+        h = vp()
+        _check(load().pss_server_create(ctypes.byref(cfg), ctypes.byref(h)), "pss_server_create")
+        self._h = h
+        self.k = int(k)
+        self.tenants = int(tenants)
+        self._keep = []  # device buffers of caller-provided segments
+
+    def submit(self, requests):
+        """requests: iterable of dicts with id, arrival, tenant, n and either
+        items (a CUDA uint32 tensor) or s, log2u, seed, stream_id; optional p."""
+        reqs = list(requests)
+        arr = (Request * len(reqs))()
+        for i, r in enumerate(reqs):
+            items = r.get("items")
+            if items is not None:
+                if _check_items(items) != 4:
+                    raise ValueError("served segments are 4-byte items")
+                self._keep.append(items)
+            arr[i] = Request(int(r["id"]), float(r.get("arrival", 0.0)), int(r["tenant"]),
+                             int(r["n"]), items.data_ptr() if items is not None else None,
+                             float(r.get("s", 1.0)), int(r.get("log2u", 24)), int(r.get("seed", 0)),
+                             int(r.get("stream_id", 0)), int(r.get("p", 0) or 0))
+        _check(load().pss_server_submit(self._h, arr, len(reqs)), "pss_server_submit")
+
+    def start(self):
+        _check(load().pss_server_start(self._h), "pss_server_start")
+
+    def wait(self, timeout_s: float = 600.0):
+        _check(load().pss_server_wait(self._h, float(timeout_s)), "pss_server_wait")
+
+    def poll(self, cap: int = 1 << 16) -> list[dict]:
+        out = []
+        buf = (Completion * cap)()
+        while True:
+            n = u32()
+            _check(load().pss_server_poll(self._h, buf, cap, ctypes.byref(n)), "pss_server_poll")
+            for i in range(n.value):
+                c = buf[i]
+                out.append({f: getattr(c, f) for f, _ in Completion._fields_})
+            if n.value < cap:
+                return out
+
+    def result(self, rid: int):
+        """(segment query, tenant query) of a completed request, as Exported."""
+        a = (Entry * self.k)()
+        b = (Entry * self.k)()
+        na = u32()
+        nb = u32()
+        _check(load().pss_server_result(self._h, int(rid), a, ctypes.byref(na), b, ctypes.byref(nb)),
+               "pss_server_result")
+        sa = _entries_to_arrays(a, na.value)
+        sb = _entries_to_arrays(b, nb.value)
+        return Exported(*sa, 0, 0), Exported(*sb, 0, 0)
+
+    def tenant_export(self, tenant: int) -> Exported:
+        buf = (Entry * self.k)()
+        size = u32()
+        m = u64()
+        cov = u64()
+        _check(load().pss_server_tenant_export(self._h, int(tenant), buf, self.k, ctypes.byref(size),
+                                               ctypes.byref(m), ctypes.byref(cov)),
+               "pss_server_tenant_export")
+        it, ct, er = _entries_to_arrays(buf, size.value)
+        return Exported(it, ct, er, int(m.value), int(cov.value))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().pss_server_destroy(self._h)
+        self._h = None
+        self._keep = []
 
     def __del__(self):
         try:
