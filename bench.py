@@ -85,6 +85,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def replica_aggregate(local_ms: float, local_items: int, dist=None, device="cpu"):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    and the items of all ranks (value = items / time).  With dist=None (one
+    GPU) the local figures are returned."""
+    if dist is None:
+        return local_ms, local_items
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([local_items], dtype=torch.int64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -483,13 +497,9 @@ def main():
     clk = clocks.stop()
     prof = P.profile_read(reset=True)
     P.profile_enable(False)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, items_all = replica_aggregate(ev0.elapsed_time(ev1) / args.steps, n, dist, "cuda")
     barrier()
-    value = n * world / (ms / 1e3)
+    value = items_all / (ms / 1e3)
     hbm, peak_kind = peaks()
     input_gbs = n * w * world / (ms / 1e3) / 1e9
 
@@ -525,12 +535,8 @@ def main():
             qq = estep()
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1) / esteps
-        if dist is not None:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": n * world / (ems / 1e3), "unit": "items/s", "ms_per_step": ems,
+        ems, eitems = replica_aggregate(e0.elapsed_time(e1) / esteps, n, dist, "cuda")
+        e2e = {"value": eitems / (ems / 1e3), "unit": "items/s", "ms_per_step": ems,
                "h2d_bytes_per_step": n * w, "d2h_bytes_per_step": 8 + 24 * qq.size,
                "api": "pss_summarize_host + pss_query (pinned host input)"}
         del hx

@@ -52,37 +52,41 @@ def plan_blocks(n: int, k: int, skew: float = 1.0) -> int:
     return p
 
 
-def sweep(n: int = 1 << 27, item_bytes: int = 8, steps: int = 3, seed: int = 77):
-    """Measure items/s of the summarize path for every (k, skew, length) and
-    return (results, table).  Runs on the current CUDA device."""
+def sweep(blocks: int = 2048, item_bytes: int = 8, steps: int = 3, seed: int = 77):
+    """Measure items/s of the summarize path for every (k, skew, length),
+    each with the same number of blocks (so that only the block length
+    changes), and return (results, table).  Runs on the current CUDA device."""
     import torch
 
     import paper_1606_04669_gb300 as P
     stream = torch.cuda.current_stream()
     results, table = [], {}
-    for k in K_CLASSES:
-        table[k] = {}
-        for zs in SKEW_CLASSES:
-            x = P.gen_zipf(n, seed=seed, s=zs, log2u=32, item_bytes=item_bytes)
+    nmax = blocks * max(LENGTHS)
+    for zs in SKEW_CLASSES:
+        x = P.gen_zipf(nmax, seed=seed, s=zs, log2u=32, item_bytes=item_bytes)
+        for k in K_CLASSES:
+            table.setdefault(k, {})
             best = None
             for length in LENGTHS:
-                p = max(1, n // length)
-                P.summarize(x, k, p).close()
+                n = blocks * length
+                xs = x[:n]
+                P.summarize(xs, k, blocks).close()
                 torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 for _ in range(steps):
-                    P.summarize(x, k, p, stream=stream).close()
+                    P.summarize(xs, k, blocks, stream=stream).close()
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / steps
                 rate = n / (ms / 1e3)
-                results.append({"k": k, "skew": zs, "block_length": length, "p": p, "ms": ms,
+                results.append({"k": k, "skew": zs, "block_length": length, "p": blocks, "ms": ms,
                                 "items_per_s": rate})
                 if best is None or rate > best[1]:
                     best = (length, rate)
             table[k][zs] = best[0]
+        del x
     return results, table
 
 
