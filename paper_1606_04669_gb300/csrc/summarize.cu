@@ -28,8 +28,11 @@
 //     is processed again from the new state.
 //
 // Table: item -> counter slot in buckets of four 32-bit cells (16-bit tag,
-// slot + 1) read with one 128-bit shared load; deletions clear the cell (no
-// tombstones); each home bucket records how far its items were displaced.
+// slot + 1) read with one 128-bit shared load.  Each item has two buckets
+// (two hashes); it goes to the first unless that one is full, and a bit per
+// bucket records that some item of the first bucket lives in its second.
+// Deletions clear the cell (no tombstones); the bits are recounted at every
+// bucket-list rebuild, so they stay close to exact.
 //
 // Output: the block's summary sorted by item ascending, with size, minimum m
 // (the minimum count if k counters are in use, else 0) and the block length.
@@ -51,6 +54,7 @@ struct ItemOps<uint32_t> {
   static constexpr uint32_t SENT = 0xFFFFFFFFu;
   __device__ static __forceinline__ uint32_t h1(uint32_t x) { return x * 0x9E3779B1u; }
   __device__ static __forceinline__ uint32_t h2(uint32_t x) { return x * 0x85EBCA77u; }
+  __device__ static __forceinline__ uint32_t h3(uint32_t x) { return x * 0xC2B2AE35u; }
   __device__ static __forceinline__ u64 sort_key(uint32_t x, uint32_t slot) {
     return ((u64)x << 16) | slot;
   }
@@ -63,6 +67,9 @@ struct ItemOps<u64> {
   }
   __device__ static __forceinline__ uint32_t h2(u64 x) {
     return (uint32_t)((x * 0xC2B2AE3D27D4EB4Full) >> 32);
+  }
+  __device__ static __forceinline__ uint32_t h3(u64 x) {
+    return (uint32_t)((x * 0xD6E8FEB86659FD93ull) >> 32);
   }
   __device__ static __forceinline__ u64 sort_key(u64 x, uint32_t) { return x; }
 };
@@ -80,21 +87,22 @@ struct SSState {
   uint32_t cut;          // exact prefix of the window
   uint32_t exhausted;
   uint32_t need;         // 0 none, 1 incremental list rebuild, 2 full
-  uint32_t maxdisp;      // largest bucket displacement since the last table rebuild
+  uint32_t maxdisp;      // largest distance of an item past its second bucket
   uint32_t stall;
   uint32_t status;
 };
 
 template <typename ItemT>
 struct SSSmem {
-  uint32_t NB, nbshift, WT, wshift, CMAX, SORTN;
+  uint32_t NB, nbshift, NBW, WT, wshift, CMAX, SORTN;
   // persistent state
   ItemT* item;
   uint32_t* cnt;
   uint32_t* err;
   uint32_t* touch;
   uint32_t* cell;     // NB * 4 cells: (tag << 16) | (slot + 1), 0 = empty
-  uint32_t* dmax;     // per home bucket: largest displacement of its items
+  uint32_t* ovf;      // 2 * NBW words: bit b set when an item of first bucket b lives
+                      // outside it; second half: past its second bucket
   uint32_t* hfirst;   // per slot: first hit position in the window (members only)
   uint16_t* cellof;   // per slot: its cell
   uint16_t* list;
@@ -105,6 +113,7 @@ struct SSSmem {
   uint32_t* wpos;
   uint16_t* wslot;
   uint16_t* rankpos;
+  uint16_t* evwc;     // per event (time order): its window-table cell
   uint16_t* logpos;
   uint16_t* cand;
   uint16_t* candidx;
@@ -135,6 +144,7 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   const uint32_t nbk = (k + 1) / 2;
   L.NB = next_pow2(nbk < 16 ? 16 : nbk);
   L.nbshift = 32 - ilog2c(L.NB);
+  L.NBW = (L.NB + 31) / 32;
   L.WT = 2 * W;
   L.wshift = 32 - ilog2c(L.WT);
   L.CMAX = W + 2 * BS;
@@ -152,7 +162,7 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   const size_t after_touch = off;
   L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
   L.cell = (uint32_t*)take(16ull * L.NB);
-  L.dmax = (uint32_t*)take(4ull * L.NB);
+  L.ovf = (uint32_t*)take(8ull * L.NBW);
   L.hfirst = (uint32_t*)take(4ull * k);
   L.cellof = (uint16_t*)take(2ull * k);
   L.list = (uint16_t*)take(2ull * k);
@@ -163,6 +173,7 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   L.wpos = (uint32_t*)take(4ull * (L.WT + 1));
   L.wslot = (uint16_t*)take(2ull * (L.WT + 1));
   L.rankpos = (uint16_t*)take(2ull * W);
+  L.evwc = (uint16_t*)take(2ull * W);
   L.logpos = (uint16_t*)take(2ull * W);
   L.cand = (uint16_t*)take(2ull * L.CMAX);
   L.candidx = (uint16_t*)take(2ull * L.CMAX);
@@ -225,56 +236,75 @@ struct SSBlock {
     return block_exclusive_scan<BS>(v, buf, total);
   }
 
-  __device__ __forceinline__ int lookup(ItemT x) const {
-    const uint32_t h = ItemOps<ItemT>::h1(x);
-    const uint32_t b = h >> s.nbshift, tag = h & 0xFFFFu, mask = s.NB - 1;
-    const uint32_t d = s.dmax[b];
-    for (uint32_t dd = 0; dd <= d; ++dd) {
-      const uint4 c = *(const uint4*)&s.cell[((b + dd) & mask) * 4];
-      const uint32_t cs[4] = {c.x, c.y, c.z, c.w};
+  __device__ __forceinline__ bool ovf_bit(uint32_t half, uint32_t b) const {
+    return (s.ovf[half * s.NBW + (b >> 5)] >> (b & 31)) & 1u;
+  }
+
+  __device__ __forceinline__ int find_in(uint32_t bb, uint32_t tag, ItemT x) const {
+    const uint4 c = *(const uint4*)&s.cell[bb * 4];
+    const uint32_t cs[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (cs[i] && (cs[i] >> 16) == tag) {
-          const uint32_t q = (cs[i] & 0xFFFFu) - 1;
-          if (s.item[q] == x) return (int)q;
-        }
+    for (int i = 0; i < 4; ++i) {
+      if (cs[i] && (cs[i] >> 16) == tag) {
+        const uint32_t q = (cs[i] & 0xFFFFu) - 1;
+        if (s.item[q] == x) return (int)q;
       }
     }
     return -1;
+  }
+
+  __device__ __forceinline__ int lookup(ItemT x) const {
+    const uint32_t h = ItemOps<ItemT>::h1(x);
+    const uint32_t b = h >> s.nbshift, tag = h & 0xFFFFu, mask = s.NB - 1;
+    int q = find_in(b, tag, x);
+    if (q >= 0 || !ovf_bit(0, b)) return q;
+    const uint32_t b2 = ItemOps<ItemT>::h3(x) >> s.nbshift;
+    const uint32_t d = ovf_bit(1, b) ? S->maxdisp : 0u;
+    for (uint32_t dd = 0; dd <= d; ++dd) {
+      q = find_in((b2 + dd) & mask, tag, x);
+      if (q >= 0) return q;
+    }
+    return -1;
+  }
+
+  // Claims an empty cell of bucket bb for val; cells only fill up while
+  // inserting, so one seen taken stays taken.
+  __device__ __forceinline__ bool claim(uint32_t bb, uint32_t val, uint32_t slot) {
+    const uint4 cv = *(const uint4*)&s.cell[bb * 4];
+    const uint32_t cs[4] = {cv.x, cv.y, cv.z, cv.w};
+    for (int i = 0; i < 4; ++i) {
+      if (cs[i] == 0u && atomicCAS(&s.cell[bb * 4 + i], 0u, val) == 0u) {
+        s.cellof[slot] = (uint16_t)(bb * 4 + i);
+        return true;
+      }
+    }
+    return false;
   }
 
   __device__ __forceinline__ void insert(ItemT x, uint32_t slot, uint32_t& status) {
     const uint32_t h = ItemOps<ItemT>::h1(x);
     const uint32_t b = h >> s.nbshift, mask = s.NB - 1;
     const uint32_t val = ((h & 0xFFFFu) << 16) | (slot + 1);
+    if (claim(b, val, slot)) return;
+    atomicOr(&s.ovf[b >> 5], 1u << (b & 31));
+    const uint32_t b2 = ItemOps<ItemT>::h3(x) >> s.nbshift;
     for (uint32_t dd = 0; dd < s.NB; ++dd) {
-      const uint32_t bb = (b + dd) & mask;
-      for (int i = 0; i < 4; ++i) {
-        uint32_t* c = &s.cell[bb * 4 + i];
-        if (*c == 0u && atomicCAS(c, 0u, val) == 0u) {
-          s.cellof[slot] = (uint16_t)(bb * 4 + i);
-          if (dd) {
-            atomicMax(&s.dmax[b], dd);
-            atomicMax(&S->maxdisp, dd);
-          }
-          return;
+      if (claim((b2 + dd) & mask, val, slot)) {
+        if (dd) {
+          atomicOr(&s.ovf[s.NBW + (b >> 5)], 1u << (b & 31));
+          atomicMax(&S->maxdisp, dd);
         }
+        return;
       }
     }
     status |= ST_PROBE;
   }
 
-  // One occurrence at position t for counter tgt (NONE32: none); lanes of the
-  // warp with the same counter add theirs with one atomic (frequent items
-  // would otherwise serialize on their counter).  All lanes call it.
+  // One occurrence at position t for counter tgt (NONE32: none).
   __device__ __forceinline__ void add_occurrence(uint32_t tgt, uint32_t t) {
-    const unsigned grp = __match_any_sync(0xffffffffu, tgt);
     if (tgt != NONE32) {
-      const uint32_t mx = __reduce_max_sync(grp, t);
-      if ((threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1)) {
-        atomicAdd(&s.cnt[tgt], (uint32_t)__popc(grp));
-        atomicMax(&s.touch[tgt], mx);
-      }
+      atomicAdd(&s.cnt[tgt], 1u);
+      atomicMax(&s.touch[tgt], t);
     }
   }
 
@@ -285,7 +315,8 @@ struct SSBlock {
     } else {
       c = ItemOps<ItemT>::h2(x) >> s.wshift;
       for (uint32_t i = 0; i < s.WT; ++i) {
-        const ItemT prev = atomicCAS(&s.wkey[c], ItemOps<ItemT>::SENT, x);
+        ItemT prev = s.wkey[c];
+        if (prev == ItemOps<ItemT>::SENT) prev = atomicCAS(&s.wkey[c], ItemOps<ItemT>::SENT, x);
         if (prev == ItemOps<ItemT>::SENT || prev == x) break;
         c = (c + 1) & (s.WT - 1);
       }
@@ -306,12 +337,11 @@ struct SSBlock {
 
   __device__ void rebuild_table(uint32_t& status) {
     for (uint32_t c = threadIdx.x; c < 4 * s.NB; c += BS) s.cell[c] = 0;
-    for (uint32_t b = threadIdx.x; b < s.NB; b += BS) s.dmax[b] = 0;
+    for (uint32_t w = threadIdx.x; w < 2 * s.NBW; w += BS) s.ovf[w] = 0;
+    if (threadIdx.x == 0) S->maxdisp = 0;
     __syncthreads();
     const uint32_t used = S->used;
     for (uint32_t i = threadIdx.x; i < used; i += BS) insert(s.item[i], i, status);
-    __syncthreads();
-    if (threadIdx.x == 0) S->maxdisp = 0;
     __syncthreads();
   }
 
@@ -324,7 +354,23 @@ struct SSBlock {
     const uint32_t c0 = min(threadIdx.x * per, k), c1 = min(c0 + per, k);
     uint32_t mn = 0xFFFFFFFFu;
     for (uint32_t i = c0; i < c1; ++i) mn = min(mn, s.cnt[i]);
+    for (uint32_t w = threadIdx.x; w < 2 * s.NBW; w += BS) s.ovf[w] = 0;
+    if (threadIdx.x == 0) S->maxdisp = 0;
     mn = block_min_u32<BS>(mn, s.wsum);
+    // overflow bits and distances of the counters as they are placed now
+    for (uint32_t i = c0; i < c1; ++i) {
+      const ItemT x = s.item[i];
+      const uint32_t b = ItemOps<ItemT>::h1(x) >> s.nbshift;
+      const uint32_t cb = (uint32_t)s.cellof[i] >> 2;
+      if (cb != b) {
+        atomicOr(&s.ovf[b >> 5], 1u << (b & 31));
+        const uint32_t dd = (cb - (ItemOps<ItemT>::h3(x) >> s.nbshift)) & (s.NB - 1);
+        if (dd) {
+          atomicOr(&s.ovf[s.NBW + (b >> 5)], 1u << (b & 31));
+          atomicMax(&S->maxdisp, dd);
+        }
+      }
+    }
     const bool incremental = !full_scan && mn == S->m + 1;
     const uint32_t epoch = S->epoch_start;
     // (a) members to sort by touch: all of them, or those older than the epoch
@@ -439,7 +485,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   uint32_t status = 0;
 
   for (uint32_t i = tid; i < 4 * s.NB; i += BS) s.cell[i] = 0;
-  for (uint32_t i = tid; i < s.NB; i += BS) s.dmax[i] = 0;
+  for (uint32_t i = tid; i < 2 * s.NBW; i += BS) s.ovf[i] = 0;
   for (uint32_t i = tid; i < k; i += BS) {
     s.hfirst[i] = NONE32;
     s.fate[i] = 0;
@@ -487,7 +533,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
         const uint32_t b = h >> s.nbshift;
         tg[j] = h & 0xFFFFu;
         hc[j] = *(const uint4*)&s.cell[b * 4];
-        hd[j] = s.dmax[b];
+        hd[j] = (s.ovf[b >> 5] >> (b & 31)) & 1u;
       }
       int q1[IPT];
       ItemT it1[IPT];
@@ -546,13 +592,15 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       }
     uint32_t M;
     const uint32_t rbase = B.scan(nf, &M);
-    uint32_t rank[IPT];
     {
       uint32_t rr = rbase;
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
-        rank[j] = rr;
-        if (first >> j & 1) s.rankpos[rr++] = (uint16_t)(tid * IPT + j);
+        if (first >> j & 1) {
+          s.rankpos[rr] = (uint16_t)(tid * IPT + j);
+          s.evwc[rr] = (uint16_t)wc[j];
+          ++rr;
+        }
       }
     }
     if (tid == 0) {
@@ -682,44 +730,47 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     }
     __syncthreads();
 
-    // ---- P5: every event's victim (or the cut)
+    // ---- P5: every event's victim (or the cut), one thread per event; the
+    // victim of a miss goes to its window-table cell
     const uint32_t nconv = S.nconv, nskip = S.nskip;
     const uint32_t limit = full ? min(S.nvalid, S.astop) : 0u;
     const bool can_exhaust = full && list_end && S.astop >= S.nvalid;
     const uint32_t nfree = full ? 0u : k - S.used;
     const uint32_t used0 = S.used;
-    // event e passes skipped member i iff e >= skipl[i] - i
+    // event e passes skipped member i iff skipl[i] - i <= e (non-decreasing in i)
     auto assign = [&](uint32_t e) {
-      uint32_t a = e;
-      for (uint32_t i = 0; i < nskip; ++i) a += (s.skipl[i] - i <= e) ? 1u : 0u;
-      return a;
+      uint32_t lo = 0, hi = nskip;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s.skipl[mid] - mid <= e) lo = mid + 1;
+        else hi = mid;
+      }
+      return e + lo;
     };
-    uint32_t vict[IPT];
-    uint32_t va[IPT];
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      vict[j] = 0;
-      va[j] = NONE32;
-      if (!(first >> j & 1)) continue;
-      const uint32_t rel = tid * IPT + j;
+    for (uint32_t r = tid; r < M; r += BS) {
+      const uint32_t wcr = s.evwc[r];
       if (!full) {
-        if (rank[j] < nfree) vict[j] = used0 + rank[j];
-        else atomicMin(&S.cut, rel);
+        if (r < nfree) s.wslot[wcr] = (uint16_t)(used0 + r);
+        else atomicMin(&S.cut, (uint32_t)s.rankpos[r]);
         continue;
       }
-      uint32_t e = rank[j];
-      for (uint32_t c = 0; c < nconv; ++c) e += s.convlo[c] <= rank[j] ? 1u : 0u;
-      const uint32_t a = assign(e);
+      // conversions merged before this event: convlo is non-decreasing
+      uint32_t lo = 0, hi = nconv;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s.convlo[mid] <= r) lo = mid + 1;
+        else hi = mid;
+      }
+      const uint32_t a = assign(r + lo);
       if (a < limit) {
-        vict[j] = s.cand[a];
-        va[j] = a;
+        s.wslot[wcr] = s.cand[a];
       } else {
-        atomicMin(&S.cut, rel);
+        atomicMin(&S.cut, (uint32_t)s.rankpos[r]);
         if (can_exhaust) S.exhausted = 1;
       }
     }
     // conversion events: thread c handles conversion c
-    uint32_t cvict = 0, cva = NONE32, ctime = NONE32, csrc = 0;
+    uint32_t cvict = 0, ctime = NONE32, csrc = 0;
     ItemT citem = (ItemT)0;
     if (tid < nconv) {
       ctime = s.convt[tid];
@@ -728,7 +779,6 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       const uint32_t a = assign(tid + s.convlo[tid]);
       if (a < limit) {
         cvict = s.cand[a];
-        cva = a;
       } else {
         atomicMin(&S.cut, ctime);
         if (can_exhaust) S.exhausted = 1;
@@ -739,25 +789,24 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
 
     // ---- P6: evictions take the victims' items out of the table
     if (full) {
-#pragma unroll
-      for (int j = 0; j < IPT; ++j)
-        if ((first >> j & 1) && tid * IPT + j < cut) s.cell[s.cellof[vict[j]]] = 0u;
+      for (uint32_t r = tid; r < M && s.rankpos[r] < cut; r += BS)
+        s.cell[s.cellof[s.wslot[s.evwc[r]]]] = 0u;
       if (tid < nconv && ctime < cut) s.cell[s.cellof[cvict]] = 0u;
     }
     __syncthreads();
 
     // ---- P7: insertions; new counters start at m (their occurrences are added next)
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t rel = tid * IPT + j;
-      if (!(first >> j & 1) || rel >= cut) continue;
-      const uint32_t v = vict[j];
-      B.insert(x[j], v, status);
-      s.item[v] = x[j];
+    for (uint32_t r = tid; r < M; r += BS) {
+      const uint32_t rel = s.rankpos[r];
+      if (rel >= cut) break;
+      const uint32_t wcr = s.evwc[r];
+      const uint32_t v = s.wslot[wcr];
+      const ItemT xr = s.wkey[wcr];  // the window-table key is the item
+      B.insert(xr, v, status);
+      s.item[v] = xr;
       s.cnt[v] = full ? m : 0u;
       s.err[v] = full ? m : 0u;
       s.touch[v] = 0;
-      s.wslot[wc[j]] = (uint16_t)v;
       if (full) s.logpos[rel] = (uint16_t)(v + 1);
     }
     if (tid < nconv && ctime < cut) {
