@@ -17,7 +17,10 @@
 //     time order by construction.
 //   * events: the first occurrence of each item missing from the table
 //     ("misses"), plus "conversions": the first occurrence of a bucket
-//     member's item after that member was evicted in this window.
+//     member's item after that member was evicted in this window.  A missed
+//     item claims a "pending" cell of the table in the lookup pass itself,
+//     keyed by the window position of the occurrence that claimed it; its
+//     counter is written into that cell once its victim is known.
 //   * event e (in time order) evicts the (e + s)-th bucket member, s being the
 //     number of members before it that were "skipped" (hit before their turn).
 //     Only members hit inside the window can be skipped or converted; one warp
@@ -44,6 +47,8 @@ namespace pss {
 namespace {
 
 constexpr uint32_t NONE32 = 0xFFFFFFFFu;
+constexpr uint16_t NONE16 = 0xFFFFu;
+constexpr uint32_t PEND = 0x8000u;  // cell reference of a pending item: PEND | window position
 constexpr int HMAX = 256;     // skipped members tracked per window
 constexpr int CONVMAX = 32;   // conversions tracked per window (one per lane)
 
@@ -51,9 +56,7 @@ template <typename ItemT>
 struct ItemOps;
 template <>
 struct ItemOps<uint32_t> {
-  static constexpr uint32_t SENT = 0xFFFFFFFFu;
   __device__ static __forceinline__ uint32_t h1(uint32_t x) { return x * 0x9E3779B1u; }
-  __device__ static __forceinline__ uint32_t h2(uint32_t x) { return x * 0x85EBCA77u; }
   __device__ static __forceinline__ uint32_t h3(uint32_t x) { return x * 0xC2B2AE35u; }
   __device__ static __forceinline__ u64 sort_key(uint32_t x, uint32_t slot) {
     return ((u64)x << 16) | slot;
@@ -61,12 +64,8 @@ struct ItemOps<uint32_t> {
 };
 template <>
 struct ItemOps<u64> {
-  static constexpr u64 SENT = ~0ull;
   __device__ static __forceinline__ uint32_t h1(u64 x) {
     return (uint32_t)((x * 0x9E3779B97F4A7C15ull) >> 32);
-  }
-  __device__ static __forceinline__ uint32_t h2(u64 x) {
-    return (uint32_t)((x * 0xC2B2AE3D27D4EB4Full) >> 32);
   }
   __device__ static __forceinline__ uint32_t h3(u64 x) {
     return (uint32_t)((x * 0xD6E8FEB86659FD93ull) >> 32);
@@ -94,26 +93,26 @@ struct SSState {
 
 template <typename ItemT>
 struct SSSmem {
-  uint32_t NB, nbshift, NBW, WT, wshift, CMAX, SORTN;
+  uint32_t NB, nbshift, NBW, CMAX, SORTN;
   // persistent state
   ItemT* item;
   uint32_t* cnt;
-  uint32_t* err;
   uint32_t* touch;
-  uint32_t* cell;     // NB * 4 cells: (tag << 16) | (slot + 1), 0 = empty
+  uint32_t* cell;     // NB * 4 cells: (tag << 16) | ref, 0 = empty; ref = slot + 1 or
+                      // PEND | window position of a pending item
   uint32_t* ovf;      // 2 * NBW words: bit b set when an item of first bucket b lives
                       // outside it; second half: past its second bucket
   uint32_t* hfirst;   // per slot: first hit position in the window (members only)
   uint16_t* cellof;   // per slot: its cell
   uint16_t* list;
   uint16_t* logq;
-  uint16_t* fate;     // per evicted member with a conversion: its new slot + 1
   // window scratch (aliased by the rebuild sort)
-  ItemT* wkey;
-  uint32_t* wpos;
-  uint16_t* wslot;
-  uint16_t* rankpos;
-  uint16_t* evwc;     // per event (time order): its window-table cell
+  ItemT* wbuf;        // the window's items
+  uint32_t* ppos;     // per claiming position: first occurrence of its item
+  uint16_t* pslot;    // per claiming position: the counter its item gets
+  uint16_t* pcell;    // per claiming position: the claimed cell
+  uint16_t* rankpos;  // per event (time order): its position
+  uint16_t* evpid;    // per event: the claiming position of its item
   uint16_t* logpos;
   uint16_t* cand;
   uint16_t* candidx;
@@ -122,11 +121,14 @@ struct SSSmem {
   uint16_t* convt;
   uint16_t* convlo;
   uint16_t* convsrc;
+  uint16_t* convfrom;  // per conversion: the evicted member's slot
+  uint16_t* convto;    // per conversion: the slot its item gets (NONE16 past the cut)
   uint32_t* wsum;
   uint32_t* rkey;     // rebuild sort (over the window scratch)
   uint16_t* rpay;
   u64* fkey;          // final sort (over everything after touch)
   uint16_t* fpay;
+  uint32_t* ferr;
 };
 
 __host__ __device__ inline uint32_t ilog2c(uint32_t x) {
@@ -141,12 +143,11 @@ template <typename ItemT, int BS, int IPT>
 __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSmem<ItemT>* out) {
   constexpr uint32_t W = BS * IPT;
   SSSmem<ItemT> L;
-  const uint32_t nbk = (k + 1) / 2;
+  // room for k counters and a window of pending items at <= 1/2 load
+  const uint32_t nbk = (k + W + 1) / 2;
   L.NB = next_pow2(nbk < 16 ? 16 : nbk);
   L.nbshift = 32 - ilog2c(L.NB);
   L.NBW = (L.NB + 31) / 32;
-  L.WT = 2 * W;
-  L.wshift = 32 - ilog2c(L.WT);
   L.CMAX = W + 2 * BS;
   L.SORTN = next_pow2(k);
   size_t off = 0;
@@ -157,7 +158,6 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   };
   L.item = (ItemT*)take(sizeof(ItemT) * k);
   L.cnt = (uint32_t*)take(4ull * k);
-  L.err = (uint32_t*)take(4ull * k);
   L.touch = (uint32_t*)take(4ull * k);
   const size_t after_touch = off;
   L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
@@ -167,13 +167,13 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   L.cellof = (uint16_t*)take(2ull * k);
   L.list = (uint16_t*)take(2ull * k);
   L.logq = (uint16_t*)take(2ull * k);
-  L.fate = (uint16_t*)take(2ull * k);
   const size_t u0 = off;
-  L.wkey = (ItemT*)take(sizeof(ItemT) * (L.WT + 1));
-  L.wpos = (uint32_t*)take(4ull * (L.WT + 1));
-  L.wslot = (uint16_t*)take(2ull * (L.WT + 1));
+  L.wbuf = (ItemT*)take(sizeof(ItemT) * W);
+  L.ppos = (uint32_t*)take(4ull * W);
+  L.pslot = (uint16_t*)take(2ull * W);
+  L.pcell = (uint16_t*)take(2ull * W);
   L.rankpos = (uint16_t*)take(2ull * W);
-  L.evwc = (uint16_t*)take(2ull * W);
+  L.evpid = (uint16_t*)take(2ull * W);
   L.logpos = (uint16_t*)take(2ull * W);
   L.cand = (uint16_t*)take(2ull * L.CMAX);
   L.candidx = (uint16_t*)take(2ull * L.CMAX);
@@ -182,6 +182,8 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   L.convt = (uint16_t*)take(2ull * CONVMAX);
   L.convlo = (uint16_t*)take(2ull * CONVMAX);
   L.convsrc = (uint16_t*)take(2ull * CONVMAX);
+  L.convfrom = (uint16_t*)take(2ull * CONVMAX);
+  L.convto = (uint16_t*)take(2ull * CONVMAX);
   // The rebuild sort reuses the window scratch.
   L.rkey = (uint32_t*)(base + u0);
   L.rpay = (uint16_t*)(base + u0 + align16(4ull * L.SORTN));
@@ -190,7 +192,9 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   // The final sort reuses everything after touch (the state is dead by then).
   L.fkey = (u64*)(base + after_touch);
   L.fpay = (uint16_t*)(base + after_touch + 8ull * L.SORTN);
-  const size_t final_end = align16(after_touch + 8ull * L.SORTN + 2ull * L.SORTN);
+  L.ferr = (uint32_t*)(base + after_touch + 8ull * L.SORTN + align16(2ull * L.SORTN));
+  const size_t final_end =
+      align16(after_touch + 8ull * L.SORTN + align16(2ull * L.SORTN) + 4ull * k);
   if (final_end > off) off = final_end;
   if (out) *out = L;
   return off;
@@ -240,35 +244,80 @@ struct SSBlock {
     return (s.ovf[half * s.NBW + (b >> 5)] >> (b & 31)) & 1u;
   }
 
+  // Result of a table match: slot >= 0, -2 - pid for the pending item of
+  // claiming position pid, -1 for none.
+  __device__ __forceinline__ int cell_match(uint32_t c, uint32_t tag, ItemT x) const {
+    if (c == 0u || (c >> 16) != tag) return -1;
+    const uint32_t ref = c & 0xFFFFu;
+    if (ref & PEND) {
+      const uint32_t pid = ref & (PEND - 1);
+      return s.wbuf[pid] == x ? -2 - (int)pid : -1;
+    }
+    return s.item[ref - 1] == x ? (int)(ref - 1) : -1;
+  }
+
   __device__ __forceinline__ int find_in(uint32_t bb, uint32_t tag, ItemT x) const {
     const uint4 c = *(const uint4*)&s.cell[bb * 4];
     const uint32_t cs[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (cs[i] && (cs[i] >> 16) == tag) {
-        const uint32_t q = (cs[i] & 0xFFFFu) - 1;
-        if (s.item[q] == x) return (int)q;
-      }
+      const int r = cell_match(cs[i], tag, x);
+      if (r != -1) return r;
     }
     return -1;
   }
 
-  __device__ __forceinline__ int lookup(ItemT x) const {
+  // x outside its first bucket b: in its second bucket or past it, where the
+  // overflow bits of b say so
+  __device__ __forceinline__ int find_overflow(ItemT x, uint32_t b, uint32_t tag) const {
+    if (!ovf_bit(0, b)) return -1;
+    const uint32_t b2 = ItemOps<ItemT>::h3(x) >> s.nbshift, mask = s.NB - 1;
+    const uint32_t d = ovf_bit(1, b) ? *(volatile uint32_t*)&S->maxdisp : 0u;
+    for (uint32_t dd = 0; dd <= d; ++dd) {
+      const int r = find_in((b2 + dd) & mask, tag, x);
+      if (r != -1) return r;
+    }
+    return -1;
+  }
+
+  // x (occurring at window position rel) in the table, or else a pending cell
+  // claimed for it.  Claims run concurrently and nothing leaves the table
+  // meanwhile: every claimant of one item walks the same cells in the same
+  // order, and compares each filled cell with x, so they agree on one cell.
+  __device__ int find_or_claim(ItemT x, uint32_t rel, uint32_t& status) {
     const uint32_t h = ItemOps<ItemT>::h1(x);
     const uint32_t b = h >> s.nbshift, tag = h & 0xFFFFu, mask = s.NB - 1;
-    int q = find_in(b, tag, x);
-    if (q >= 0 || !ovf_bit(0, b)) return q;
+    int r = find_overflow(x, b, tag);
+    if (r != -1) return r;
+    const uint32_t val = (tag << 16) | PEND | rel;
     const uint32_t b2 = ItemOps<ItemT>::h3(x) >> s.nbshift;
-    const uint32_t d = ovf_bit(1, b) ? S->maxdisp : 0u;
-    for (uint32_t dd = 0; dd <= d; ++dd) {
-      q = find_in((b2 + dd) & mask, tag, x);
-      if (q >= 0) return q;
+    for (uint32_t step = 0; step <= s.NB; ++step) {
+      const uint32_t bb = step == 0 ? b : ((b2 + step - 1) & mask);
+      // the overflow bits go up before any claim they describe
+      if (step == 1) atomicOr(&s.ovf[b >> 5], 1u << (b & 31));
+      if (step == 2) atomicOr(&s.ovf[s.NBW + (b >> 5)], 1u << (b & 31));
+      const uint4 cv = *(const uint4*)&s.cell[bb * 4];
+      const uint32_t cs[4] = {cv.x, cv.y, cv.z, cv.w};
+      for (int i = 0; i < 4; ++i) {
+        uint32_t c = cs[i];
+        if (c == 0u) {
+          c = atomicCAS(&s.cell[bb * 4 + i], 0u, val);
+          if (c == 0u) {
+            s.pcell[rel] = (uint16_t)(bb * 4 + i);
+            if (step >= 2) atomicMax(&S->maxdisp, step - 1);
+            return -2 - (int)rel;
+          }
+        }
+        r = cell_match(c, tag, x);
+        if (r != -1) return r;
+      }
     }
-    return -1;
+    status |= ST_PROBE;  // cannot happen: the table has room for k + W items
+    s.pcell[rel] = NONE16;
+    return -2 - (int)rel;
   }
 
-  // Claims an empty cell of bucket bb for val; cells only fill up while
-  // inserting, so one seen taken stays taken.
+  // Claims an empty cell of bucket bb for val (a cell seen taken is skipped).
   __device__ __forceinline__ bool claim(uint32_t bb, uint32_t val, uint32_t slot) {
     const uint4 cv = *(const uint4*)&s.cell[bb * 4];
     const uint32_t cs[4] = {cv.x, cv.y, cv.z, cv.w};
@@ -308,31 +357,13 @@ struct SSBlock {
     }
   }
 
-  __device__ __forceinline__ uint32_t wtab_insert(ItemT x, uint32_t rel) {
-    uint32_t c;
-    if (x == ItemOps<ItemT>::SENT) {
-      c = s.WT;
-    } else {
-      c = ItemOps<ItemT>::h2(x) >> s.wshift;
-      for (uint32_t i = 0; i < s.WT; ++i) {
-        ItemT prev = s.wkey[c];
-        if (prev == ItemOps<ItemT>::SENT) prev = atomicCAS(&s.wkey[c], ItemOps<ItemT>::SENT, x);
-        if (prev == ItemOps<ItemT>::SENT || prev == x) break;
-        c = (c + 1) & (s.WT - 1);
-      }
-    }
-    atomicMin(&s.wpos[c], rel);
-    return c;
-  }
-
   // Window scratch that must start clear (the rebuild sort writes over it).
   __device__ void reset_window_scratch() {
     constexpr uint32_t W = BS * IPT;
-    for (uint32_t i = threadIdx.x; i <= s.WT; i += BS) {
-      s.wkey[i] = ItemOps<ItemT>::SENT;
-      s.wpos[i] = NONE32;
+    for (uint32_t i = threadIdx.x; i < W; i += BS) {
+      s.ppos[i] = NONE32;
+      s.logpos[i] = 0;
     }
-    for (uint32_t i = threadIdx.x; i < W; i += BS) s.logpos[i] = 0;
   }
 
   __device__ void rebuild_table(uint32_t& status) {
@@ -486,10 +517,9 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
 
   for (uint32_t i = tid; i < 4 * s.NB; i += BS) s.cell[i] = 0;
   for (uint32_t i = tid; i < 2 * s.NBW; i += BS) s.ovf[i] = 0;
-  for (uint32_t i = tid; i < k; i += BS) {
-    s.hfirst[i] = NONE32;
-    s.fate[i] = 0;
-  }
+  for (uint32_t i = tid; i < k; i += BS) s.hfirst[i] = NONE32;
+  // err of slot q is kept in the output node (written once per insertion)
+  u64* __restrict__ gerr = out.err + obase;
   B.reset_window_scratch();
   if (tid == 0) {
     S.m = 0; S.head = 0; S.list_len = 0; S.log_len = 0; S.used = 0; S.full = 0;
@@ -518,53 +548,82 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       }
     }
     const uint32_t full = S.full, m = S.m;
+    // the window's items, for pending cells (which name them by position)
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) s.wbuf[tid * IPT + j] = x[j];
+    __syncthreads();
 
-    // ---- P1: look up; first hit of bucket members; misses into the window table
-    int sl[IPT];
-    uint32_t wc[IPT];
+    // ---- P1: look up or claim; first hit of bucket members; first occurrence of misses
+    int sl[IPT];                  // slot, or -2 - pid for a pending item
     uint32_t miss = 0, mhit = 0;  // bit j: item j missed / hit a bucket member
     {
-      // home buckets of all items first (independent loads), then resolve
+      // first buckets of all items first (independent loads), then resolve
       uint4 hc[IPT];
-      uint32_t hd[IPT], tg[IPT];
+      uint32_t tg[IPT];
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const uint32_t h = ItemOps<ItemT>::h1(x[j]);
-        const uint32_t b = h >> s.nbshift;
         tg[j] = h & 0xFFFFu;
-        hc[j] = *(const uint4*)&s.cell[b * 4];
-        hd[j] = (s.ovf[b >> 5] >> (b & 31)) & 1u;
+        hc[j] = *(const uint4*)&s.cell[(h >> s.nbshift) * 4];
       }
-      int q1[IPT];
-      ItemT it1[IPT];
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const uint32_t cs[4] = {hc[j].x, hc[j].y, hc[j].z, hc[j].w};
-        q1[j] = -1;
+        int r = -1;
 #pragma unroll
-        for (int i = 3; i >= 0; --i)
-          if (cs[i] && (cs[i] >> 16) == tg[j]) q1[j] = (int)(cs[i] & 0xFFFFu) - 1;
-        it1[j] = q1[j] >= 0 ? s.item[q1[j]] : (ItemT)0;
+        for (int i = 0; i < 4; ++i)
+          if (r == -1) r = B.cell_match(cs[i], tg[j], x[j]);
+        sl[j] = r;
+      }
+      // the rest (past the first bucket, or not in the table), packed onto
+      // the warp's lanes; results by position in evpid (free until P2):
+      // slot, or PEND | pid
+      {
+        unsigned bal[IPT];
+        uint32_t base[IPT], tot = 0;
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+          bal[j] = __ballot_sync(0xffffffffu, sl[j] == -1 && tid * IPT + j < nact);
+          base[j] = tot;
+          tot += __popc(bal[j]);
+        }
+        for (uint32_t g0 = 0; g0 < tot; g0 += 32) {
+          const uint32_t g = g0 + lane;
+          if (g < tot) {
+            int jj = 0;
+#pragma unroll
+            for (int j = 1; j < IPT; ++j) jj += g >= base[j] ? 1 : 0;
+            unsigned bj = bal[0];
+#pragma unroll
+            for (int j = 1; j < IPT; ++j)
+              if (jj == j) bj = bal[j];
+            const uint32_t src = __fns(bj, 0, (int)(g - base[jj]) + 1);
+            const uint32_t rel = ((warp << 5) + src) * IPT + (uint32_t)jj;
+            const int r = B.find_or_claim(s.wbuf[rel], rel, status);
+            s.evpid[rel] = (uint16_t)(r >= 0 ? (uint32_t)r : (PEND | (uint32_t)(-2 - r)));
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+          if (bal[j] >> lane & 1) {
+            const uint32_t v = s.evpid[tid * IPT + j];
+            sl[j] = (v & PEND) ? -2 - (int)(v & (PEND - 1)) : (int)v;
+          }
+        }
       }
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
-        if (q1[j] >= 0 && it1[j] == x[j]) sl[j] = q1[j];
-        else if (q1[j] < 0 && hd[j] == 0) sl[j] = -1;
-        else sl[j] = B.lookup(x[j]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t rel = tid * IPT + j;
-      wc[j] = 0;
-      if (rel >= nact) sl[j] = -1;
-      if (rel < nact) {
-        if (sl[j] < 0) {
-          miss |= 1u << j;
-          wc[j] = B.wtab_insert(x[j], rel);
-        } else if (full && s.cnt[sl[j]] == m) {
-          mhit |= 1u << j;
-          atomicMin(&s.hfirst[sl[j]], rel);
+        const uint32_t rel = tid * IPT + j;
+        const int r = sl[j];
+        if (rel < nact) {
+          if (r < 0) {
+            miss |= 1u << j;
+            atomicMin(&s.ppos[-2 - r], rel);
+          } else if (full && s.cnt[r] == m) {
+            mhit |= 1u << j;
+            atomicMin(&s.hfirst[r], rel);
+          }
         }
       }
     }
@@ -582,11 +641,11 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       continue;
     }
 
-    // ---- P2: first occurrences of the misses, ranked by position
+    // ---- P2: first occurrences of the misses (the events), ranked by position
     uint32_t first = 0, nf = 0;
 #pragma unroll
     for (int j = 0; j < IPT; ++j)
-      if ((miss >> j & 1) && s.wpos[wc[j]] == tid * IPT + j) {
+      if ((miss >> j & 1) && s.ppos[-2 - sl[j]] == tid * IPT + j) {
         first |= 1u << j;
         ++nf;
       }
@@ -598,7 +657,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       for (int j = 0; j < IPT; ++j) {
         if (first >> j & 1) {
           s.rankpos[rr] = (uint16_t)(tid * IPT + j);
-          s.evwc[rr] = (uint16_t)wc[j];
+          s.evpid[rr] = (uint16_t)(-2 - sl[j]);
           ++rr;
         }
       }
@@ -731,7 +790,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     __syncthreads();
 
     // ---- P5: every event's victim (or the cut), one thread per event; the
-    // victim of a miss goes to its window-table cell
+    // victim of a miss is kept by its claiming position
     const uint32_t nconv = S.nconv, nskip = S.nskip;
     const uint32_t limit = full ? min(S.nvalid, S.astop) : 0u;
     const bool can_exhaust = full && list_end && S.astop >= S.nvalid;
@@ -748,9 +807,9 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       return e + lo;
     };
     for (uint32_t r = tid; r < M; r += BS) {
-      const uint32_t wcr = s.evwc[r];
+      const uint32_t pid = s.evpid[r];
       if (!full) {
-        if (r < nfree) s.wslot[wcr] = (uint16_t)(used0 + r);
+        if (r < nfree) s.pslot[pid] = (uint16_t)(used0 + r);
         else atomicMin(&S.cut, (uint32_t)s.rankpos[r]);
         continue;
       }
@@ -763,7 +822,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       }
       const uint32_t a = assign(r + lo);
       if (a < limit) {
-        s.wslot[wcr] = s.cand[a];
+        s.pslot[pid] = s.cand[a];
       } else {
         atomicMin(&S.cut, (uint32_t)s.rankpos[r]);
         if (can_exhaust) S.exhausted = 1;
@@ -787,35 +846,40 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     __syncthreads();
     const uint32_t cut = S.cut;
 
-    // ---- P6: evictions take the victims' items out of the table
-    if (full) {
-      for (uint32_t r = tid; r < M && s.rankpos[r] < cut; r += BS)
-        s.cell[s.cellof[s.wslot[s.evwc[r]]]] = 0u;
-      if (tid < nconv && ctime < cut) s.cell[s.cellof[cvict]] = 0u;
-    }
-    __syncthreads();
-
-    // ---- P7: insertions; new counters start at m (their occurrences are added next)
+    // ---- P6: commit the events before the cut: each victim's cell is freed and
+    // the event's claimed cell names the victim, whose counter starts at m
+    // (the occurrences are added next); claims past the cut are dropped.
+    // Every cell here has one writer; conversions claim cells that are free.
     for (uint32_t r = tid; r < M; r += BS) {
-      const uint32_t rel = s.rankpos[r];
-      if (rel >= cut) break;
-      const uint32_t wcr = s.evwc[r];
-      const uint32_t v = s.wslot[wcr];
-      const ItemT xr = s.wkey[wcr];  // the window-table key is the item
-      B.insert(xr, v, status);
-      s.item[v] = xr;
+      const uint32_t pid = s.evpid[r], rel = s.rankpos[r];
+      const uint32_t pc = s.pcell[pid];
+      if (rel >= cut) {
+        if (pc != NONE16) s.cell[pc] = 0u;
+        continue;
+      }
+      const uint32_t v = s.pslot[pid];
+      if (full) s.cell[s.cellof[v]] = 0u;
+      if (pc != NONE16) {
+        s.cell[pc] = (s.cell[pc] & 0xFFFF0000u) | (v + 1);
+        s.cellof[v] = (uint16_t)pc;
+      }
+      s.item[v] = s.wbuf[pid];
       s.cnt[v] = full ? m : 0u;
-      s.err[v] = full ? m : 0u;
+      gerr[v] = full ? m : 0u;
       s.touch[v] = 0;
       if (full) s.logpos[rel] = (uint16_t)(v + 1);
     }
+    if (tid < nconv) {
+      s.convfrom[tid] = (uint16_t)csrc;
+      s.convto[tid] = ctime < cut ? (uint16_t)cvict : NONE16;
+    }
     if (tid < nconv && ctime < cut) {
+      s.cell[s.cellof[cvict]] = 0u;
       B.insert(citem, cvict, status);
       s.item[cvict] = citem;
       s.cnt[cvict] = m;
-      s.err[cvict] = m;
+      gerr[cvict] = m;
       s.touch[cvict] = 0;
-      s.fate[csrc] = (uint16_t)(cvict + 1);
       s.logpos[ctime] = (uint16_t)(cvict + 1);
     }
     __syncthreads();
@@ -827,12 +891,14 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       uint32_t tgt = NONE32;
       if (rel < cut) {
         if (miss >> j & 1) {
-          tgt = s.wslot[wc[j]];
+          tgt = s.pslot[-2 - sl[j]];
         } else {
           tgt = (uint32_t)sl[j];
           if (mhit >> j & 1) {
-            const uint32_t f = s.fate[tgt];
-            if (f) tgt = f - 1;  // the member was evicted: its item was re-inserted
+            uint32_t f = NONE16;  // the member was evicted: its item was re-inserted
+            for (uint32_t c = 0; c < nconv; ++c)
+              if (s.convfrom[c] == tgt) f = s.convto[c];
+            if (f != NONE16) tgt = f;
             else if (s.hfirst[tgt] == rel) s.logpos[rel] = (uint16_t)(tgt + 1);  // m -> m + 1
           }
         }
@@ -866,12 +932,8 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       if (mhit >> j & 1) s.hfirst[sl[j]] = NONE32;
-      if (first >> j & 1) {
-        if (wc[j] != s.WT) s.wkey[wc[j]] = ItemOps<ItemT>::SENT;
-        s.wpos[wc[j]] = NONE32;
-      }
+      s.ppos[tid * IPT + j] = NONE32;
     }
-    if (tid < nconv) s.fate[csrc] = 0;
     if (warp == 0) {
       // the applied events are the prefix of the merged sequence before the cut
       const uint32_t norig = warp_lower_bound(s.rankpos, M, cut);
@@ -917,6 +979,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   for (uint32_t i = tid; i < used; i += BS) mn = min(mn, s.cnt[i]);
   mn = block_min_u32<BS>(mn, s.wsum);  // before the sort keys overwrite wsum
   const uint32_t n2p = next_pow2(used ? used : 1);
+  for (uint32_t i = tid; i < used; i += BS) s.ferr[i] = (uint32_t)gerr[i];
   for (uint32_t i = tid; i < n2p; i += BS) {
     if (i < used) {
       s.fkey[i] = ItemOps<ItemT>::sort_key(s.item[i], i);
@@ -932,7 +995,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     const uint32_t q = s.fpay[i];
     out.item[obase + i] = s.item[q];
     out.count[obase + i] = s.cnt[q];
-    out.err[obase + i] = s.err[q];
+    out.err[obase + i] = s.ferr[q];
   }
   if (tid == 0) {
     out.size[node] = used;
