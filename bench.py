@@ -303,7 +303,7 @@ def run_batched(args):
     ks = [sp.k for sp in specs]
     ps = [autotune.plan_blocks(sp.n, sp.k, sp.s) for sp in specs]
     total = sum(sp.n for sp in specs)
-    batch = P.Batch(items, ks, ps=ps)
+    batch = P.Batch(items, ks, ps=ps, skews=[sp.s for sp in specs])
     for _ in range(max(args.warmup, 1)):
         batch.run(use_graph=True)
     torch.cuda.synchronize()

@@ -335,6 +335,19 @@ int pss_server_tenant_export(pss_server* server, uint32_t tenant, pss_entry* hos
 void pss_server_destroy(pss_server* server);
 
 /*
+ * Kernel choice for the block summaries of pss_summarize*.  Blocks with
+ * k <= kmax counters are summarized by one warp each, the counters in the
+ * warp's registers (kmax is clamped to 256); larger k, or kmax = 0, use the
+ * window-parallel CTA kernel.  Both apply the same sequential rule, so the
+ * summaries are the same either way; the warp kernel is the faster one where
+ * misses dominate (small k, weak skew).  The default is 64.  The batch API
+ * chooses per stream from k <= 256 and its skew hint, unless kmax is 0.
+ * Process-wide; returns the previous value.  Launches already enqueued (or
+ * captured) keep their kernel.
+ */
+uint32_t pss_set_warp_kmax(uint32_t kmax);
+
+/*
  * Profiling.  The paper reports run time and the "fractional overhead" of
  * the reduction relative to the computation (Section 4.1); the library can
  * time its own kernel groups with CUDA events on the launching stream.

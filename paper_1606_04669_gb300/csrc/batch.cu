@@ -26,7 +26,24 @@ struct StreamPlan {
   std::vector<size_t> level_off;     // arena offset of each level's set
   std::vector<uint32_t> level_nodes;
   uint32_t out_off;                  // first result entry of this stream
+  bool warp;                         // block summaries on the warp kernel
 };
+
+// Kernel for a stream's block summaries.  Both kernels compute the same
+// summaries; the warp kernel (counters in registers, one item at a time)
+// wins where misses dominate, the window-parallel CTA kernel where hits do.
+// Crossovers measured on a GB300 at full occupancy (u64 items, 2^29 items
+// in 4096..65536 blocks, 1e9 items/s warp vs CTA): k = 64: 14.5 vs 2.1 at
+// s = 0.8, 22 vs 5.6 at 1.4, 26 vs 35 at 2.0; k = 128: 9.9 vs 3.8, 15 vs
+// 14, 17 vs 52; k = 256: 5.8 vs 6.9, 10 vs 23, 11 vs 64.  An unknown skew
+// (hint <= 0) counts as weak.
+bool use_warp_kernel(uint32_t k, double skew) {
+  if (warp_kmax() == 0 || k > WARP_SS_MAX_K) return false;
+  if (skew <= 0.0) return k <= 64;
+  if (k <= 64) return skew < 1.8;
+  if (k <= 128) return skew < 1.45;
+  return skew < 0.7;
+}
 
 struct LevelLaunch {
   size_t descs_off, tasks_off;
@@ -38,6 +55,8 @@ struct KClass {
   std::vector<uint32_t> sids;
   size_t tasks_off = 0, counter_off = 0, qids_off = 0;
   uint32_t ntasks = 0, grid = 0;
+  size_t wtasks_off = 0, wcounter_off = 0;  // the class's streams on the warp kernel
+  uint32_t wntasks = 0, wgrid = 0;
   std::vector<LevelLaunch> levels;
   cudaStream_t side = nullptr;
   cudaEvent_t join = nullptr;
@@ -108,13 +127,25 @@ int enqueue(pss_batch* b, cudaStream_t s) {
     e = cudaStreamWaitEvent(c.side, b->kc[0].join, 0);
     if (e != cudaSuccess) return from_cuda(e);
     e = cudaMemsetAsync(b->arena + c.counter_off, 0, 4, c.side);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->arena + c.wcounter_off, 0, 4, c.side);
     if (e != cudaSuccess) return from_cuda(e);
     {
-      ProfScope prof(PROF_SUMMARIZE, c.side, 1);
-      count_launches(1);
-      e = launch_summarize_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
-                                        (const BatchTask*)(b->arena + c.tasks_off), c.ntasks,
-                                        (uint32_t*)(b->arena + c.counter_off), c.k, c.grid, c.side);
+      ProfScope prof(PROF_SUMMARIZE, c.side, (c.ntasks ? 1 : 0) + (c.wntasks ? 1 : 0));
+      if (c.wntasks) {
+        count_launches(1);
+        e = launch_summarize_warp_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
+                                               (const BatchTask*)(b->arena + c.wtasks_off),
+                                               c.wntasks, (uint32_t*)(b->arena + c.wcounter_off),
+                                               c.k, c.wgrid, c.side);
+        if (e != cudaSuccess) return from_cuda(e);
+      }
+      if (c.ntasks) {
+        count_launches(1);
+        e = launch_summarize_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
+                                          (const BatchTask*)(b->arena + c.tasks_off), c.ntasks,
+                                          (uint32_t*)(b->arena + c.counter_off), c.k, c.grid,
+                                          c.side);
+      }
     }
     if (e != cudaSuccess) return from_cuda(e);
     {
@@ -199,6 +230,7 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
     sp.k = desc->k[i];
     const double skew = desc->skew_hint ? desc->skew_hint[i] : 0.0;
     sp.p = (desc->p && desc->p[i]) ? desc->p[i] : pss_plan_blocks(sp.n, sp.k, w, skew);
+    sp.warp = use_warp_kernel(sp.k, skew);
     if (sp.k < 2 || sp.k > PSS_MAX_K || sp.p == 0 || (sp.n > 0 && !sp.items) ||
         (sp.n + sp.p - 1) / sp.p >= (1ull << 32)) {
       destroy(b);
@@ -244,30 +276,49 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
     c.k = kvals[ci];
     for (uint32_t i = 0; i < ns; ++i)
       if (b->s[i].k == c.k) c.sids.push_back(i);
-    std::vector<BatchTask> tasks;
-    std::vector<uint64_t> lens;
-    for (uint32_t i : c.sids)
-      for (uint32_t r = 0; r < b->s[i].p; ++r) tasks.push_back(BatchTask{i, r});
-    std::vector<uint64_t> key(tasks.size());
-    for (size_t t = 0; t < tasks.size(); ++t) {
-      const StreamPlan& sp = b->s[tasks[t].stream];
-      key[t] = block_bound(tasks[t].index + 1ull, sp.n, sp.p) - block_bound(tasks[t].index, sp.n, sp.p);
+    // tasks of each kernel, longest blocks first so that the last wave is short
+    auto plan_tasks = [&](bool warp, size_t* off, size_t* counter, uint32_t* count) {
+      std::vector<BatchTask> tasks;
+      for (uint32_t i : c.sids)
+        if (b->s[i].warp == warp)
+          for (uint32_t r = 0; r < b->s[i].p; ++r) tasks.push_back(BatchTask{i, r});
+      std::vector<uint64_t> key(tasks.size());
+      for (size_t t = 0; t < tasks.size(); ++t) {
+        const StreamPlan& sp = b->s[tasks[t].stream];
+        key[t] = block_bound(tasks[t].index + 1ull, sp.n, sp.p) -
+                 block_bound(tasks[t].index, sp.n, sp.p);
+      }
+      std::vector<size_t> order(tasks.size());
+      for (size_t t = 0; t < order.size(); ++t) order[t] = t;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](size_t a, size_t bb) { return key[a] > key[bb]; });
+      std::vector<BatchTask> sorted(tasks.size());
+      for (size_t t = 0; t < order.size(); ++t) sorted[t] = tasks[order[t]];
+      *count = (uint32_t)sorted.size();
+      *off = take(sizeof(BatchTask) * (sorted.size() ? sorted.size() : 1));
+      upload(*off, sorted.data(), sizeof(BatchTask) * sorted.size());
+      *counter = take(4);
+    };
+    plan_tasks(false, &c.tasks_off, &c.counter_off, &c.ntasks);
+    plan_tasks(true, &c.wtasks_off, &c.wcounter_off, &c.wntasks);
+    if (c.ntasks) {
+      const int per_sm = w == 4 ? summarize_ctas_per_sm<uint32_t>(c.k) : summarize_ctas_per_sm<u64>(c.k);
+      if (per_sm <= 0) {
+        destroy(b);
+        return PSS_EINVAL;
+      }
+      c.grid = (uint32_t)std::min<uint64_t>((uint64_t)sms * per_sm, c.ntasks);
     }
-    std::vector<size_t> order(tasks.size());
-    for (size_t t = 0; t < order.size(); ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t bb) { return key[a] > key[bb]; });
-    std::vector<BatchTask> sorted(tasks.size());
-    for (size_t t = 0; t < order.size(); ++t) sorted[t] = tasks[order[t]];
-    c.ntasks = (uint32_t)sorted.size();
-    c.tasks_off = take(sizeof(BatchTask) * (sorted.size() ? sorted.size() : 1));
-    upload(c.tasks_off, sorted.data(), sizeof(BatchTask) * sorted.size());
-    c.counter_off = take(4);
-    const int per_sm = w == 4 ? summarize_ctas_per_sm<uint32_t>(c.k) : summarize_ctas_per_sm<u64>(c.k);
-    if (per_sm <= 0) {
-      destroy(b);
-      return PSS_EINVAL;
+    if (c.wntasks) {
+      const int per_sm = w == 4 ? summarize_warp_ctas_per_sm<uint32_t>(c.k)
+                                : summarize_warp_ctas_per_sm<u64>(c.k);
+      if (per_sm <= 0) {
+        destroy(b);
+        return PSS_EINVAL;
+      }
+      // WS_WPB blocks per CTA
+      c.wgrid = (uint32_t)std::min<uint64_t>((uint64_t)sms * per_sm, (c.wntasks + 3) / 4);
     }
-    c.grid = (uint32_t)std::min<uint64_t>((uint64_t)sms * per_sm, c.ntasks);
     // merge levels: level l -> l + 1 for every stream of the class that has it
     for (uint32_t l = 0;; ++l) {
       std::vector<MergeDesc> descs;

@@ -74,13 +74,35 @@ template <typename ItemT>
 cudaError_t launch_copy_node(SetView<ItemT> in, uint32_t node, SetView<ItemT> out,
                              uint32_t out_node, cudaStream_t stream);
 
-// Batch forms (batch.cu).  Persistent block summaries over a task list.
+// Batch forms (batch.cu).  Persistent block summaries over a task list (the
+// window-parallel CTA kernel; the warp kernel has its own entry point).
 template <typename ItemT>
 cudaError_t launch_summarize_batch(const BatchStream* streams, const BatchTask* tasks,
                                    uint32_t ntasks, uint32_t* counter, uint32_t k, uint32_t grid,
                                    cudaStream_t stream);
 
-// Resident summarize CTAs per SM for k counters (0 if it cannot run).
+// Warp-per-block summaries for k <= WARP_SS_MAX_K (summarize_warp.cu).  The
+// plain path (launch_summarize_blocks) uses them for k <= warp_kmax()
+// (default WARP_SS_DEFAULT_K); the batch picks per stream (batch.cu).
+constexpr uint32_t WARP_SS_MAX_K = 256;
+constexpr uint32_t WARP_SS_DEFAULT_K = 64;
+uint32_t warp_kmax();
+
+template <typename ItemT>
+cudaError_t launch_summarize_warp_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
+                                         uint32_t count, SetView<ItemT> out, uint32_t node0,
+                                         cudaStream_t stream);
+
+template <typename ItemT>
+cudaError_t launch_summarize_warp_batch(const BatchStream* streams, const BatchTask* tasks,
+                                        uint32_t ntasks, uint32_t* counter, uint32_t k,
+                                        uint32_t grid, cudaStream_t stream);
+
+template <typename ItemT>
+int summarize_warp_ctas_per_sm(uint32_t k);
+
+// Resident CTAs per SM of the persistent CTA kernel for k counters (0 if it
+// cannot run).
 template <typename ItemT>
 int summarize_ctas_per_sm(uint32_t k);
 

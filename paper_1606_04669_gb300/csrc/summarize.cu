@@ -39,6 +39,8 @@
 //
 // Output: the block's summary sorted by item ascending, with size, minimum m
 // (the minimum count if k counters are in use, else 0) and the block length.
+#include <atomic>
+
 #include "pss_internal.cuh"
 #include "pss_kernels.cuh"
 
@@ -1041,6 +1043,12 @@ __global__ void __launch_bounds__(BS) ss_batch_kernel(const BatchStream* __restr
 
 }  // namespace
 
+namespace {
+std::atomic<uint32_t> g_warp_kmax{WARP_SS_DEFAULT_K};
+}  // namespace
+
+uint32_t warp_kmax() { return g_warp_kmax.load(); }
+
 template <typename ItemT>
 size_t ss_smem_bytes(uint32_t k) {
   return ss_carve<ItemT, SS_BS, SS_IPT>(k, nullptr, nullptr);
@@ -1050,6 +1058,8 @@ template <typename ItemT>
 cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
                                     uint32_t count, SetView<ItemT> out, uint32_t node0,
                                     cudaStream_t stream) {
+  if (out.k <= warp_kmax())
+    return launch_summarize_warp_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
   const size_t smem = ss_smem_bytes<ItemT>(out.k);
   auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
@@ -1098,3 +1108,7 @@ template cudaError_t launch_summarize_blocks<u64>(const u64*, u64, uint32_t, uin
                                                   SetView<u64>, uint32_t, cudaStream_t);
 
 }  // namespace pss
+
+extern "C" uint32_t pss_set_warp_kmax(uint32_t kmax) {
+  return pss::g_warp_kmax.exchange(kmax < pss::WARP_SS_MAX_K ? kmax : pss::WARP_SS_MAX_K);
+}

@@ -118,6 +118,7 @@ SIGNATURES = {
     "pss_server_tenant_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p,
                                                 u64p]),
     "pss_server_destroy": (None, [vp]),
+    "pss_set_warp_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
     "pss_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
     "pss_gen_zipf": (ctypes.c_int, [vp, u64, ctypes.c_int, u64, u32, u64, ctypes.c_double,
@@ -361,6 +362,12 @@ def gen_zipf(count: int, *, seed: int, s: float, log2u: int, item_bytes: int = 4
                                int(stream_id), int(start), float(s), int(log2u),
                                vp(_stream_handle(stream))), "pss_gen_zipf")
     return out
+
+
+def set_warp_kmax(kmax: int) -> int:
+    """Blocks with k <= kmax counters use the warp-per-block kernel (kmax <= 256;
+    0 forces the window-parallel CTA kernel).  Returns the previous value."""
+    return int(load().pss_set_warp_kmax(int(kmax)))
 
 
 def profile_enable(on: bool = True):

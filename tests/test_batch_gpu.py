@@ -77,3 +77,30 @@ def test_batch_explicit_plan_and_workload_params():
         x = oracle.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, width=8, stream=sp.index)
         root, rq = oracle.parallel_space_saving(x, sp.k, ps[i])
         assert ents(res[i]) == summary_entries(rq), i
+
+
+@pytest.mark.parametrize("kmax", [0, 64])
+def test_batch_kernel_choice_by_skew(kmax):
+    # Streams with k <= 256 go to the warp kernel where the skew hint says
+    # misses dominate, the others to the CTA kernel (kmax = 0: all CTA);
+    # every result against the oracle.
+    prev = P.set_warp_kmax(kmax)
+    try:
+        ks = [64, 128, 256, 64, 128, 256, 2, 100, 1024]
+        skews = [0.6, 0.9, 0.5, 2.5, 1.9, 1.2, 1.0, 0.0, 0.8]
+        items = [P.gen_zipf(60_000 + 1000 * i, seed=11, s=max(sk, 0.7), log2u=20, item_bytes=8,
+                            stream_id=i) for i, sk in enumerate(skews)]
+        ps = [1 + i % 4 for i in range(len(ks))]
+        batch = P.Batch(items, ks, ps=ps, skews=skews)
+        batch.run(use_graph=True)
+        res = batch.results()
+        for i, (k, sk) in enumerate(zip(ks, skews)):
+            x = oracle.gen_zipf(60_000 + 1000 * i, seed=11, s=max(sk, 0.7), log2u=20, width=8,
+                                stream=i)
+            root, rq = oracle.parallel_space_saving(x, k, ps[i])
+            e = batch.export(i)
+            assert ents(e) == summary_entries(root) and (e.m, e.n_covered) == (root.m, len(x)), i
+            assert ents(res[i]) == summary_entries(rq), i
+        batch.close()
+    finally:
+        P.set_warp_kmax(prev)

@@ -254,3 +254,32 @@ def test_sweep_corners_sampled_blocks_and_bounds(zs, k, seed):
     assert cnts[~stored].max(initial=0) <= e.m
     q = root.query(n, k)
     assert set(vals[cnts * np.uint64(k) > np.uint64(n)].tolist()) <= set(q.item.tolist())
+
+
+@pytest.fixture
+def warp_kmax():
+    prev = P.set_warp_kmax(256)
+    yield P.set_warp_kmax
+    P.set_warp_kmax(prev)
+
+
+@pytest.mark.parametrize("kmax", [0, 256])
+def test_small_k_both_kernels(warp_kmax, kmax):
+    # k <= 256 runs one warp per block (counters in registers) by default;
+    # kmax = 0 sends the same blocks through the window-parallel CTA kernel.
+    warp_kmax(kmax)
+    rng = np.random.default_rng(77 + kmax)
+    for k in (2, 3, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 200, 255, 256):
+        w = 8 if k % 2 else 4
+        s = 0.6 + 1.6 * rng.random()
+        x = oracle.gen_zipf(40_000 + 97 * k, seed=500 + k, s=s, log2u=14 if k < 64 else 32, width=w)
+        compare_tree(x, k, 1 + k % 7)
+    compare_tree(np.full(5000, 0xFFFFFFFF, np.uint32), 64, 3)
+    compare_tree(np.arange(20_000, dtype=np.uint32), 256, 2)   # every item a miss
+    compare_tree(np.zeros(0, np.uint32), 16, 3)
+
+
+def test_fuzz_small_universes_cta_kernel(warp_kmax):
+    # The fuzz cases again with every block on the window-parallel CTA kernel.
+    warp_kmax(0)
+    test_fuzz_small_universes()
