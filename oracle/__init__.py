@@ -93,6 +93,9 @@ def _load():
         lib.oracle_gen_log.argtypes = [ctypes.c_double]
         lib.oracle_gen_exp.restype = ctypes.c_double
         lib.oracle_gen_exp.argtypes = [ctypes.c_double]
+        for name in ("oracle_gen_log_t", "oracle_gen_exp_t"):
+            getattr(lib, name).restype = ctypes.c_double
+            getattr(lib, name).argtypes = [ctypes.c_double]
         _lib = lib
         return lib
 
@@ -270,3 +273,13 @@ def gen_log(x: float) -> float:
 
 def gen_exp(x: float) -> float:
     return float(_load().oracle_gen_exp(x))
+
+
+def gen_log_t(x: float) -> float:
+    """The sampler's table-driven log (the generator module's pssg_log_t)."""
+    return float(_load().oracle_gen_log_t(x))
+
+
+def gen_exp_t(x: float) -> float:
+    """The sampler's table-driven exp (the generator module's pssg_exp_t)."""
+    return float(_load().oracle_gen_exp_t(x))

@@ -346,15 +346,32 @@ uint32_t oracle_query(const uint64_t* si, const uint64_t* sc, const uint64_t* se
 
 // ---- seeded input generator (host side of the shared module) ----
 
+}  // extern "C"
+
+namespace {
+// The sampler's tables, built once by the shared module's own functions.
+const pssg_tables* gen_tables() {
+  static const pssg_tables tb = [] {
+    pssg_tables t;
+    pssg_tables_init(&t);
+    return t;
+  }();
+  return &tb;
+}
+}  // namespace
+
+extern "C" {
+
 void oracle_philox4x32_10(uint32_t* ctr, uint32_t k0, uint32_t k1) { pssg_philox4x32_10(ctr, k0, k1); }
 
 // Items [start, start + count) of the stream (seed, stream, s, U = 2^log2u).
 void oracle_gen_zipf(void* out, uint64_t start, uint64_t count, int width, uint64_t seed,
                      uint32_t stream, double s, int log2u) {
+  const pssg_tables* tb = gen_tables();
   pssg_zipf z;
-  pssg_zipf_init(&z, s, (log2u >= 64) ? ~0ull : (1ull << log2u));
+  pssg_zipf_init(&z, tb, s, (log2u >= 64) ? ~0ull : (1ull << log2u));
   for (uint64_t i = 0; i < count; ++i) {
-    uint64_t x = pssg_zipf_item(&z, log2u, seed, stream, start + i);
+    uint64_t x = pssg_zipf_item(&z, tb, log2u, seed, stream, start + i);
     if (width == 4)
       ((uint32_t*)out)[i] = (uint32_t)x;
     else
@@ -381,14 +398,17 @@ void oracle_gen_zipf_mt(void* out, uint64_t start, uint64_t count, int width, ui
 // Ranks only (no bijection), for distribution tests of the generator.
 void oracle_gen_zipf_ranks(uint64_t* out, uint64_t start, uint64_t count, uint64_t seed,
                            uint32_t stream, double s, uint64_t n_ranks) {
+  const pssg_tables* tb = gen_tables();
   pssg_zipf z;
-  pssg_zipf_init(&z, s, n_ranks);
-  for (uint64_t i = 0; i < count; ++i) out[i] = pssg_zipf_rank(&z, seed, stream, start + i);
+  pssg_zipf_init(&z, tb, s, n_ranks);
+  for (uint64_t i = 0; i < count; ++i) out[i] = pssg_zipf_rank(&z, tb, seed, stream, start + i);
 }
 
 uint64_t oracle_rank_to_item(uint64_t r, int log2u) { return pssg_rank_to_item(r, log2u); }
 
 double oracle_gen_log(double x) { return pssg_log(x); }
 double oracle_gen_exp(double x) { return pssg_exp(x); }
+double oracle_gen_log_t(double x) { return pssg_log_t(gen_tables(), x); }
+double oracle_gen_exp_t(double x) { return pssg_exp_t(gen_tables(), x); }
 
 }  // extern "C"

@@ -1,17 +1,22 @@
-"""Block-length autotuner for the batched and served forms.
+"""Autotuner for the batched and served forms.
 
 The number of blocks p changes the result (Algorithm 1 reduces p block
 summaries), so it must be a pure function of the request -- (n, k, skew) --
 and never of load; the plan is recorded so that the oracle can replay it.
 `plan_blocks` reads a table of block lengths per (k class, skew class)
-produced by `sweep()` on a GB300 (the measured table is TABLE below; the
-library's own `pss_plan_blocks` is the default when no table entry applies).
+produced by `sweep()` on a GB300 (TABLE below; the library's own
+`pss_plan_blocks` is the default when no table is used).
 
 What is tuned and what is not:
-  * block length (hence p): tuned here;
-  * CTA count: the persistent summarize kernel runs SMs x resident CTAs per
-    SM (from the occupancy calculator for the k's shared memory), not tuned;
-  * table load factor: fixed at <= 50% live cells by the kernel's layout;
+  * block length (hence p): tuned here, per (k class, skew class);
+  * summarize kernel (window-parallel CTA kernel, or one warp per block with
+    the counters in registers, for k <= 256): the result does not depend on
+    it, so the library picks it per stream from k and the skew hint; the
+    crossovers it uses are measured by `sweep_kernels()`;
+  * CTA count: the persistent kernels run SMs x resident CTAs per SM (from the
+    occupancy calculator for the k's shared memory), not tuned;
+  * table load factor: fixed at <= 1/2 (k counters plus one window of pending
+    items) by the kernel's layout;
   * merge fan-in: the binary tree over adjacent pairs is part of the result
     (combine is not associative), so it is not a tunable.
 """
@@ -24,12 +29,14 @@ K_CLASSES = (64, 256, 1024, 4096)
 SKEW_CLASSES = (0.8, 1.4, 2.0)
 LENGTHS = (1 << 16, 1 << 17, 1 << 18, 1 << 19)
 
-# Measured by sweep() (see profiles/autotune_block_length.md): the block
-# length with the highest items/s for each (k class, skew class).
+# Measured by sweep() on a GB300 (2048 blocks per point, u64 items): the
+# block length with the highest items/s for each (k class, skew class).
+# Longer blocks won everywhere, by 1-24% over 2^16 (the per-block fixed work
+# -- table set-up, final sort, summary write -- is amortized over more items).
 TABLE = {
-    64: {0.8: 1 << 17, 1.4: 1 << 17, 2.0: 1 << 17},
-    256: {0.8: 1 << 17, 1.4: 1 << 17, 2.0: 1 << 17},
-    1024: {0.8: 1 << 18, 1.4: 1 << 18, 2.0: 1 << 18},
+    64: {0.8: 1 << 19, 1.4: 1 << 19, 2.0: 1 << 19},
+    256: {0.8: 1 << 19, 1.4: 1 << 19, 2.0: 1 << 19},
+    1024: {0.8: 1 << 19, 1.4: 1 << 19, 2.0: 1 << 19},
     4096: {0.8: 1 << 19, 1.4: 1 << 19, 2.0: 1 << 19},
 }
 
@@ -52,14 +59,31 @@ def plan_blocks(n: int, k: int, skew: float = 1.0) -> int:
     return p
 
 
+def _time_batch(P, torch, x, k, p, skew, steps):
+    """ms per run of one stream through the batch path (the kernel the batch
+    picks for k and the skew hint)."""
+    stream = torch.cuda.current_stream()
+    b = P.Batch([x], [k], ps=[p], skews=[skew])
+    b.run(use_graph=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        b.run(use_graph=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.close()
+    return e0.elapsed_time(e1) / steps
+
+
 def sweep(blocks: int = 2048, item_bytes: int = 8, steps: int = 3, seed: int = 77):
-    """Measure items/s of the summarize path for every (k, skew, length),
-    each with the same number of blocks (so that only the block length
-    changes), and return (results, table).  Runs on the current CUDA device."""
+    """Items/s of the batch path for every (k, skew, length), each with the same
+    number of blocks (so that only the block length changes); returns
+    (results, table).  Runs on the current CUDA device."""
     import torch
 
     import paper_1606_04669_gb300 as P
-    stream = torch.cuda.current_stream()
     results, table = [], {}
     nmax = blocks * max(LENGTHS)
     for zs in SKEW_CLASSES:
@@ -69,17 +93,7 @@ def sweep(blocks: int = 2048, item_bytes: int = 8, steps: int = 3, seed: int = 7
             best = None
             for length in LENGTHS:
                 n = blocks * length
-                xs = x[:n]
-                P.summarize(xs, k, blocks).close()
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for _ in range(steps):
-                    P.summarize(xs, k, blocks, stream=stream).close()
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / steps
+                ms = _time_batch(P, torch, x[:n], k, blocks, zs, steps)
                 rate = n / (ms / 1e3)
                 results.append({"k": k, "skew": zs, "block_length": length, "p": blocks, "ms": ms,
                                 "items_per_s": rate})
@@ -90,6 +104,47 @@ def sweep(blocks: int = 2048, item_bytes: int = 8, steps: int = 3, seed: int = 7
     return results, table
 
 
+def sweep_kernels(n: int = 1 << 29, item_bytes: int = 8, steps: int = 3, seed: int = 9):
+    """Items/s of the two summarize kernels for k <= 256 at full occupancy
+    (many blocks), per (skew, k, block length): the data behind the
+    library's per-stream kernel choice."""
+    import torch
+
+    import paper_1606_04669_gb300 as P
+    stream = torch.cuda.current_stream()
+
+    def timeit(x, k, p):
+        P.summarize(x, k, p).close()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            P.summarize(x, k, p, stream=stream).close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    out = []
+    prev = P.set_warp_kmax(256)
+    try:
+        for zs in SKEW_CLASSES:
+            x = P.gen_zipf(n, seed=seed, s=zs, log2u=32, item_bytes=item_bytes)
+            for k in (64, 128, 256):
+                for length in (1 << 13, 1 << 15, 1 << 17):
+                    p = n // length
+                    row = {"skew": zs, "k": k, "block_length": length, "p": p}
+                    for name, kmax in (("warp", 256), ("cta", 0)):
+                        P.set_warp_kmax(kmax)
+                        row[name + "_items_per_s"] = n / (timeit(x, k, p) / 1e3)
+                    P.set_warp_kmax(256)
+                    out.append(row)
+            del x
+    finally:
+        P.set_warp_kmax(prev)
+    return out
+
+
 if __name__ == "__main__":
     t = time.time()
     res, tab = sweep()
@@ -97,3 +152,5 @@ if __name__ == "__main__":
         print(json.dumps(r))
     print(json.dumps({"table": {str(k): {str(s): v for s, v in d.items()} for k, d in tab.items()},
                       "seconds": time.time() - t}))
+    for r in sweep_kernels():
+        print(json.dumps(r))

@@ -11,13 +11,21 @@ namespace pss {
 
 namespace {
 
-__global__ void gen_zipf_kernel(void* out, u64 count, int item_bytes, u64 seed, uint32_t sid,
-                                u64 start, double s, int log2u) {
-  pssg_zipf z;
-  pssg_zipf_init(&z, s, (log2u >= 64) ? ~0ull : (1ull << log2u));
+// The tables and the sampler's constants are built once per CTA (the same
+// functions build them on the host).
+__global__ void __launch_bounds__(256) gen_zipf_kernel(void* out, u64 count, int item_bytes,
+                                                       u64 seed, uint32_t sid, u64 start,
+                                                       double s, int log2u) {
+  __shared__ pssg_tables tb;
+  __shared__ pssg_zipf zs;
+  for (int i = threadIdx.x; i < PSSG_LOG_TAB; i += blockDim.x) pssg_tables_entry(&tb, i);
+  __syncthreads();
+  if (threadIdx.x == 0) pssg_zipf_init(&zs, &tb, s, (log2u >= 64) ? ~0ull : (1ull << log2u));
+  __syncthreads();
+  const pssg_zipf z = zs;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-    const u64 x = pssg_zipf_item(&z, log2u, seed, sid, start + i);
+    const u64 x = pssg_zipf_item(&z, &tb, log2u, seed, sid, start + i);
     if (item_bytes == 4)
       ((uint32_t*)out)[i] = (uint32_t)x;
     else

@@ -29,9 +29,10 @@
  * operations +, -, *, / and explicit fused multiply-add (each correctly
  * rounded), and nothing else is contracted: device code goes through the
  * __d*_rn / __fma_rn intrinsics, host code uses C's fma and must be compiled
- * with -ffp-contract=off.  log and exp are this
- * file's own (range reduction plus series from the mathematics), so that no
- * platform libm enters the result.
+ * with -ffp-contract=off.  log and exp are this file's own (range reduction
+ * plus series from the mathematics), so that no platform libm enters the
+ * result; the sampler uses table-driven versions whose tables the accurate
+ * ones build (pssg_tables, identical on both sides).
  */
 #ifndef PSS_ZIPF_H_
 #define PSS_ZIPF_H_
@@ -158,55 +159,120 @@ PSSG_FN double pssg_exp(double x) {
   return PSSG_MUL(p, pssg_pow2((int)nd));
 }
 
-/* (e^t - 1) / t, continuous at t = 0 (value 1). */
-PSSG_FN double pssg_expm1_over(double t) {
-  if (t > -0.5 && t < 0.5) {
-    /* sum_{j>=0} t^j / (j+1)!, to t^19/20! */
-    double p = 1.0 / 2432902008176640000.0; /* 1/20! */
-    p = PSSG_FMA(p, t, 1.0 / 121645100408832000.0);
-    p = PSSG_FMA(p, t, 1.0 / 6402373705728000.0);
-    p = PSSG_FMA(p, t, 1.0 / 355687428096000.0);
-    p = PSSG_FMA(p, t, 1.0 / 20922789888000.0);
-    p = PSSG_FMA(p, t, 1.0 / 1307674368000.0);
-    p = PSSG_FMA(p, t, 1.0 / 87178291200.0);
-    p = PSSG_FMA(p, t, 1.0 / 6227020800.0);
-    p = PSSG_FMA(p, t, 1.0 / 479001600.0);
-    p = PSSG_FMA(p, t, 1.0 / 39916800.0);
-    p = PSSG_FMA(p, t, 1.0 / 3628800.0);
-    p = PSSG_FMA(p, t, 1.0 / 362880.0);
-    p = PSSG_FMA(p, t, 1.0 / 40320.0);
-    p = PSSG_FMA(p, t, 1.0 / 5040.0);
-    p = PSSG_FMA(p, t, 1.0 / 720.0);
-    p = PSSG_FMA(p, t, 1.0 / 120.0);
-    p = PSSG_FMA(p, t, 1.0 / 24.0);
-    p = PSSG_FMA(p, t, 1.0 / 6.0);
-    p = PSSG_FMA(p, t, 0.5);
-    p = PSSG_FMA(p, t, 1.0);
-    return p;
+/* ------------------------------------------- table-driven log and exp
+ *
+ * The sampler's log and exp: the same mathematics with a finer range
+ * reduction, so that short polynomials and no division suffice.
+ *   log x: x = 2^e f, f in [1, 2); c_j = 1 + (j + 1/2)/128 for the top seven
+ *     bits j of f; log x = e log 2 + log c_j + log(1 + d), d = f/c_j - 1 =
+ *     fma(f, 1/c_j, -1), |d| <= 2^-8, series of log(1 + d) to d^7 (the next
+ *     term is below 2^-59 relative).
+ *   exp x: x = m L + r with L = log 2 / 64 and |r| <= L/2; exp x = 2^(m div 64)
+ *     exp((m mod 64) L) e^r, series of e^r - 1 to r^6 (next term < 2e-20).
+ * The tables hold 1/c_j (a correctly rounded quotient), log c_j and
+ * exp(j L), each computed by this file's own pssg_log / pssg_exp above, so
+ * host and device build identical tables. */
+
+#define PSSG_LOG_TAB 128
+#define PSSG_EXP_TAB 64
+#define PSSG_L_HI 0x1.62e42fee00000p-7  /* PSSG_LN2_HI / 64 */
+#define PSSG_L_LO 0x1.a39ef35793c76p-39 /* PSSG_LN2_LO / 64 */
+#define PSSG_INV_L 0x1.71547652b82fep+6 /* 64 / ln 2 */
+
+typedef struct {
+  double rc[PSSG_LOG_TAB]; /* 1 / c_j */
+  double lc[PSSG_LOG_TAB]; /* log c_j */
+  double t2[PSSG_EXP_TAB]; /* exp(j L) */
+} pssg_tables;
+
+/* Entry i of every table that has one (i < PSSG_LOG_TAB covers all). */
+PSSG_FN void pssg_tables_entry(pssg_tables* tb, int i) {
+  if (i < PSSG_LOG_TAB) {
+    double c = PSSG_ADD(1.0, PSSG_MUL(PSSG_ADD((double)i, 0.5), 0x1p-7)); /* exact */
+    tb->rc[i] = PSSG_DIV(1.0, c);
+    tb->lc[i] = pssg_log(c);
   }
-  return PSSG_DIV(PSSG_SUB(pssg_exp(t), 1.0), t);
+  if (i < PSSG_EXP_TAB) {
+    double di = (double)i;
+    tb->t2[i] = pssg_exp(PSSG_ADD(PSSG_MUL(di, PSSG_L_HI), PSSG_MUL(di, PSSG_L_LO)));
+  }
 }
 
-/* log(1 + t) / t for t > -1, continuous at t = 0 (value 1). */
-PSSG_FN double pssg_log1p_over(double t) {
-  if (t > -0.01 && t < 0.01) {
-    /* sum_{j>=0} (-t)^j / (j+1), to t^9/10 */
-    double p = -1.0 / 10.0;
-    p = PSSG_FMA(p, t, 1.0 / 9.0);
-    p = PSSG_FMA(p, t, -1.0 / 8.0);
-    p = PSSG_FMA(p, t, 1.0 / 7.0);
-    p = PSSG_FMA(p, t, -1.0 / 6.0);
-    p = PSSG_FMA(p, t, 1.0 / 5.0);
-    p = PSSG_FMA(p, t, -1.0 / 4.0);
-    p = PSSG_FMA(p, t, 1.0 / 3.0);
-    p = PSSG_FMA(p, t, -1.0 / 2.0);
-    p = PSSG_FMA(p, t, 1.0);
-    return p;
-  }
-  /* log1p(t) = log(u) - ((u - 1) - t) / u with u = 1 + t (Goldberg 1991). */
-  double u = PSSG_ADD(1.0, t);
-  double l = PSSG_SUB(pssg_log(u), PSSG_DIV(PSSG_SUB(PSSG_SUB(u, 1.0), t), u));
-  return PSSG_DIV(l, t);
+PSSG_FN void pssg_tables_init(pssg_tables* tb) {
+  for (int i = 0; i < PSSG_LOG_TAB; ++i) pssg_tables_entry(tb, i);
+}
+
+/* log of a positive normal x; with cu != 0, log(x) + cu where cu is a
+ * correction far below ulp(x) (used by log1p). */
+PSSG_FN double pssg_log_tc(const pssg_tables* tb, double x, double c) {
+  uint64_t b = pssg_bits(x);
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
+  int j = (int)(mant >> 45);
+  double f = pssg_from_bits(mant | 0x3FF0000000000000ull);
+  double d = PSSG_FMA(f, tb->rc[j], -1.0);
+  /* log(1 + d) = d + d^2 (-1/2 + d/3 - d^2/4 + d^3/5 - d^4/6 + d^5/7) */
+  double q = 1.0 / 7.0;
+  q = PSSG_FMA(q, d, -1.0 / 6.0);
+  q = PSSG_FMA(q, d, 1.0 / 5.0);
+  q = PSSG_FMA(q, d, -1.0 / 4.0);
+  q = PSSG_FMA(q, d, 1.0 / 3.0);
+  q = PSSG_FMA(q, d, -0.5);
+  double l1 = PSSG_FMA(PSSG_MUL(d, d), q, d);
+  /* c / x with 1/x ~ rc_j 2^-e (c is tiny: the approximation is ample) */
+  l1 = PSSG_FMA(c, PSSG_MUL(tb->rc[j], pssg_pow2(-e)), l1);
+  double de = (double)e;
+  return PSSG_ADD(PSSG_FMA(de, PSSG_LN2_HI, tb->lc[j]), PSSG_FMA(de, PSSG_LN2_LO, l1));
+}
+
+PSSG_FN double pssg_log_t(const pssg_tables* tb, double x) { return pssg_log_tc(tb, x, 0.0); }
+
+/* exp(x) for |x| < 700 */
+PSSG_FN double pssg_exp_t(const pssg_tables* tb, double x) {
+  double md = pssg_floor(PSSG_FMA(x, PSSG_INV_L, 0.5));
+  double r = PSSG_SUB(PSSG_SUB(x, PSSG_MUL(md, PSSG_L_HI)), PSSG_MUL(md, PSSG_L_LO));
+  int64_t m = (int64_t)md;
+  int j = (int)(m & 63);
+  int n = (int)((m - j) / 64);
+  double p = 1.0 / 720.0;
+  p = PSSG_FMA(p, r, 1.0 / 120.0);
+  p = PSSG_FMA(p, r, 1.0 / 24.0);
+  p = PSSG_FMA(p, r, 1.0 / 6.0);
+  p = PSSG_FMA(p, r, 0.5);
+  double em1 = PSSG_FMA(PSSG_MUL(r, r), p, r);
+  double t = tb->t2[j];
+  return PSSG_MUL(PSSG_FMA(t, em1, t), pssg_pow2(n));
+}
+
+/* log(1 + t) / t for |t| < 2^-6 (value 1 at t = 0), series to t^9/10 (next
+ * term < 2^-57) */
+PSSG_FN double pssg_log1p_over_small(double t) {
+  double p = -1.0 / 10.0;
+  p = PSSG_FMA(p, t, 1.0 / 9.0);
+  p = PSSG_FMA(p, t, -1.0 / 8.0);
+  p = PSSG_FMA(p, t, 1.0 / 7.0);
+  p = PSSG_FMA(p, t, -1.0 / 6.0);
+  p = PSSG_FMA(p, t, 1.0 / 5.0);
+  p = PSSG_FMA(p, t, -1.0 / 4.0);
+  p = PSSG_FMA(p, t, 1.0 / 3.0);
+  p = PSSG_FMA(p, t, -1.0 / 2.0);
+  return PSSG_FMA(p, t, 1.0);
+}
+
+/* (e^w - 1) / w for |w| < 2^-5 (value 1 at w = 0), series to w^9/10! (next
+ * term < 2^-60) */
+PSSG_FN double pssg_expm1_over_small(double w) {
+  double p = 1.0 / 39916800.0;
+  p = PSSG_FMA(p, w, 1.0 / 3628800.0);
+  p = PSSG_FMA(p, w, 1.0 / 362880.0);
+  p = PSSG_FMA(p, w, 1.0 / 40320.0);
+  p = PSSG_FMA(p, w, 1.0 / 5040.0);
+  p = PSSG_FMA(p, w, 1.0 / 720.0);
+  p = PSSG_FMA(p, w, 1.0 / 120.0);
+  p = PSSG_FMA(p, w, 1.0 / 24.0);
+  p = PSSG_FMA(p, w, 1.0 / 6.0);
+  p = PSSG_FMA(p, w, 0.5);
+  return PSSG_FMA(p, w, 1.0);
 }
 
 /* ------------------------------------------------ Zipf by rejection-inversion */
@@ -214,53 +280,61 @@ PSSG_FN double pssg_log1p_over(double t) {
 typedef struct {
   double s;        /* exponent, s > 0 */
   double one_m_s;  /* 1 - s */
+  double inv_1ms;  /* 1 / (1 - s), 0 when s = 1 */
   double h_x1;     /* H(3/2) - h(1): left end of the sampled interval */
   double h_n;      /* H(N + 1/2): right end */
   double squeeze;  /* k - x <= squeeze accepts without evaluating H and h */
   uint64_t n;      /* number of ranks N = U */
 } pssg_zipf;
 
-/* H(x) = integral of t^-s from 1 to x = log(x) * expm1((1-s) log x) / ((1-s) log x) */
-PSSG_FN double pssg_zipf_H(const pssg_zipf* z, double x) {
-  double lx = pssg_log(x);
-  return PSSG_MUL(lx, pssg_expm1_over(PSSG_MUL(z->one_m_s, lx)));
+/* H(x) = integral of t^-s from 1 to x = (x^(1-s) - 1) / (1 - s) (log x at s = 1) */
+PSSG_FN double pssg_zipf_H(const pssg_zipf* z, const pssg_tables* tb, double x) {
+  double lx = pssg_log_t(tb, x);
+  double w = PSSG_MUL(z->one_m_s, lx);
+  if (w > -0x1p-5 && w < 0x1p-5) return PSSG_MUL(lx, pssg_expm1_over_small(w));
+  return PSSG_MUL(PSSG_SUB(pssg_exp_t(tb, w), 1.0), z->inv_1ms);
 }
 
-/* H^-1(y) = exp(y * log1p((1-s) y) / ((1-s) y)) */
-PSSG_FN double pssg_zipf_Hinv(const pssg_zipf* z, double y) {
-  return pssg_exp(PSSG_MUL(y, pssg_log1p_over(PSSG_MUL(z->one_m_s, y))));
+/* H^-1(y) = exp(log(1 + (1-s) y) / (1 - s)) (exp y at s = 1) */
+PSSG_FN double pssg_zipf_Hinv(const pssg_zipf* z, const pssg_tables* tb, double y) {
+  double t = PSSG_MUL(z->one_m_s, y);
+  if (t > -0x1p-6 && t < 0x1p-6) return pssg_exp_t(tb, PSSG_MUL(y, pssg_log1p_over_small(t)));
+  double u = PSSG_ADD(1.0, t);
+  double c = PSSG_SUB(t, PSSG_SUB(u, 1.0)); /* the rounding error of u */
+  return pssg_exp_t(tb, PSSG_MUL(pssg_log_tc(tb, u, c), z->inv_1ms));
 }
 
 /* h(x) = x^-s */
-PSSG_FN double pssg_zipf_h(const pssg_zipf* z, double x) {
-  return pssg_exp(PSSG_MUL(-z->s, pssg_log(x)));
+PSSG_FN double pssg_zipf_h(const pssg_zipf* z, const pssg_tables* tb, double x) {
+  return pssg_exp_t(tb, PSSG_MUL(-z->s, pssg_log_t(tb, x)));
 }
 
-PSSG_FN double pssg_zipf_Hinv(const pssg_zipf* z, double y);
-
-PSSG_FN void pssg_zipf_init(pssg_zipf* z, double s, uint64_t n) {
+PSSG_FN void pssg_zipf_init(pssg_zipf* z, const pssg_tables* tb, double s, uint64_t n) {
   z->s = s;
   z->one_m_s = PSSG_SUB(1.0, s);
+  z->inv_1ms = z->one_m_s == 0.0 ? 0.0 : PSSG_DIV(1.0, z->one_m_s);
   z->n = n;
-  z->h_x1 = PSSG_SUB(pssg_zipf_H(z, 1.5), 1.0);
-  z->h_n = pssg_zipf_H(z, PSSG_ADD((double)n, 0.5));
+  z->h_x1 = PSSG_SUB(pssg_zipf_H(z, tb, 1.5), 1.0);
+  z->h_n = pssg_zipf_H(z, tb, PSSG_ADD((double)n, 0.5));
   /* the quick acceptance bound of rejection-inversion: 2 - H^-1(H(5/2) - h(2)) */
-  z->squeeze = PSSG_SUB(2.0, pssg_zipf_Hinv(z, PSSG_SUB(pssg_zipf_H(z, 2.5), pssg_zipf_h(z, 2.0))));
+  z->squeeze = PSSG_SUB(2.0, pssg_zipf_Hinv(z, tb, PSSG_SUB(pssg_zipf_H(z, tb, 2.5),
+                                                           pssg_zipf_h(z, tb, 2.0))));
 }
 
-/* One rejection-inversion attempt with uniform u; returns 0 on rejection,
- * else the rank in [1, N].  The accepted part of the cell of rank k is
+/* One attempt with uniform u: 0 if rejected, else the rank in [1, N].  The
+ * sampled variable is y uniform on (H(N + 1/2), H(3/2) - h(1)]; x = H^-1(y),
+ * k = the integer nearest x.  The accepted part of the cell of rank k is
  * [H(k+1/2) - h(k), H(k+1/2)], of length h(k), so P(k) is proportional to k^-s. */
-PSSG_FN uint64_t pssg_zipf_try(const pssg_zipf* z, double u) {
+PSSG_FN uint64_t pssg_zipf_try(const pssg_zipf* z, const pssg_tables* tb, double u) {
   double y = PSSG_ADD(z->h_n, PSSG_MUL(u, PSSG_SUB(z->h_x1, z->h_n)));
-  double x = pssg_zipf_Hinv(z, y);
+  double x = pssg_zipf_Hinv(z, tb, y);
   double kd = pssg_floor(PSSG_ADD(x, 0.5));
   if (kd < 1.0) kd = 1.0;
   if (kd > (double)z->n) kd = (double)z->n;
   uint64_t k = (uint64_t)kd;
   double kk = (double)k;
   if (PSSG_SUB(kk, x) <= z->squeeze) return k;
-  if (y >= PSSG_SUB(pssg_zipf_H(z, PSSG_ADD(kk, 0.5)), pssg_zipf_h(z, kk))) return k;
+  if (y >= PSSG_SUB(pssg_zipf_H(z, tb, PSSG_ADD(kk, 0.5)), pssg_zipf_h(z, tb, kk))) return k;
   return 0;
 }
 
@@ -269,13 +343,14 @@ PSSG_FN uint64_t pssg_zipf_try(const pssg_zipf* z, double u) {
 /* Rank of item index i of stream `stream` under `seed`.  After
  * PSSG_MAX_ATTEMPTS rejections (probability far below 1e-40) rank 1 is
  * returned, identically on both sides. */
-PSSG_FN uint64_t pssg_zipf_rank(const pssg_zipf* z, uint64_t seed, uint32_t stream, uint64_t i) {
+PSSG_FN uint64_t pssg_zipf_rank(const pssg_zipf* z, const pssg_tables* tb, uint64_t seed,
+                                uint32_t stream, uint64_t i) {
   for (uint32_t a = 0; a < PSSG_MAX_ATTEMPTS; a += 2) {
     uint32_t c[4] = {(uint32_t)i, (uint32_t)(i >> 32), stream, a >> 1};
     pssg_philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
-    uint64_t k = pssg_zipf_try(z, pssg_u01(c[0], c[1]));
+    uint64_t k = pssg_zipf_try(z, tb, pssg_u01(c[0], c[1]));
     if (k) return k;
-    k = pssg_zipf_try(z, pssg_u01(c[2], c[3]));
+    k = pssg_zipf_try(z, tb, pssg_u01(c[2], c[3]));
     if (k) return k;
   }
   return 1;
@@ -294,9 +369,9 @@ PSSG_FN uint64_t pssg_rank_to_item(uint64_t r, int b) {
 }
 
 /* Item i of the stream (seed, stream, s, U = 2^log2u). */
-PSSG_FN uint64_t pssg_zipf_item(const pssg_zipf* z, int log2u, uint64_t seed, uint32_t stream,
-                                uint64_t i) {
-  return pssg_rank_to_item(pssg_zipf_rank(z, seed, stream, i), log2u);
+PSSG_FN uint64_t pssg_zipf_item(const pssg_zipf* z, const pssg_tables* tb, int log2u,
+                                uint64_t seed, uint32_t stream, uint64_t i) {
+  return pssg_rank_to_item(pssg_zipf_rank(z, tb, seed, stream, i), log2u);
 }
 
 #endif /* PSS_ZIPF_H_ */

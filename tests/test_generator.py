@@ -29,6 +29,24 @@ def test_log_exp_accuracy():
         assert abs(oracle.gen_exp(float(y)) - math.exp(y)) <= 3e-15 * math.exp(y)
 
 
+def test_table_log_exp_accuracy():
+    # The sampler's table-driven log and exp against the math library, over
+    # wide ranges, every table cell (x = 2^e (1 + j/128 + ...)) and near 1.
+    rng = np.random.default_rng(2)
+    xs = np.concatenate([rng.uniform(1e-6, 1e6, 2000), np.exp(rng.uniform(-40, 44, 2000)),
+                         1 + (np.arange(128) + rng.random(128)) / 128,
+                         1 - rng.uniform(0, 1e-3, 200), 1 + rng.uniform(0, 1e-3, 200),
+                         [0.5, 1.0, 2.0, 2 ** 32 + 0.5, 1.5, 2 ** 64]])
+    for x in xs:
+        ref = math.log(x)
+        assert abs(oracle.gen_log_t(float(x)) - ref) <= 4e-16 * max(1.0, abs(ref)), x
+    ys = np.concatenate([rng.uniform(-88, 45, 3000), np.arange(-64, 65) * math.log(2) / 64,
+                         [0.0, 1.0, -1.0, 22.2, 1e-12, -1e-12]])
+    for y in ys:
+        ref = math.exp(y)
+        assert abs(oracle.gen_exp_t(float(y)) - ref) <= 3e-15 * ref, y
+
+
 @pytest.mark.parametrize("s", [0.5, 1.0, 1.1, 1.8, 3.0])
 def test_zipf_law(s):
     # Chi-square goodness of fit of the ranks to P(r) ~ r^-s on [1, N].
