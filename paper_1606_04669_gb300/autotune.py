@@ -27,17 +27,18 @@ import time
 
 K_CLASSES = (64, 256, 1024, 4096)
 SKEW_CLASSES = (0.8, 1.4, 2.0)
-LENGTHS = (1 << 16, 1 << 17, 1 << 18, 1 << 19)
+LENGTHS = (1 << 15, 1 << 16, 1 << 17, 1 << 18, 1 << 19)
 
-# Measured by sweep() on a GB300 (2048 blocks per point, u64 items): the
-# block length with the highest items/s for each (k class, skew class).
-# Longer blocks won everywhere, by 1-24% over 2^16 (the per-block fixed work
-# -- table set-up, final sort, summary write -- is amortized over more items).
+# Measured by sweep() on a GB300 (one stream of 2^27 u64 items per point,
+# through the batch path): the block length with the highest items/s for each
+# (k class, skew class).  Short blocks win for small k (more blocks in flight,
+# and the warp kernel's per-block work is small); k = 4096 (one CTA per SM)
+# prefers 2^17, where the per-block set-up and output are amortized.
 TABLE = {
-    64: {0.8: 1 << 19, 1.4: 1 << 19, 2.0: 1 << 19},
-    256: {0.8: 1 << 19, 1.4: 1 << 19, 2.0: 1 << 19},
-    1024: {0.8: 1 << 19, 1.4: 1 << 19, 2.0: 1 << 19},
-    4096: {0.8: 1 << 19, 1.4: 1 << 19, 2.0: 1 << 19},
+    64: {0.8: 1 << 15, 1.4: 1 << 15, 2.0: 1 << 15},
+    256: {0.8: 1 << 15, 1.4: 1 << 15, 2.0: 1 << 15},
+    1024: {0.8: 1 << 15, 1.4: 1 << 16, 2.0: 1 << 16},
+    4096: {0.8: 1 << 17, 1.4: 1 << 17, 2.0: 1 << 17},
 }
 
 
@@ -77,25 +78,25 @@ def _time_batch(P, torch, x, k, p, skew, steps):
     return e0.elapsed_time(e1) / steps
 
 
-def sweep(blocks: int = 2048, item_bytes: int = 8, steps: int = 3, seed: int = 77):
-    """Items/s of the batch path for every (k, skew, length), each with the same
-    number of blocks (so that only the block length changes); returns
-    (results, table).  Runs on the current CUDA device."""
+def sweep(n: int = 1 << 27, item_bytes: int = 8, steps: int = 3, seed: int = 77):
+    """Items/s of the batch path for one stream of n items (about the largest
+    stream of the batched workload) for every (k, skew, block length), so
+    that the length trades per-block fixed work against the number of blocks
+    in flight; returns (results, table).  Runs on the current CUDA device."""
     import torch
 
     import paper_1606_04669_gb300 as P
     results, table = [], {}
-    nmax = blocks * max(LENGTHS)
     for zs in SKEW_CLASSES:
-        x = P.gen_zipf(nmax, seed=seed, s=zs, log2u=32, item_bytes=item_bytes)
+        x = P.gen_zipf(n, seed=seed, s=zs, log2u=32, item_bytes=item_bytes)
         for k in K_CLASSES:
             table.setdefault(k, {})
             best = None
             for length in LENGTHS:
-                n = blocks * length
-                ms = _time_batch(P, torch, x[:n], k, blocks, zs, steps)
+                p = (n + length - 1) // length
+                ms = _time_batch(P, torch, x, k, p, zs, steps)
                 rate = n / (ms / 1e3)
-                results.append({"k": k, "skew": zs, "block_length": length, "p": blocks, "ms": ms,
+                results.append({"k": k, "skew": zs, "block_length": length, "p": p, "ms": ms,
                                 "items_per_s": rate})
                 if best is None or rate > best[1]:
                     best = (length, rate)
