@@ -35,8 +35,8 @@ inline cudaError_t ensure_kernel_attrs(const void* kern) {
   return e;
 }
 
-constexpr int SS_BS = 256;     // threads per CTA of the summarize kernel
-constexpr int SS_IPT = 4;      // items per thread per window (window = SS_BS * SS_IPT)
+constexpr int SS_BS = 512;     // threads per CTA of the summarize kernel
+constexpr int SS_IPT = 2;      // items per thread per window (window = SS_BS * SS_IPT)
 constexpr int MERGE_BS = 512;  // threads per CTA of the combine kernel
 constexpr int CANON_BS = 1024; // threads per CTA of the query/export kernel
 

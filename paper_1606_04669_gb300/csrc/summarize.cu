@@ -1008,7 +1008,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
 }
 
 template <typename ItemT, int BS, int IPT>
-__global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ items, u64 n,
+__global__ void __launch_bounds__(BS, 2) ss_block_kernel(const ItemT* __restrict__ items, u64 n,
                                                       uint32_t p, uint32_t r0,
                                                       SetView<ItemT> out, uint32_t node0) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1020,7 +1020,7 @@ __global__ void __launch_bounds__(BS) ss_block_kernel(const ItemT* __restrict__ 
 // a shared counter until the list is exhausted.  Tasks are listed longest
 // block first so that the last wave is short.
 template <typename ItemT, int BS, int IPT>
-__global__ void __launch_bounds__(BS) ss_batch_kernel(const BatchStream* __restrict__ streams,
+__global__ void __launch_bounds__(BS, 2) ss_batch_kernel(const BatchStream* __restrict__ streams,
                                                       const BatchTask* __restrict__ tasks,
                                                       uint32_t ntasks, uint32_t* counter) {
   extern __shared__ __align__(16) unsigned char smem[];
