@@ -186,10 +186,13 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   L.convsrc = (uint16_t*)take(2ull * CONVMAX);
   L.convfrom = (uint16_t*)take(2ull * CONVMAX);
   L.convto = (uint16_t*)take(2ull * CONVMAX);
-  // The rebuild sort reuses the window scratch.
-  L.rkey = (uint32_t*)(base + u0);
-  L.rpay = (uint16_t*)(base + u0 + align16(4ull * L.SORTN));
-  const size_t sort_end = u0 + align16(4ull * L.SORTN) + align16(2ull * L.SORTN);
+  // The rebuild sort reuses the window scratch
+  // (after wbuf, which holds the next window's items, copied in during the
+  // window's last phases)
+  const size_t s0 = u0 + align16(sizeof(ItemT) * W);
+  L.rkey = (uint32_t*)(base + s0);
+  L.rpay = (uint16_t*)(base + s0 + align16(4ull * L.SORTN));
+  const size_t sort_end = s0 + align16(4ull * L.SORTN) + align16(2ull * L.SORTN);
   if (sort_end > off) off = sort_end;
   // The final sort reuses everything after touch (the state is dead by then).
   L.fkey = (u64*)(base + after_touch);
@@ -486,6 +489,30 @@ struct SSBlock {
   }
 };
 
+// Asynchronous copy of items [t, t + W) of xs (those below len; zeros past it)
+// into wbuf, one element per copy (a window may start at any item).  Every
+// thread issues its share; cp_wait() + a barrier make the window visible.
+template <typename ItemT, int BS, int IPT>
+__device__ __forceinline__ void copy_window(ItemT* wbuf, const ItemT* __restrict__ xs, uint32_t t,
+                                            uint32_t len) {
+  constexpr uint32_t W = BS * IPT;
+  for (uint32_t i = threadIdx.x; i < W; i += BS) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(wbuf + i);
+    const bool in = t + i < len;
+    const ItemT* src = xs + (in ? t + i : 0u);
+    const uint32_t n = in ? (uint32_t)sizeof(ItemT) : 0u;
+    if (sizeof(ItemT) == 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(n)
+                   : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(n)
+                   : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // The summary of block r of p (Algorithm 1 bounds over n items) into node
 // `node` of `out`; called by all threads of the CTA.
 template <typename ItemT, int BS, int IPT>
@@ -529,31 +556,18 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   }
   __syncthreads();
 
-  ItemT nx[IPT];
-  bool have_next = false;
+  // The window's items sit in wbuf (pending cells name them by position);
+  // the next window is copied in as soon as its start is known.
   uint32_t t0 = 0;
+  if (len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, 0, len);
   while (t0 < len) {
     const uint32_t nact = min(W, len - t0);
+    cp_wait();
+    __syncthreads();
     ItemT x[IPT];
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t rel = tid * IPT + j;
-      x[j] = have_next ? nx[j] : (rel < nact ? xs[t0 + rel] : (ItemT)0);
-    }
-    // Prefetch the next window on the assumption that this one is not cut.
-    have_next = t0 + W < len;
-    if (have_next) {
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint32_t t = t0 + W + tid * IPT + j;
-        nx[j] = t < len ? xs[t] : (ItemT)0;
-      }
-    }
+    for (int j = 0; j < IPT; ++j) x[j] = s.wbuf[tid * IPT + j];
     const uint32_t full = S.full, m = S.m;
-    // the window's items, for pending cells (which name them by position)
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) s.wbuf[tid * IPT + j] = x[j];
-    __syncthreads();
 
     // ---- P1: look up or claim; first hit of bucket members; first occurrence of misses
     int sl[IPT];                  // slot, or -2 - pid for a pending item
@@ -632,14 +646,13 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     // Hits on counters outside the minimum bucket commute with everything:
     // a window of those only just adds its occurrences.
     if (!__syncthreads_or((miss | mhit) != 0)) {
+      if (t0 + nact < len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, t0 + nact, len);
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const uint32_t rel = tid * IPT + j;
         B.add_occurrence(rel < nact ? (uint32_t)sl[j] : NONE32, t0 + rel);
       }
-      __syncthreads();
       t0 += nact;
-      if (nact < W) have_next = false;
       continue;
     }
 
@@ -885,6 +898,9 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       s.logpos[ctime] = (uint16_t)(cvict + 1);
     }
     __syncthreads();
+    // the next window starts at the cut: its items come in while the
+    // remaining phases run (nothing reads wbuf from here on)
+    if (t0 + cut < len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, t0 + cut, len);
 
     // ---- P8: every occurrence before the cut adds one to its counter
 #pragma unroll
@@ -969,9 +985,10 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       break;
     }
     __syncthreads();
-    if (cut < W) have_next = false;
     t0 += cut;
   }
+  cp_wait();  // a copy may be in flight after an error exit
+
 
   // ---- output: the summary sorted by item ascending
   if (status) atomicOr(&S.status, status);
