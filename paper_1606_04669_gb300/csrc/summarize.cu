@@ -83,7 +83,7 @@ struct SSState {
   uint32_t used;         // counters in use
   uint32_t full;         // used == k
   uint32_t epoch_start;  // position at which the current bucket list was built
-  uint32_t nvalid, nhit, j0;  // candidate compaction
+  uint32_t nvalid, nhit;  // candidate compaction
   uint32_t nskip, nconv, astop;
   uint32_t cut;          // exact prefix of the window
   uint32_t exhausted;
@@ -239,10 +239,31 @@ struct SSBlock {
   uint32_t k;
   uint32_t par;  // scan scratch parity
 
+  // Exclusive block scan with one barrier: every warp scans the warp totals
+  // itself.  Consecutive scans alternate two buffers, so the barrier of the
+  // next scan separates a buffer's reads from its next writes.
   __device__ __forceinline__ uint32_t scan(uint32_t v, uint32_t* total) {
     uint32_t* buf = s.wsum + (par ? (BS / 32 + 1) : 0);
     par ^= 1;
-    return block_exclusive_scan<BS>(v, buf, total);
+    constexpr int NW = BS / 32;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) buf[warp] = x;
+    __syncthreads();
+    uint32_t w = lane < (uint32_t)NW ? buf[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= (uint32_t)o) w += y;
+    }
+    const uint32_t before = __shfl_sync(0xffffffffu, w, (warp + 31) & 31);
+    *total = __shfl_sync(0xffffffffu, w, NW - 1);
+    return (warp ? before : 0u) + x - v;
   }
 
   __device__ __forceinline__ bool ovf_bit(uint32_t half, uint32_t b) const {
@@ -568,6 +589,17 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
 #pragma unroll
     for (int j = 0; j < IPT; ++j) x[j] = s.wbuf[tid * IPT + j];
     const uint32_t full = S.full, m = S.m;
+    // per-window state: written here, first read after the lookup's barrier
+    if (tid == 0) {
+      S.cut = nact;
+      S.exhausted = 0;
+      S.nvalid = 0;
+      S.nhit = 0;
+      S.nskip = 0;
+      S.nconv = 0;
+      S.astop = NONE32;
+      S.need = 0;
+    }
 
     // ---- P1: look up or claim; first hit of bucket members; first occurrence of misses
     int sl[IPT];                  // slot, or -2 - pid for a pending item
@@ -677,24 +709,14 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
         }
       }
     }
-    if (tid == 0) {
-      S.cut = nact;
-      S.exhausted = 0;
-      S.nvalid = 0;
-      S.nhit = 0;
-      S.j0 = S.head;
-      S.nskip = 0;
-      S.nconv = 0;
-      S.astop = NONE32;
-      S.need = 0;
-    }
-    __syncthreads();
 
-    // ---- P3: the bucket members still at count m, in list order
+    // ---- P3: the bucket members still at count m, in list order (the scan
+    // totals give every thread the running counts)
     bool list_end = false;
     if (full && M > 0) {
+      uint32_t nv = 0, nh = 0, j0 = S.head;
+      const uint32_t ll = S.list_len;
       for (;;) {
-        const uint32_t nv = S.nvalid, nh = S.nhit, j0 = S.j0, ll = S.list_len;
         if (nv >= M + 2 * nh + 1) break;
         if (j0 >= ll) {
           list_end = true;
@@ -717,14 +739,16 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
           s.candidx[a] = (uint16_t)j;
           if (hit) s.hitc[nh + (ex >> 16)] = (uint16_t)a;
         }
-        if (tid == 0) {
-          S.nvalid = nv + (tt & 0xFFFFu);
-          S.nhit = nh + (tt >> 16);
-          S.j0 = j0 + BS;
-        }
-        __syncthreads();
+        nv += tt & 0xFFFFu;
+        nh += tt >> 16;
+        j0 += BS;
+      }
+      if (tid == 0) {
+        S.nvalid = nv;
+        S.nhit = nh;
       }
     }
+    __syncthreads();
 
     // ---- P4: one warp walks the members hit in this window (skips, conversions)
     if (full && M > 0 && warp == 0) {
