@@ -567,7 +567,12 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
 
   for (uint32_t i = tid; i < 4 * s.NB; i += BS) s.cell[i] = 0;
   for (uint32_t i = tid; i < 2 * s.NBW; i += BS) s.ovf[i] = 0;
-  for (uint32_t i = tid; i < k; i += BS) s.hfirst[i] = NONE32;
+  // counters start at 0 (a fresh slot is never written before it counts)
+  for (uint32_t i = tid; i < k; i += BS) {
+    s.hfirst[i] = NONE32;
+    s.cnt[i] = 0;
+    s.touch[i] = 0;
+  }
   // err of slot q is kept in the output node (written once per insertion)
   u64* __restrict__ gerr = out.err + obase;
   B.reset_window_scratch();
@@ -881,14 +886,21 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
         atomicMin(&S.cut, ctime);
         if (can_exhaust) S.exhausted = 1;
       }
+      // occurrences of the evicted member's item go to the new slot
+      s.convfrom[tid] = (uint16_t)csrc;
+      s.convto[tid] = a < limit ? (uint16_t)cvict : NONE16;
     }
     __syncthreads();
     const uint32_t cut = S.cut;
 
-    // ---- P6: commit the events before the cut: each victim's cell is freed and
-    // the event's claimed cell names the victim, whose counter starts at m
-    // (the occurrences are added next); claims past the cut are dropped.
-    // Every cell here has one writer; conversions claim cells that are free.
+    // ---- P6: commit the events before the cut and count every occurrence
+    // before it.  A victim's counter is already at m (it was not hit before
+    // its eviction, or it would have been skipped) and every new item occurs
+    // before the cut, which raises its touch above the victim's, so the
+    // commit writes neither count nor touch and the counting needs no
+    // barrier after it.  Each victim's cell is freed and the event's claimed
+    // cell names the victim; claims past the cut are dropped.  Every cell has
+    // one writer; conversions claim cells that are free.
     for (uint32_t r = tid; r < M; r += BS) {
       const uint32_t pid = s.evpid[r], rel = s.rankpos[r];
       const uint32_t pc = s.pcell[pid];
@@ -903,30 +915,16 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
         s.cellof[v] = (uint16_t)pc;
       }
       s.item[v] = s.wbuf[pid];
-      s.cnt[v] = full ? m : 0u;
       gerr[v] = full ? m : 0u;
-      s.touch[v] = 0;
       if (full) s.logpos[rel] = (uint16_t)(v + 1);
-    }
-    if (tid < nconv) {
-      s.convfrom[tid] = (uint16_t)csrc;
-      s.convto[tid] = ctime < cut ? (uint16_t)cvict : NONE16;
     }
     if (tid < nconv && ctime < cut) {
       s.cell[s.cellof[cvict]] = 0u;
       B.insert(citem, cvict, status);
       s.item[cvict] = citem;
-      s.cnt[cvict] = m;
       gerr[cvict] = m;
-      s.touch[cvict] = 0;
       s.logpos[ctime] = (uint16_t)(cvict + 1);
     }
-    __syncthreads();
-    // the next window starts at the cut: its items come in while the
-    // remaining phases run (nothing reads wbuf from here on)
-    if (t0 + cut < len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, t0 + cut, len);
-
-    // ---- P8: every occurrence before the cut adds one to its counter
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const uint32_t rel = tid * IPT + j;
@@ -939,7 +937,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
           if (mhit >> j & 1) {
             uint32_t f = NONE16;  // the member was evicted: its item was re-inserted
             for (uint32_t c = 0; c < nconv; ++c)
-              if (s.convfrom[c] == tgt) f = s.convto[c];
+              if (s.convfrom[c] == tgt && s.convt[c] < cut) f = s.convto[c];
             if (f != NONE16) tgt = f;
             else if (s.hfirst[tgt] == rel) s.logpos[rel] = (uint16_t)(tgt + 1);  // m -> m + 1
           }
@@ -948,6 +946,9 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       B.add_occurrence(tgt, t0 + rel);
     }
     __syncthreads();
+    // the next window starts at the cut: its items come in while the
+    // remaining phases run (nothing reads wbuf from here on)
+    if (t0 + cut < len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, t0 + cut, len);
 
     // ---- P9: log in time order, reset the window scratch, advance
     uint32_t nl = 0;
