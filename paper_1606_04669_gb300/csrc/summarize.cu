@@ -87,9 +87,7 @@ struct SSState {
   uint32_t nskip, nconv, astop;
   uint32_t cut;          // exact prefix of the window
   uint32_t exhausted;
-  uint32_t need;         // 0 none, 1 incremental list rebuild, 2 full
   uint32_t maxdisp;      // largest distance of an item past its second bucket
-  uint32_t stall;
   uint32_t status;
 };
 
@@ -578,13 +576,13 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   B.reset_window_scratch();
   if (tid == 0) {
     S.m = 0; S.head = 0; S.list_len = 0; S.log_len = 0; S.used = 0; S.full = 0;
-    S.epoch_start = 0; S.maxdisp = 0; S.stall = 0; S.status = 0; S.need = 0;
+    S.epoch_start = 0; S.maxdisp = 0; S.status = 0;
   }
   __syncthreads();
 
   // The window's items sit in wbuf (pending cells name them by position);
   // the next window is copied in as soon as its start is known.
-  uint32_t t0 = 0;
+  uint32_t t0 = 0, stall = 0;
   if (len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, 0, len);
   while (t0 < len) {
     const uint32_t nact = min(W, len - t0);
@@ -603,7 +601,6 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       S.nskip = 0;
       S.nconv = 0;
       S.astop = NONE32;
-      S.need = 0;
     }
 
     // ---- P1: look up or claim; first hit of bucket members; first occurrence of misses
@@ -951,6 +948,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     if (t0 + cut < len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, t0 + cut, len);
 
     // ---- P9: log in time order, reset the window scratch, advance
+    const uint32_t log0 = S.log_len;  // read before the scan's barrier: warp 0 rewrites it
     uint32_t nl = 0;
     uint16_t lg[IPT];
 #pragma unroll
@@ -963,7 +961,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     uint32_t ltot;
     const uint32_t lbase = B.scan(nl, &ltot);
     {
-      uint32_t o = S.log_len + lbase;
+      uint32_t o = log0 + lbase;
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         if (lg[j] && tid * IPT + j < cut) {
@@ -977,39 +975,44 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       if (mhit >> j & 1) s.hfirst[sl[j]] = NONE32;
       s.ppos[tid * IPT + j] = NONE32;
     }
+    // The applied events are the prefix of the merged sequence before the cut.
+    // Every thread derives the rebuild decision itself (no barrier here; the
+    // rebuild's own barriers order warp 0's state updates before their use).
+    uint32_t norig = 0;
+    {
+      uint32_t hi = M;
+      while (norig < hi) {
+        const uint32_t mid = (norig + hi) >> 1;
+        if (s.rankpos[mid] < cut) norig = mid + 1;
+        else hi = mid;
+      }
+    }
+    const uint32_t need = full ? ((S.exhausted && cut < nact) ? 1u : 0u)
+                               : (used0 + norig == k ? 2u : 0u);
     if (warp == 0) {
-      // the applied events are the prefix of the merged sequence before the cut
-      const uint32_t norig = warp_lower_bound(s.rankpos, M, cut);
       const uint32_t nc = __popc(__ballot_sync(0xffffffffu, lane < nconv && s.convt[lane] < cut));
       const uint32_t nev = norig + nc;
       if (lane == 0) {
-        const uint32_t nlog = S.log_len + ltot;
+        const uint32_t nlog = log0 + ltot;
         S.log_len = nlog < k ? nlog : k;
         if (full) {
           if (nev) S.head = s.candidx[assign(nev - 1)] + 1u;
-          if (S.exhausted && cut < nact) S.need = 1;
         } else {
-          S.used += norig;
-          if (S.used == k) {
-            S.full = 1;
-            S.need = 2;
-          }
+          S.used = used0 + norig;
+          if (S.used == k) S.full = 1;
         }
-        S.stall = cut ? 0u : S.stall + 1u;
       }
     }
-    __syncthreads();
-    const uint32_t need = S.need;
+    stall = cut ? 0u : stall + 1u;
     if (need) {
       const bool clobbered = B.rebuild_list(need == 2, t0 + cut);
       if (S.maxdisp > 2) B.rebuild_table(status);
       if (clobbered) B.reset_window_scratch();
     }
-    if (S.stall >= 3) {
+    if (stall >= 3) {
       status |= ST_NOPROGRESS;
       break;
     }
-    __syncthreads();
     t0 += cut;
   }
   cp_wait();  // a copy may be in flight after an error exit
