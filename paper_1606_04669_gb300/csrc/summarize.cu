@@ -86,6 +86,7 @@ struct SSState {
   uint32_t nvalid, nhit;  // candidate compaction
   uint32_t nskip, nconv, astop;
   uint32_t cut;          // exact prefix of the window
+  uint32_t norig;        // events (not conversions) before the cut
   uint32_t exhausted;
   uint32_t maxdisp;      // largest distance of an item past its second bucket
   uint32_t status;
@@ -262,6 +263,36 @@ struct SSBlock {
     const uint32_t before = __shfl_sync(0xffffffffu, w, (warp + 31) & 31);
     *total = __shfl_sync(0xffffffffu, w, NW - 1);
     return (warp ? before : 0u) + x - v;
+  }
+
+  // The same scan for values made of single-bit fields (BITS marks the bit
+  // positions used): the warp part is one ballot per field.
+  template <uint32_t BITS>
+  __device__ __forceinline__ uint32_t scan_bits(uint32_t v, uint32_t* total) {
+    uint32_t* buf = s.wsum + (par ? (BS / 32 + 1) : 0);
+    par ^= 1;
+    constexpr int NW = BS / 32;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    uint32_t x = 0, wt = 0;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      if (!((BITS >> b) & 1u)) continue;
+      const unsigned bal = __ballot_sync(0xffffffffu, (v >> b) & 1u);
+      x += (uint32_t)__popc(bal & below) << b;
+      wt += (uint32_t)__popc(bal) << b;
+    }
+    if (lane == 0) buf[warp] = wt;
+    __syncthreads();
+    uint32_t w = lane < (uint32_t)NW ? buf[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= (uint32_t)o) w += y;
+    }
+    const uint32_t before = __shfl_sync(0xffffffffu, w, (warp + 31) & 31);
+    *total = __shfl_sync(0xffffffffu, w, NW - 1);
+    return (warp ? before : 0u) + x;
   }
 
   __device__ __forceinline__ bool ovf_bit(uint32_t half, uint32_t b) const {
@@ -539,6 +570,8 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
                                 const SetView<ItemT>& out, uint32_t node, unsigned char* smem,
                                 SSState& S_) {
   constexpr uint32_t W = BS * IPT;
+  // bit fields of a per-thread count in [0, IPT]
+  constexpr uint32_t kCountBits = IPT < 2 ? 1u : (IPT < 4 ? 3u : (IPT < 8 ? 7u : 15u));
   SSBlock<ItemT, BS, IPT> B;
   B.k = out.k;
   B.S = &S_;
@@ -601,6 +634,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       S.nskip = 0;
       S.nconv = 0;
       S.astop = NONE32;
+      S.norig = 0;
     }
 
     // ---- P1: look up or claim; first hit of bucket members; first occurrence of misses
@@ -691,15 +725,12 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     }
 
     // ---- P2: first occurrences of the misses (the events), ranked by position
-    uint32_t first = 0, nf = 0;
+    uint32_t first = 0;
 #pragma unroll
     for (int j = 0; j < IPT; ++j)
-      if ((miss >> j & 1) && s.ppos[-2 - sl[j]] == tid * IPT + j) {
-        first |= 1u << j;
-        ++nf;
-      }
+      if ((miss >> j & 1) && s.ppos[-2 - sl[j]] == tid * IPT + j) first |= 1u << j;
     uint32_t M;
-    const uint32_t rbase = B.scan(nf, &M);
+    const uint32_t rbase = B.template scan_bits<kCountBits>(__popc(first), &M);
     {
       uint32_t rr = rbase;
 #pragma unroll
@@ -734,7 +765,8 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
           hit = valid && s.hfirst[q] != NONE32;
         }
         uint32_t tt;
-        const uint32_t ex = B.scan((valid ? 1u : 0u) | (hit ? 0x10000u : 0u), &tt);
+        const uint32_t ex =
+            B.template scan_bits<0x10001u>((valid ? 1u : 0u) | (hit ? 0x10000u : 0u), &tt);
         if (valid) {
           const uint32_t a = nv + (ex & 0xFFFFu);
           s.cand[a] = q;
@@ -901,6 +933,8 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     for (uint32_t r = tid; r < M; r += BS) {
       const uint32_t pid = s.evpid[r], rel = s.rankpos[r];
       const uint32_t pc = s.pcell[pid];
+      // the last event before the cut records how many there are
+      if (rel < cut && (r + 1 == M || s.rankpos[r + 1] >= cut)) S.norig = r + 1;
       if (rel >= cut) {
         if (pc != NONE16) s.cell[pc] = 0u;
         continue;
@@ -959,7 +993,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       s.logpos[rel] = 0;
     }
     uint32_t ltot;
-    const uint32_t lbase = B.scan(nl, &ltot);
+    const uint32_t lbase = B.template scan_bits<kCountBits>(nl, &ltot);
     {
       uint32_t o = log0 + lbase;
 #pragma unroll
@@ -978,15 +1012,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     // The applied events are the prefix of the merged sequence before the cut.
     // Every thread derives the rebuild decision itself (no barrier here; the
     // rebuild's own barriers order warp 0's state updates before their use).
-    uint32_t norig = 0;
-    {
-      uint32_t hi = M;
-      while (norig < hi) {
-        const uint32_t mid = (norig + hi) >> 1;
-        if (s.rankpos[mid] < cut) norig = mid + 1;
-        else hi = mid;
-      }
-    }
+    const uint32_t norig = S.norig;
     const uint32_t need = full ? ((S.exhausted && cut < nact) ? 1u : 0u)
                                : (used0 + norig == k ? 2u : 0u);
     if (warp == 0) {
