@@ -301,9 +301,13 @@ struct SSBlock {
 
   // Result of a table match: slot >= 0, -2 - pid for the pending item of
   // claiming position pid, -1 for none.
-  __device__ __forceinline__ int cell_match(uint32_t c, uint32_t tag, ItemT x) const {
-    if (c == 0u || (c >> 16) != tag) return -1;
-    const uint32_t ref = c & 0xFFFFu;
+  // Tags are never 0, so an empty cell never matches.
+  static __device__ __forceinline__ uint32_t tag_of(uint32_t h) {
+    const uint32_t t = h & 0xFFFFu;
+    return t ? t : 1u;
+  }
+
+  __device__ __forceinline__ int ref_match(uint32_t ref, ItemT x) const {
     if (ref & PEND) {
       const uint32_t pid = ref & (PEND - 1);
       return s.wbuf[pid] == x ? -2 - (int)pid : -1;
@@ -311,15 +315,28 @@ struct SSBlock {
     return s.item[ref - 1] == x ? (int)(ref - 1) : -1;
   }
 
-  __device__ __forceinline__ int find_in(uint32_t bb, uint32_t tag, ItemT x) const {
-    const uint4 c = *(const uint4*)&s.cell[bb * 4];
-    const uint32_t cs[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = cell_match(cs[i], tag, x);
+  __device__ __forceinline__ int cell_match(uint32_t c, uint32_t tag, ItemT x) const {
+    if ((c >> 16) != tag) return -1;
+    return ref_match(c & 0xFFFFu, x);
+  }
+
+  // The cells of one bucket with x's tag, checked in cell order.
+  __device__ __forceinline__ int match4(const uint4& c, uint32_t tag, ItemT x) const {
+    unsigned mm = ((c.x >> 16) == tag ? 1u : 0u) | ((c.y >> 16) == tag ? 2u : 0u) |
+                  ((c.z >> 16) == tag ? 4u : 0u) | ((c.w >> 16) == tag ? 8u : 0u);
+    while (mm) {
+      const int i = __ffs(mm) - 1;
+      const uint32_t cv = i == 0 ? c.x : (i == 1 ? c.y : (i == 2 ? c.z : c.w));
+      const int r = ref_match(cv & 0xFFFFu, x);
       if (r != -1) return r;
+      mm &= mm - 1;
     }
     return -1;
+  }
+
+  __device__ __forceinline__ int find_in(uint32_t bb, uint32_t tag, ItemT x) const {
+    const uint4 c = *(const uint4*)&s.cell[bb * 4];
+    return match4(c, tag, x);
   }
 
   // x outside its first bucket b: in its second bucket or past it, where the
@@ -341,7 +358,7 @@ struct SSBlock {
   // order, and compares each filled cell with x, so they agree on one cell.
   __device__ int find_or_claim(ItemT x, uint32_t rel, uint32_t& status) {
     const uint32_t h = ItemOps<ItemT>::h1(x);
-    const uint32_t b = h >> s.nbshift, tag = h & 0xFFFFu, mask = s.NB - 1;
+    const uint32_t b = h >> s.nbshift, tag = tag_of(h), mask = s.NB - 1;
     int r = find_overflow(x, b, tag);
     if (r != -1) return r;
     const uint32_t val = (tag << 16) | PEND | rel;
@@ -388,7 +405,7 @@ struct SSBlock {
   __device__ __forceinline__ void insert(ItemT x, uint32_t slot, uint32_t& status) {
     const uint32_t h = ItemOps<ItemT>::h1(x);
     const uint32_t b = h >> s.nbshift, mask = s.NB - 1;
-    const uint32_t val = ((h & 0xFFFFu) << 16) | (slot + 1);
+    const uint32_t val = (tag_of(h) << 16) | (slot + 1);
     if (claim(b, val, slot)) return;
     atomicOr(&s.ovf[b >> 5], 1u << (b & 31));
     const uint32_t b2 = ItemOps<ItemT>::h3(x) >> s.nbshift;
@@ -647,18 +664,11 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const uint32_t h = ItemOps<ItemT>::h1(x[j]);
-        tg[j] = h & 0xFFFFu;
+        tg[j] = B.tag_of(h);
         hc[j] = *(const uint4*)&s.cell[(h >> s.nbshift) * 4];
       }
 #pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint32_t cs[4] = {hc[j].x, hc[j].y, hc[j].z, hc[j].w};
-        int r = -1;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (r == -1) r = B.cell_match(cs[i], tg[j], x[j]);
-        sl[j] = r;
-      }
+      for (int j = 0; j < IPT; ++j) sl[j] = B.match4(hc[j], tg[j], x[j]);
       // the rest (past the first bucket, or not in the table), packed onto
       // the warp's lanes; results by position in evpid (free until P2):
       // slot, or PEND | pid
