@@ -725,10 +725,25 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     // a window of those only just adds its occurrences.
     if (!__syncthreads_or((miss | mhit) != 0)) {
       if (t0 + nact < len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, t0 + nact, len);
+      // Skewed windows hit a few counters over and over: the warp adds its
+      // occurrences of one of them (lane 0's first) with a single atomic pair.
+      const uint32_t hot = __shfl_sync(0xffffffffu, tid * IPT < nact ? (uint32_t)sl[0] : NONE32, 0);
+      uint32_t hot_n = 0, hot_t = 0;
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const uint32_t rel = tid * IPT + j;
-        B.add_occurrence(rel < nact ? (uint32_t)sl[j] : NONE32, t0 + rel);
+        const uint32_t tgt = rel < nact ? (uint32_t)sl[j] : NONE32;
+        const bool h = tgt == hot && hot != NONE32;
+        const unsigned bal = __ballot_sync(0xffffffffu, h);
+        if (bal) {
+          hot_n += __popc(bal);
+          hot_t = max(hot_t, t0 + (((uint32_t)warp << 5) + 31u - __clz(bal)) * IPT + j);
+        }
+        if (!h) B.add_occurrence(tgt, t0 + rel);
+      }
+      if (lane == 0 && hot_n) {
+        atomicAdd(&s.cnt[hot], hot_n);
+        atomicMax(&s.touch[hot], hot_t);
       }
       t0 += nact;
       continue;
