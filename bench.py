@@ -512,6 +512,17 @@ def main():
     merge_ms = prof["merge_ms"] / max(args.steps, 1)
     query_ms = prof["query_ms"] / max(prof["query_calls"], 1)
 
+    # Accuracy of the answer (the paper's Section 4 metrics), outside the
+    # timed region: exact counts on the device, ARE / precision / recall.
+    accuracy = None
+    if wl["log2u"] <= 28:
+        sm = P.summarize(x, k, p, stream=stream)
+        counts = P.exact_counts(x, wl["log2u"], stream=stream)
+        accuracy = sm.accuracy(counts, wl["log2u"], n, k, stream=stream)
+        accuracy["reported_as"] = "query count*k > n; ARE over the reported items"
+        sm.close()
+        del counts
+
     e2e = None
     if not args.no_e2e:
         hx = torch.empty(n, dtype=x.dtype, pin_memory=True)
@@ -553,8 +564,8 @@ def main():
             "dtype": "u32" if w == 4 else "u64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "k": k, "p": p, "item_bytes": w,
                        "zipf_s": wl["s"], "universe": f"2^{wl['log2u']}", "seed": wl["seed"],
-                       "l2": "input (4 GiB) larger than L2; no flush" if n * w > (256 << 20)
-                       else "input smaller than L2",
+                       "l2": (f"input ({n * w / 2**30:.2f} GiB) larger than L2; no flush"
+                              if n * w > (256 << 20) else "input smaller than L2"),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "input_gbs": input_gbs,
             "hbm_frac": input_gbs / hbm,
@@ -568,6 +579,7 @@ def main():
                           "query_ms": query_ms,
                           "fractional_overhead": merge_ms / sum_ms if sum_ms > 0 else None},
             "frequent_items": int(q.size),
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(prof["launches"]),

@@ -243,6 +243,55 @@ int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* hos
               uint32_t* n_out, void* stream);
 
 /*
+ * pss_query_mode — pss_query with a choice of bound.  PSS_QUERY_CANDIDATES is
+ * pss_query (count * k > n: every true k-majority item is among them, the
+ * 100% recall of Section 4).  PSS_QUERY_GUARANTEED keeps the entries whose
+ * lower bound already exceeds the threshold, (count - err) * k > n: since
+ * count - err <= f, each of them is a true k-majority item (no false
+ * positive).  The paper reports only the first; the second is its
+ * counterpart from the same error bound.  Same order, arguments and errors as
+ * pss_query; any other mode is PSS_EINVAL.
+ */
+#define PSS_QUERY_CANDIDATES 0
+#define PSS_QUERY_GUARANTEED 1
+int pss_query_mode(const pss_summary* summary, uint64_t n, uint32_t k, int mode, pss_entry* host_out,
+                   uint32_t cap, uint32_t* n_out, void* stream);
+
+/*
+ * Exact frequencies, the reference of the paper's accuracy metrics
+ * (Section 4).  pss_exact_counts overwrites d_counts[0 .. 2^log2u] (caller
+ * memory, 2^log2u + 1 u32 words, 1 <= log2u <= 32): word x is the number of
+ * occurrences of item x among the n items at d_items (item_bytes 4 or 8), the
+ * last word the number of items outside [0, 2^log2u).  Counts wrap past
+ * 2^32 - 1 occurrences of one item.  Asynchronous.
+ */
+int pss_exact_counts(const void* d_items, uint64_t n, int item_bytes, int log2u, uint32_t* d_counts,
+                     void* stream);
+
+/*
+ * pss_accuracy_of — the accuracy of a summary's answer against exact counts
+ * (from pss_exact_counts over the same n items), as Section 4 defines it:
+ * the relative error |f - count| / f of every reported item averaged over
+ * the reported items (ARE), precision = reported true k-majority items /
+ * reported items, recall = reported true k-majority items / true k-majority
+ * items.  "Reported" means pss_query's answer (count * k > n), "true
+ * k-majority" f * k > n.  Empty denominators give ARE 0, precision 1,
+ * recall 1.  Synchronizes stream.
+ */
+typedef struct {
+  uint64_t reported;      /* entries with count * k > n */
+  uint64_t true_frequent; /* items with f * k > n */
+  uint64_t true_positive; /* reported items that are truly frequent */
+  uint64_t guaranteed;    /* reported entries with (count - err) * k > n */
+  uint64_t outside;       /* items of the stream outside [0, 2^log2u) */
+  double are;
+  double precision;
+  double recall;
+} pss_accuracy;
+int pss_accuracy_of(const pss_summary* summary, const uint32_t* d_counts, int log2u, uint64_t n,
+                    uint32_t k, pss_accuracy* out, void* stream);
+
+/*
  * pss_export — copy a whole summary to the host in canonical order (count
  * descending, item ascending) with its minimum m and the number of stream
  * items it describes.  host_out holds cap >= k entries (PSS_ERANGE if the

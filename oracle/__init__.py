@@ -232,6 +232,48 @@ def parallel_space_saving(items, k: int, p: int) -> tuple[Summary, Summary]:
     return root, query(root, n, k)
 
 
+# ----------------------------------------------- accuracy (Section 4 metrics)
+
+def query_guaranteed(s: Summary, n: int, k: int) -> Summary:
+    """Entries whose lower bound count - err exceeds n/k ((count - err) * k > n;
+    count - err <= f makes each a true k-majority item), canonical order."""
+    keep = [i for i in range(s.size) if (int(s.count[i]) - int(s.err[i])) * k > n]
+    order = sorted(keep, key=lambda i: (-int(s.count[i]), int(s.item[i])))
+    idx = np.array(order, np.int64)
+    return Summary(s.item[idx].copy(), s.count[idx].copy(), s.err[idx].copy(), s.m, s.n_covered)
+
+
+def exact_counts(items, log2u: int) -> np.ndarray:
+    """Exact occurrences of every item of [0, 2^log2u); the last entry counts
+    the items outside (the exact reference of Section 4's metrics)."""
+    x = np.asarray(items).astype(np.uint64)
+    u = 1 << log2u
+    inside = x < np.uint64(u)
+    c = np.bincount(x[inside].astype(np.int64), minlength=u).astype(np.uint64)
+    return np.append(c, np.uint64(int((~inside).sum())))
+
+
+def accuracy(s: Summary, counts: np.ndarray, n: int, k: int) -> dict:
+    """Section 4: the relative error |f - f^| / f of each reported frequency
+    averaged over the reported items (ARE); precision = true k-majority items
+    reported / items reported; recall = true k-majority items reported / true
+    k-majority items (f * k > n).  Reported = the query's answer (count * k >
+    n).  Empty denominators: ARE 0, precision 1, recall 1."""
+    u = counts.shape[0] - 1
+    rep = query(s, n, k)
+    freq = [int(counts[int(x)]) if int(x) < u else 0 for x in rep.item]
+    true_frequent = int(sum(1 for f in counts[:u] if int(f) * k > n))
+    tp = sum(1 for f in freq if f * k > n)
+    guaranteed = sum(1 for c, e in zip(rep.count, rep.err) if (int(c) - int(e)) * k > n)
+    rel = [abs(int(c) - f) / f for c, f in zip(rep.count, freq) if f > 0]
+    r = rep.size
+    return {"reported": r, "true_frequent": true_frequent, "true_positive": tp,
+            "guaranteed": guaranteed, "outside": int(counts[u]),
+            "are": (sum(rel) / r) if r else 0.0,
+            "precision": (tp / r) if r else 1.0,
+            "recall": (tp / true_frequent) if true_frequent else 1.0}
+
+
 # ---------------------------------------------------------------- generator
 
 def philox4x32_10(counter, key):

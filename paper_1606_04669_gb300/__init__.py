@@ -7,4 +7,5 @@ the C ABI of include/pss.h.  This package is its thin Python binding.
 from .pss import (  # noqa: F401
     Batch, PSS_EDEVICE, PSS_EINVAL, PSS_EMISMATCH, PSS_ENOMEM, PSS_ERANGE, PSS_MAX_K, PSS_OK, Exported,
     PssError, Server, Summary, Tree, gen_zipf, lib_path, load, merge, profile_enable, profile_read, strerror,
-    plan_blocks, set_warp_kmax, summarize, summarize_host, summarize_tree)
+    plan_blocks, set_warp_kmax, summarize, summarize_host, summarize_tree, exact_counts,
+    QUERY_CANDIDATES, QUERY_GUARANTEED)

@@ -511,6 +511,54 @@ int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* hos
                    n_out, (cudaStream_t)stream);
 }
 
+int pss_query_mode(const pss_summary* summary, uint64_t n, uint32_t k, int mode, pss_entry* host_out,
+                   uint32_t cap, uint32_t* n_out, void* stream) {
+  if (mode != PSS_QUERY_CANDIDATES && mode != PSS_QUERY_GUARANTEED) return PSS_EINVAL;
+  if (!summary || !n_out || k < 2) return PSS_EINVAL;
+  if (cap > 0 && !host_out) return PSS_EINVAL;
+  return canon_out(summary->mem, 1, 0, summary->k, summary->item_bytes, n, k,
+                   mode == PSS_QUERY_GUARANTEED ? 2 : 1, host_out, cap, n_out, (cudaStream_t)stream);
+}
+
+int pss_exact_counts(const void* d_items, uint64_t n, int item_bytes, int log2u, uint32_t* d_counts,
+                     void* stream) {
+  if ((item_bytes != 4 && item_bytes != 8) || log2u < 1 || log2u > 32 || !d_counts) return PSS_EINVAL;
+  if (n > 0 && !d_items) return PSS_EINVAL;
+  cudaError_t e = prepare_device();
+  if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(pss::launch_exact_counts(d_items, n, item_bytes, log2u, d_counts,
+                                            (cudaStream_t)stream));
+}
+
+int pss_accuracy_of(const pss_summary* summary, const uint32_t* d_counts, int log2u, uint64_t n,
+                    uint32_t k, pss_accuracy* out, void* stream) {
+  if (!summary || !d_counts || !out || k < 2 || log2u < 1 || log2u > 32) return PSS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* dmem = nullptr;
+  cudaError_t e = cudaMallocAsync(&dmem, sizeof(pss::AccOut), s);
+  if (e != cudaSuccess) return from_cuda(e);
+  pss::AccOut* d = (pss::AccOut*)dmem;
+  e = summary->item_bytes == 4
+          ? pss::launch_accuracy<uint32_t>(set_view<uint32_t>(summary->mem, 1, summary->k), d_counts,
+                                           log2u, n, k, d, s)
+          : pss::launch_accuracy<u64>(set_view<u64>(summary->mem, 1, summary->k), d_counts, log2u, n,
+                                      k, d, s);
+  pss::AccOut h{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(dmem, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  out->reported = h.reported;
+  out->true_frequent = h.true_frequent;
+  out->true_positive = h.true_positive;
+  out->guaranteed = h.guaranteed;
+  out->outside = h.outside;
+  out->are = h.reported ? h.are_sum / (double)h.reported : 0.0;
+  out->precision = h.reported ? (double)h.true_positive / (double)h.reported : 1.0;
+  out->recall = h.true_frequent ? (double)h.true_positive / (double)h.true_frequent : 1.0;
+  return PSS_OK;
+}
+
 int pss_export(const pss_summary* summary, pss_entry* host_out, uint32_t cap, uint32_t* size,
                uint64_t* m, uint64_t* n_covered, void* stream) {
   if (!summary || !size) return PSS_EINVAL;

@@ -68,7 +68,10 @@ __device__ void canon_node(const SetView<ItemT>& in, uint32_t node, u64 n, uint3
     u64 c = 0;
     if (i < size) {
       c = in.count[base + i];
-      keep = !filter || __umul64hi(c, (u64)kq) != 0 || c * (u64)kq > n;
+      // filter 1: count k > n (candidates); 2: (count - err) k > n (guaranteed,
+      // since count - err <= f)
+      const u64 t = filter == 2 ? c - in.err[base + i] : c;
+      keep = !filter || __umul64hi(t, (u64)kq) != 0 || t * (u64)kq > n;
     }
     uint32_t tot;
     const uint32_t ex = block_exclusive_scan<BS>(keep ? 1u : 0u, wsum + (par ? (BS / 32 + 1) : 0), &tot);

@@ -64,8 +64,9 @@ template <typename ItemT>
 cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, uint32_t ib,
                               SetView<ItemT> out, cudaStream_t stream);
 
-// Canonical export of node `node`: entries with (filter == 0) or
-// count * kq > n, sorted by (count desc, item asc), written to out[0..*out_n).
+// Canonical export of node `node`: every entry (filter 0), entries with
+// count * kq > n (filter 1) or (count - err) * kq > n (filter 2), sorted by
+// (count desc, item asc), written to out[0..*out_n).
 template <typename ItemT>
 cudaError_t launch_canon(SetView<ItemT> in, uint32_t node, u64 n, uint32_t kq, int filter,
                          pss_entry* out, uint32_t* out_n, cudaStream_t stream);
@@ -80,6 +81,19 @@ template <typename ItemT>
 cudaError_t launch_summarize_batch(const BatchStream* streams, const BatchTask* tasks,
                                    uint32_t ntasks, uint32_t* counter, uint32_t k, uint32_t grid,
                                    cudaStream_t stream);
+
+// Exact frequencies and the accuracy metrics of a summary (accuracy.cu).
+struct AccOut {
+  unsigned long long reported, true_frequent, true_positive, guaranteed, outside;
+  double are_sum;
+};
+
+cudaError_t launch_exact_counts(const void* items, u64 n, int item_bytes, int log2u,
+                                uint32_t* counts, cudaStream_t stream);
+
+template <typename ItemT>
+cudaError_t launch_accuracy(SetView<ItemT> in, const uint32_t* counts, int log2u, u64 n,
+                            uint32_t kq, AccOut* out, cudaStream_t stream);
 
 // Warp-per-block summaries for k <= WARP_SS_MAX_K (summarize_warp.cu).  The
 // plain path (launch_summarize_blocks) uses them for k <= warp_kmax()

@@ -60,6 +60,17 @@ class BatchDesc(ctypes.Structure):
                 ("skew_hint", ctypes.POINTER(ctypes.c_double))]
 
 
+class Accuracy(ctypes.Structure):
+    _fields_ = [("reported", ctypes.c_uint64), ("true_frequent", ctypes.c_uint64),
+                ("true_positive", ctypes.c_uint64), ("guaranteed", ctypes.c_uint64),
+                ("outside", ctypes.c_uint64), ("are", ctypes.c_double),
+                ("precision", ctypes.c_double), ("recall", ctypes.c_double)]
+
+
+QUERY_CANDIDATES = 0
+QUERY_GUARANTEED = 1
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("tenants", ctypes.c_uint32), ("k", ctypes.c_uint32),
                 ("budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
@@ -97,6 +108,9 @@ SIGNATURES = {
     "pss_tree_free": (None, [vp]),
     "pss_merge": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
     "pss_query": (ctypes.c_int, [vp, u64, u32, ctypes.POINTER(Entry), u32, u32p, vp]),
+    "pss_query_mode": (ctypes.c_int, [vp, u64, u32, ctypes.c_int, ctypes.POINTER(Entry), u32, u32p, vp]),
+    "pss_exact_counts": (ctypes.c_int, [vp, u64, ctypes.c_int, ctypes.c_int, vp, vp]),
+    "pss_accuracy_of": (ctypes.c_int, [vp, vp, ctypes.c_int, u64, u32, ctypes.POINTER(Accuracy), vp]),
     "pss_export": (ctypes.c_int, [vp, ctypes.POINTER(Entry), u32, u32p, u64p, u64p, vp]),
     "pss_summary_info": (ctypes.c_int, [vp, u32p, ctypes.POINTER(ctypes.c_int)]),
     "pss_free": (None, [vp]),
@@ -232,14 +246,31 @@ class Summary:
         it, ct, er = _entries_to_arrays(buf, size.value)
         return Exported(it, ct, er, int(m.value), int(cov.value))
 
-    def query(self, n: int, k: int | None = None, stream=None) -> Exported:
+    def query(self, n: int, k: int | None = None, stream=None, guaranteed: bool = False) -> Exported:
+        """pss_query (count k > n), or with guaranteed=True pss_query_mode's
+        guaranteed entries ((count - err) k > n)."""
         kq = self.k if k is None else int(k)
         buf = (Entry * self.k)()
         nout = u32()
-        _check(load().pss_query(self._h, int(n), kq, buf, self.k, ctypes.byref(nout),
-                                vp(_stream_handle(stream))), "pss_query")
+        if guaranteed:
+            _check(load().pss_query_mode(self._h, int(n), kq, QUERY_GUARANTEED, buf, self.k,
+                                         ctypes.byref(nout), vp(_stream_handle(stream))),
+                   "pss_query_mode")
+        else:
+            _check(load().pss_query(self._h, int(n), kq, buf, self.k, ctypes.byref(nout),
+                                    vp(_stream_handle(stream))), "pss_query")
         it, ct, er = _entries_to_arrays(buf, nout.value)
         return Exported(it, ct, er, 0, int(n))
+
+    def accuracy(self, counts, log2u: int, n: int, k: int | None = None, stream=None) -> dict:
+        """pss_accuracy_of against exact counts (a CUDA tensor from exact_counts)."""
+        kq = self.k if k is None else int(k)
+        if not counts.is_cuda or counts.numel() < (1 << log2u) + 1:
+            raise ValueError("counts must be a CUDA tensor of 2^log2u + 1 words")
+        a = Accuracy()
+        _check(load().pss_accuracy_of(self._h, vp(counts.data_ptr()), int(log2u), int(n), kq,
+                                      ctypes.byref(a), vp(_stream_handle(stream))), "pss_accuracy_of")
+        return {name: getattr(a, name) for name, _ in Accuracy._fields_}
 
     def close(self):
         if self._h is not None and self._h.value:
@@ -361,6 +392,20 @@ def gen_zipf(count: int, *, seed: int, s: float, log2u: int, item_bytes: int = 4
     _check(load().pss_gen_zipf(vp(out.data_ptr()), int(count), int(item_bytes), int(seed),
                                int(stream_id), int(start), float(s), int(log2u),
                                vp(_stream_handle(stream))), "pss_gen_zipf")
+    return out
+
+
+def exact_counts(items, log2u: int, out=None, stream=None):
+    """pss_exact_counts: occurrences of every item of [0, 2^log2u) (int32 bit
+    patterns of u32 counts; the last word counts items outside)."""
+    import torch
+    w = _check_items(items)
+    if out is None:
+        out = torch.empty((1 << log2u) + 1, dtype=torch.int32, device=items.device)
+    elif out.numel() < (1 << log2u) + 1:
+        raise ValueError("out is too small")
+    _check(load().pss_exact_counts(vp(items.data_ptr()), int(items.numel()), int(w), int(log2u),
+                                   vp(out.data_ptr()), vp(_stream_handle(stream))), "pss_exact_counts")
     return out
 
 

@@ -11,7 +11,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def read_golden(name: str) -> dict:
-    out = {"stream": [], "a": [], "b": [], "expect": [], "query": []}
+    out = {"stream": [], "a": [], "b": [], "expect": [], "query": [], "freq": []}
     with open(os.path.join(GOLDEN, name)) as f:
         for line in f:
             line = line.split("#", 1)[0].strip()
@@ -19,10 +19,12 @@ def read_golden(name: str) -> dict:
                 continue
             key, *vals = line.split()
             ints = [int(v) for v in vals]
-            if key in ("a", "b", "expect"):
+            if key in ("a", "b", "expect", "freq"):
                 out[key].append(tuple(ints))
             elif key in ("stream", "query"):
                 out[key].extend(ints)
+            elif len(ints) == 2:
+                out[key] = (ints[0], ints[1])  # a fraction num / den
             else:
                 out[key] = ints[0]
     return out

@@ -6,6 +6,7 @@ bounds, closed forms of special streams, and a naive scan implementation."""
 from __future__ import annotations
 
 import random
+from collections import Counter
 
 import numpy as np
 import pytest
@@ -254,3 +255,51 @@ def test_query_threshold_boundary():
     assert oracle.query(s, 100, 10).item.tolist() == [1]        # floor(100/10)+1 = 11
     assert oracle.query(s, 99, 10).item.tolist() == [1, 2]      # floor(99/10)+1 = 10
     assert oracle.query(s, 2 ** 64 - 1, 2 ** 32 - 1).item.tolist() == []
+
+
+# ------------------------------------------------------- accuracy (Section 4)
+
+def test_golden_accuracy_metrics():
+    from fractions import Fraction
+    g = read_golden("accuracy_k4.txt")
+    k, n = g["k"], g["n"]
+    s = oracle.Summary(np.array([a[0] for a in g["a"]], np.uint64),
+                       np.array([a[1] for a in g["a"]], np.uint64),
+                       np.array([a[2] for a in g["a"]], np.uint64), 0, n)
+    u_bits = 3
+    counts = np.zeros((1 << u_bits) + 1, np.uint64)
+    for item, f in g["freq"]:
+        counts[item] = f
+    acc = oracle.accuracy(s, counts, n, k)
+    for key in ("reported", "true_frequent", "true_positive", "guaranteed"):
+        assert acc[key] == g["expect_" + key], key
+    for key in ("are", "precision", "recall"):
+        num, den = g["expect_" + key]
+        assert Fraction(acc[key]).limit_denominator(1000) == Fraction(num, den), key
+    gq = oracle.query_guaranteed(s, n, k)
+    assert gq.item.tolist() == [1]
+
+
+def test_exact_counts_oracle_against_counter():
+    rng = np.random.default_rng(4)
+    x = rng.integers(0, 1 << 10, size=5000).astype(np.uint32)
+    x[::97] = np.uint32(1 << 12)  # outside a 2^10 universe
+    c = oracle.exact_counts(x, 10)
+    ref = Counter(x.tolist())
+    assert int(c[-1]) == ref[1 << 12]
+    assert all(int(c[v]) == ref.get(v, 0) for v in range(1 << 10))
+
+
+@pytest.mark.parametrize("s_,k,p,seed", [(1.1, 50, 4, 31), (0.7, 200, 7, 32), (1.6, 20, 3, 33)])
+def test_accuracy_properties(s_, k, p, seed):
+    # Space Saving's error bound makes every true k-majority item a reported
+    # one (recall 1) and every guaranteed entry truly frequent.
+    x = oracle.gen_zipf(80_000, seed=seed, s=s_, log2u=14)
+    root, _ = oracle.parallel_space_saving(x, k, p)
+    counts = oracle.exact_counts(x, 14)
+    acc = oracle.accuracy(root, counts, len(x), k)
+    assert acc["recall"] == 1.0
+    assert acc["guaranteed"] <= acc["true_positive"] <= acc["reported"]
+    assert acc["outside"] == 0 and acc["are"] >= 0.0
+    g = oracle.query_guaranteed(root, len(x), k)
+    assert all(int(counts[int(v)]) * k > len(x) for v in g.item)
