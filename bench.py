@@ -238,11 +238,14 @@ def run_sweep(args):
     n, p, w = 1 << 30, 4096, 4
     stream = torch.cuda.current_stream()
     x = torch.empty(n, dtype=torch.int32, device="cuda")
+    # k = 8000 (the top of the paper's k sweep) runs only when named in
+    # --points, with seed 30 + i_s.
     for i_s, zs in enumerate(SWEEP_S):
-        for i_k, k in enumerate(SWEEP_K):
-            if args.points and f"{zs}:{k}" not in args.points.split(","):
+        for i_k, k in enumerate(SWEEP_K + (8000,)):
+            named = bool(args.points) and f"{zs}:{k}" in args.points.split(",")
+            if (args.points and not named) or (k == 8000 and not named):
                 continue
-            seed = 10 + 4 * i_s + i_k
+            seed = 10 + 4 * i_s + i_k if k != 8000 else 30 + i_s
             P.gen_zipf(n, seed=seed, s=zs, log2u=32, out=x)
             torch.cuda.synchronize()
 

@@ -58,7 +58,8 @@ extern "C" {
 #define PSS_ERANGE (-7)    /* output capacity too small */
 
 /* Largest k the shared-memory resident summarize kernel supports. */
-#define PSS_MAX_K 4096u
+#define PSS_MAX_K 8192u          /* pss_summarize*, pss_merge, pss_query*, pss_export */
+#define PSS_MAX_K_RESIDENT 4096u /* the batch, server and allocation-free forms */
 
 typedef struct pss_summary pss_summary; /* one summary (opaque, device-resident) */
 typedef struct pss_tree pss_tree;       /* every level of one reduction tree */
@@ -81,7 +82,10 @@ int pss_abi_version(void);
  * in a binary tree over adjacent pairs (an odd last summary is carried up).
  *   d_items     device array of n items of item_bytes each (4 or 8);
  *               may be NULL only when n == 0.
- *   k           counters per summary, 2 <= k <= PSS_MAX_K.
+ *   k           counters per summary, 2 <= k <= PSS_MAX_K (the paper's k
+ *               sweep reaches 8000); above 4096 part of each block's state
+ *               and of each combine's union lives in HBM scratch taken on
+ *               the stream for the call.
  *   p           number of blocks, p >= 1; blocks may be empty when n < p;
  *               a block must hold fewer than 2^32 items.
  *   out         receives a new summary (release with pss_free).
@@ -115,6 +119,7 @@ int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t
  *     block summaries and the reduction tree live in one fixed array of
  *     PSS_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that
  *     loads the library holds that array until the process exits.
+ *   - k <= PSS_MAX_K_RESIDENT (larger k need stream-ordered scratch).
  *   - Limit: the p block summaries plus ceil(p/2) merged summaries must fit
  *     in the array (about 1.5 p k (item_bytes + 16) bytes; e.g. p = 8,
  *     k = 2000 fits, p = 4096, k = 2000 does not); otherwise PSS_ERANGE and
@@ -183,7 +188,7 @@ typedef struct {
   int item_bytes;                /* 4 or 8, the same for every stream */
   const void* const* d_items;    /* nstreams device pointers */
   const uint64_t* n;             /* nstreams lengths */
-  const uint32_t* k;             /* nstreams counter counts, 2 <= k <= PSS_MAX_K */
+  const uint32_t* k;             /* nstreams counter counts, 2 <= k <= PSS_MAX_K_RESIDENT */
   const uint32_t* p;             /* nstreams block counts; NULL or 0 entries: pss_plan_blocks */
   const double* skew_hint;       /* optional per-stream skew for the planner (NULL: unknown) */
 } pss_batch_desc;
@@ -324,7 +329,7 @@ typedef struct pss_server pss_server;
 
 typedef struct {
   uint32_t tenants;        /* tenant summaries kept resident */
-  uint32_t k;              /* counters of every segment and tenant summary */
+  uint32_t k;              /* counters of every segment and tenant summary (<= PSS_MAX_K_RESIDENT) */
   uint64_t budget_bytes;   /* device memory admitted requests may hold at once */
   uint32_t max_batch;      /* requests admitted per scheduling tick */
   uint32_t max_inflight;   /* admitted, not yet completed requests (host result slots) */

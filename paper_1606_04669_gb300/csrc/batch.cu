@@ -231,7 +231,7 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
     const double skew = desc->skew_hint ? desc->skew_hint[i] : 0.0;
     sp.p = (desc->p && desc->p[i]) ? desc->p[i] : pss_plan_blocks(sp.n, sp.k, w, skew);
     sp.warp = use_warp_kernel(sp.k, skew);
-    if (sp.k < 2 || sp.k > PSS_MAX_K || sp.p == 0 || (sp.n > 0 && !sp.items) ||
+    if (sp.k < 2 || sp.k > PSS_MAX_K_RESIDENT || sp.p == 0 || (sp.n > 0 && !sp.items) ||
         (sp.n + sp.p - 1) / sp.p >= (1ull << 32)) {
       destroy(b);
       return PSS_EINVAL;

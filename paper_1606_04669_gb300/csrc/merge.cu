@@ -35,25 +35,35 @@ struct MSmem {
   u64* red;
 };
 
-template <typename ItemT, int BS>
-__host__ __device__ inline size_t merge_carve(uint32_t k, unsigned char* base, MSmem<ItemT>* s) {
-  size_t off = 0;
+// Shared-memory layout (returns its bytes).  BIG (k above what fits): the
+// union's counts and source indices live in a per-CTA slice of global memory
+// (gbase; bytes to *gbytes).
+template <typename ItemT, int BS, bool BIG>
+__host__ __device__ inline size_t merge_carve(uint32_t k, unsigned char* base, unsigned char* gbase,
+                                              MSmem<ItemT>* s, size_t* gbytes = nullptr) {
+  size_t off = 0, goff = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off = (off + bytes + 15) & ~(size_t)15;
     return base + o;
   };
+  auto gtake = [&](size_t bytes) {
+    size_t o = goff;
+    goff = (goff + bytes + 15) & ~(size_t)15;
+    return gbase + o;
+  };
   MSmem<ItemT> L;
-  L.uc = (u64*)take(8ull * 2 * k);
+  L.uc = (u64*)(BIG ? gtake(8ull * 2 * k) : take(8ull * 2 * k));
   L.red = (u64*)take(8ull * (BS / 32 + 1));
   L.ia = (ItemT*)take(sizeof(ItemT) * k);
   L.ib = (ItemT*)take(sizeof(ItemT) * k);
   L.borank = (uint32_t*)take(4ull * (k + 1));
   L.hist = (uint32_t*)take(4ull * 256);
   L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
-  L.srcA = (uint16_t*)take(2ull * 2 * k);
-  L.srcB = (uint16_t*)take(2ull * 2 * k);
+  L.srcA = (uint16_t*)(BIG ? gtake(2ull * 2 * k) : take(2ull * 2 * k));
+  L.srcB = (uint16_t*)(BIG ? gtake(2ull * 2 * k) : take(2ull * 2 * k));
   if (s) *s = L;
+  if (gbytes) *gbytes = goff;
   return off;
 }
 
@@ -85,15 +95,15 @@ __device__ __forceinline__ u64 block_reduce_u64(u64 v, u64* scratch, bool is_max
 }
 
 // out node `no` = combine(A node na, B node nb).
-template <typename ItemT, int BS>
+template <typename ItemT, int BS, bool BIG>
 __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<ItemT>& B,
                             uint32_t nb, const SetView<ItemT>& O, uint32_t no,
-                            unsigned char* smem) {
+                            unsigned char* smem, unsigned char* gslice) {
   __shared__ u64 sh_prefix;
   __shared__ uint32_t sh_need;
   MSmem<ItemT> s;
   const uint32_t k = O.k;
-  merge_carve<ItemT, BS>(k, smem, &s);
+  merge_carve<ItemT, BS, BIG>(k, smem, gslice, &s);
   const uint32_t tid = threadIdx.x;
   const uint32_t sa = A.size[na], sb = B.size[nb];
   const u64 mA = A.m[na], mB = B.m[nb];
@@ -244,23 +254,25 @@ __device__ void copy_node(const SetView<ItemT>& in, uint32_t ni, const SetView<I
   }
 }
 
-template <typename ItemT, int BS>
-__global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out) {
+template <typename ItemT, int BS, bool BIG>
+__global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out,
+                                                         unsigned char* gscratch, size_t gslice) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t j = blockIdx.x;
   if (2 * j + 1 >= in.nodes) {
     copy_node<ItemT, BS>(in, 2 * j, out, j);
     return;
   }
-  merge_nodes<ItemT, BS>(in, 2 * j, in, 2 * j + 1, out, j, smem);
+  merge_nodes<ItemT, BS, BIG>(in, 2 * j, in, 2 * j + 1, out, j, smem,
+                              BIG ? gscratch + (size_t)j * gslice : nullptr);
 }
 
-template <typename ItemT, int BS>
+template <typename ItemT, int BS, bool BIG>
 __global__ void __launch_bounds__(BS) merge_pair_kernel(SetView<ItemT> a, uint32_t ia,
                                                         SetView<ItemT> b, uint32_t ib,
-                                                        SetView<ItemT> out) {
+                                                        SetView<ItemT> out, unsigned char* gscratch) {
   extern __shared__ __align__(16) unsigned char smem[];
-  merge_nodes<ItemT, BS>(a, ia, b, ib, out, 0, smem);
+  merge_nodes<ItemT, BS, BIG>(a, ia, b, ib, out, 0, smem, gscratch);
 }
 
 // Batch form: task (d, j) builds node j of the next level of descriptor d.
@@ -277,7 +289,7 @@ __global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __rest
     copy_node<ItemT, BS>(in, 2 * j, out, j);
     return;
   }
-  merge_nodes<ItemT, BS>(in, 2 * j, in, 2 * j + 1, out, j, smem);
+  merge_nodes<ItemT, BS, false>(in, 2 * j, in, 2 * j + 1, out, j, smem, nullptr);
 }
 
 template <typename ItemT, int BS>
@@ -290,28 +302,64 @@ __global__ void __launch_bounds__(BS) copy_node_kernel(SetView<ItemT> in, uint32
 
 template <typename ItemT>
 size_t merge_smem_bytes(uint32_t k) {
-  return merge_carve<ItemT, MERGE_BS>(k, nullptr, nullptr);
+  return k > SS_SMEM_MAX_K ? merge_carve<ItemT, MERGE_BS, true>(k, nullptr, nullptr, nullptr)
+                           : merge_carve<ItemT, MERGE_BS, false>(k, nullptr, nullptr, nullptr);
 }
+
+namespace {
+
+// Global scratch of `ctas` large-k merges, ordered on the stream.
+template <typename ItemT>
+cudaError_t merge_scratch(uint32_t k, uint32_t ctas, cudaStream_t stream, void** g, size_t* gslice) {
+  merge_carve<ItemT, MERGE_BS, true>(k, nullptr, nullptr, nullptr, gslice);
+  return cudaMallocAsync(g, *gslice * (ctas ? ctas : 1), stream);
+}
+
+}  // namespace
 
 template <typename ItemT>
 cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream) {
   const size_t smem = merge_smem_bytes<ItemT>(in.k);
-  auto kern = merge_level_kernel<ItemT, MERGE_BS>;
+  if (in.k <= SS_SMEM_MAX_K) {
+    auto kern = merge_level_kernel<ItemT, MERGE_BS, false>;
+    cudaError_t e = ensure_kernel_attrs((const void*)kern);
+    if (e != cudaSuccess) return e;
+    kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out, nullptr, 0);
+    return cudaGetLastError();
+  }
+  auto kern = merge_level_kernel<ItemT, MERGE_BS, true>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
-  kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out);
-  return cudaGetLastError();
+  void* g = nullptr;
+  size_t gslice = 0;
+  if ((e = merge_scratch<ItemT>(in.k, out.nodes, stream, &g, &gslice)) != cudaSuccess) return e;
+  kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out, (unsigned char*)g, gslice);
+  e = cudaGetLastError();
+  const cudaError_t f = cudaFreeAsync(g, stream);
+  return e != cudaSuccess ? e : f;
 }
 
 template <typename ItemT>
 cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, uint32_t ib,
                               SetView<ItemT> out, cudaStream_t stream) {
   const size_t smem = merge_smem_bytes<ItemT>(out.k);
-  auto kern = merge_pair_kernel<ItemT, MERGE_BS>;
+  if (out.k <= SS_SMEM_MAX_K) {
+    auto kern = merge_pair_kernel<ItemT, MERGE_BS, false>;
+    cudaError_t e = ensure_kernel_attrs((const void*)kern);
+    if (e != cudaSuccess) return e;
+    kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out, nullptr);
+    return cudaGetLastError();
+  }
+  auto kern = merge_pair_kernel<ItemT, MERGE_BS, true>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
-  kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out);
-  return cudaGetLastError();
+  void* g = nullptr;
+  size_t gslice = 0;
+  if ((e = merge_scratch<ItemT>(out.k, 1, stream, &g, &gslice)) != cudaSuccess) return e;
+  kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out, (unsigned char*)g);
+  e = cudaGetLastError();
+  const cudaError_t f = cudaFreeAsync(g, stream);
+  return e != cudaSuccess ? e : f;
 }
 
 template <typename ItemT>
@@ -324,6 +372,7 @@ cudaError_t launch_copy_node(SetView<ItemT> in, uint32_t node, SetView<ItemT> ou
 template <typename ItemT>
 cudaError_t launch_merge_tasks(const MergeDesc* descs, const BatchTask* tasks, uint32_t ntasks,
                                uint32_t k, cudaStream_t stream) {
+  if (k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;  // the batch keeps k in shared memory
   const size_t smem = merge_smem_bytes<ItemT>(k);
   auto kern = merge_tasks_kernel<ItemT, MERGE_BS>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);

@@ -118,7 +118,7 @@ extern "C" int pss_summarize_noalloc(const void* d_items, uint64_t n, int item_b
                                      uint64_t* d_out_errs, uint64_t* d_out_header, void* stream) {
   using namespace pss;
   if (item_bytes != 4 && item_bytes != 8) return PSS_EINVAL;
-  if (k < 2 || k > PSS_MAX_K || p == 0) return PSS_EINVAL;
+  if (k < 2 || k > PSS_MAX_K_RESIDENT || p == 0) return PSS_EINVAL;
   if (n > 0 && !d_items) return PSS_EINVAL;
   if (!d_out_items || !d_out_counts || !d_out_errs || !d_out_header) return PSS_EINVAL;
   if ((n + p - 1) / p >= (1ull << 32)) return PSS_EINVAL;

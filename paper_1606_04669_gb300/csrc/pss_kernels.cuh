@@ -35,6 +35,7 @@ inline cudaError_t ensure_kernel_attrs(const void* kern) {
   return e;
 }
 
+constexpr uint32_t SS_SMEM_MAX_K = 4096;  // larger k keep part of the summarize and merge state in HBM
 constexpr int SS_BS = 512;     // threads per CTA of the summarize kernel
 constexpr int SS_IPT = 2;      // items per thread per window (window = SS_BS * SS_IPT)
 constexpr int MERGE_BS = 512;  // threads per CTA of the combine kernel

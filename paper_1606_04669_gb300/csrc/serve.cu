@@ -330,7 +330,7 @@ void destroy(pss_server* sv) {
 extern "C" int pss_server_create(const pss_server_config* cfg, pss_server** out) {
   if (!cfg || !out) return PSS_EINVAL;
   *out = nullptr;
-  if (cfg->tenants == 0 || cfg->k < 2 || cfg->k > PSS_MAX_K || cfg->max_batch == 0 ||
+  if (cfg->tenants == 0 || cfg->k < 2 || cfg->k > PSS_MAX_K_RESIDENT || cfg->max_batch == 0 ||
       cfg->max_inflight == 0)
     return PSS_EINVAL;
   pss_server* sv = new (std::nothrow) pss_server;

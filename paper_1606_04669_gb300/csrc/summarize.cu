@@ -140,22 +140,33 @@ __host__ __device__ inline uint32_t ilog2c(uint32_t x) {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-template <typename ItemT, int BS, int IPT>
-__host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSmem<ItemT>* out) {
+// Shared-memory layout of one CTA (returns its bytes).  BIG (k above what
+// fits): the bucket list, its log, each slot's cell, the first-hit positions
+// and the large rebuild sort live in a per-CTA slice of global memory
+// (gbase; the bytes go to *gbytes), the table is sized for <= 3/4 load, and
+// the candidate list holds one chunk less.
+template <typename ItemT, int BS, int IPT, bool BIG>
+__host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, unsigned char* gbase,
+                                           SSSmem<ItemT>* out, size_t* gbytes = nullptr) {
   constexpr uint32_t W = BS * IPT;
   SSSmem<ItemT> L;
-  // room for k counters and a window of pending items at <= 1/2 load
-  const uint32_t nbk = (k + W + 1) / 2;
+  // room for k counters and a window of pending items at <= 1/2 load (3/4 BIG)
+  const uint32_t nbk = BIG ? (k + W + 2) / 3 : (k + W + 1) / 2;
   L.NB = next_pow2(nbk < 16 ? 16 : nbk);
   L.nbshift = 32 - ilog2c(L.NB);
   L.NBW = (L.NB + 31) / 32;
-  L.CMAX = W + 2 * BS;
+  L.CMAX = BIG ? W + BS : W + 2 * BS;
   L.SORTN = next_pow2(k);
-  size_t off = 0;
+  size_t off = 0, goff = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off = align16(off + bytes);
     return base + o;
+  };
+  auto gtake = [&](size_t bytes) {
+    size_t o = goff;
+    goff = align16(goff + bytes);
+    return gbase + o;
   };
   L.item = (ItemT*)take(sizeof(ItemT) * k);
   L.cnt = (uint32_t*)take(4ull * k);
@@ -164,10 +175,17 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
   L.cell = (uint32_t*)take(16ull * L.NB);
   L.ovf = (uint32_t*)take(8ull * L.NBW);
-  L.hfirst = (uint32_t*)take(4ull * k);
-  L.cellof = (uint16_t*)take(2ull * k);
-  L.list = (uint16_t*)take(2ull * k);
-  L.logq = (uint16_t*)take(2ull * k);
+  if (BIG) {
+    L.hfirst = (uint32_t*)gtake(4ull * k);
+    L.cellof = (uint16_t*)gtake(2ull * k);
+    L.list = (uint16_t*)gtake(2ull * k);
+    L.logq = (uint16_t*)gtake(2ull * k);
+  } else {
+    L.hfirst = (uint32_t*)take(4ull * k);
+    L.cellof = (uint16_t*)take(2ull * k);
+    L.list = (uint16_t*)take(2ull * k);
+    L.logq = (uint16_t*)take(2ull * k);
+  }
   const size_t u0 = off;
   L.wbuf = (ItemT*)take(sizeof(ItemT) * W);
   L.ppos = (uint32_t*)take(4ull * W);
@@ -188,19 +206,29 @@ __host__ __device__ inline size_t ss_carve(uint32_t k, unsigned char* base, SSSm
   // The rebuild sort reuses the window scratch
   // (after wbuf, which holds the next window's items, copied in during the
   // window's last phases)
-  const size_t s0 = u0 + align16(sizeof(ItemT) * W);
-  L.rkey = (uint32_t*)(base + s0);
-  L.rpay = (uint16_t*)(base + s0 + align16(4ull * L.SORTN));
-  const size_t sort_end = s0 + align16(4ull * L.SORTN) + align16(2ull * L.SORTN);
-  if (sort_end > off) off = sort_end;
+  if (BIG) {
+    L.rkey = (uint32_t*)gtake(4ull * L.SORTN);
+    L.rpay = (uint16_t*)gtake(2ull * L.SORTN);
+  } else {
+    const size_t s0 = u0 + align16(sizeof(ItemT) * W);
+    L.rkey = (uint32_t*)(base + s0);
+    L.rpay = (uint16_t*)(base + s0 + align16(4ull * L.SORTN));
+    const size_t sort_end = s0 + align16(4ull * L.SORTN) + align16(2ull * L.SORTN);
+    if (sort_end > off) off = sort_end;
+  }
   // The final sort reuses everything after touch (the state is dead by then).
   L.fkey = (u64*)(base + after_touch);
   L.fpay = (uint16_t*)(base + after_touch + 8ull * L.SORTN);
-  L.ferr = (uint32_t*)(base + after_touch + 8ull * L.SORTN + align16(2ull * L.SORTN));
-  const size_t final_end =
-      align16(after_touch + 8ull * L.SORTN + align16(2ull * L.SORTN) + 4ull * k);
+  size_t final_end = align16(after_touch + 8ull * L.SORTN + align16(2ull * L.SORTN));
+  if (BIG) {
+    L.ferr = (uint32_t*)gtake(4ull * k);
+  } else {
+    L.ferr = (uint32_t*)(base + final_end);
+    final_end = align16(final_end + 4ull * k);
+  }
   if (final_end > off) off = final_end;
   if (out) *out = L;
+  if (gbytes) *gbytes = goff;
   return off;
 }
 
@@ -582,10 +610,10 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group 0;
 
 // The summary of block r of p (Algorithm 1 bounds over n items) into node
 // `node` of `out`; called by all threads of the CTA.
-template <typename ItemT, int BS, int IPT>
+template <typename ItemT, int BS, int IPT, bool BIG>
 __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t p, uint32_t r,
                                 const SetView<ItemT>& out, uint32_t node, unsigned char* smem,
-                                SSState& S_) {
+                                unsigned char* gslice, SSState& S_) {
   constexpr uint32_t W = BS * IPT;
   // bit fields of a per-thread count in [0, IPT]
   constexpr uint32_t kCountBits = IPT < 2 ? 1u : (IPT < 4 ? 3u : (IPT < 8 ? 7u : 15u));
@@ -593,7 +621,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   B.k = out.k;
   B.S = &S_;
   B.par = 0;
-  ss_carve<ItemT, BS, IPT>(B.k, smem, &B.s);
+  ss_carve<ItemT, BS, IPT, BIG>(B.k, smem, gslice, &B.s);
   SSState& S = S_;
   auto& s = B.s;
   const uint32_t k = B.k;
@@ -1103,13 +1131,16 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   }
 }
 
-template <typename ItemT, int BS, int IPT>
+template <typename ItemT, int BS, int IPT, bool BIG>
 __global__ void __launch_bounds__(BS, 2) ss_block_kernel(const ItemT* __restrict__ items, u64 n,
                                                       uint32_t p, uint32_t r0,
-                                                      SetView<ItemT> out, uint32_t node0) {
+                                                      SetView<ItemT> out, uint32_t node0,
+                                                      unsigned char* gscratch, size_t gslice) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SSState S;
-  summarize_block<ItemT, BS, IPT>(items, n, p, r0 + blockIdx.x, out, node0 + blockIdx.x, smem, S);
+  summarize_block<ItemT, BS, IPT, BIG>(items, n, p, r0 + blockIdx.x, out, node0 + blockIdx.x,
+                                       smem, BIG ? gscratch + (size_t)blockIdx.x * gslice : nullptr,
+                                       S);
 }
 
 // Persistent form for many streams: each CTA takes (stream, block) tasks from
@@ -1131,8 +1162,8 @@ __global__ void __launch_bounds__(BS, 2) ss_batch_kernel(const BatchStream* __re
     const BatchTask task = tasks[t];
     const BatchStream st = streams[task.stream];
     const SetView<ItemT> out = set_view_dev<ItemT>(st.level0, st.p, st.k);
-    summarize_block<ItemT, BS, IPT>((const ItemT*)st.items, st.n, st.p, task.index, out,
-                                    task.index, smem, S);
+    summarize_block<ItemT, BS, IPT, false>((const ItemT*)st.items, st.n, st.p, task.index, out,
+                                           task.index, smem, nullptr, S);
     __syncthreads();
   }
 }
@@ -1147,7 +1178,8 @@ uint32_t warp_kmax() { return g_warp_kmax.load(); }
 
 template <typename ItemT>
 size_t ss_smem_bytes(uint32_t k) {
-  return ss_carve<ItemT, SS_BS, SS_IPT>(k, nullptr, nullptr);
+  return k > SS_SMEM_MAX_K ? ss_carve<ItemT, SS_BS, SS_IPT, true>(k, nullptr, nullptr, nullptr)
+                           : ss_carve<ItemT, SS_BS, SS_IPT, false>(k, nullptr, nullptr, nullptr);
 }
 
 template <typename ItemT>
@@ -1157,18 +1189,35 @@ cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint3
   if (out.k <= warp_kmax())
     return launch_summarize_warp_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
   const size_t smem = ss_smem_bytes<ItemT>(out.k);
-  auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT>;
+  if (out.k <= SS_SMEM_MAX_K) {
+    auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT, false>;
+    cudaError_t e = ensure_kernel_attrs((const void*)kern);
+    if (e != cudaSuccess) return e;
+    if (count == 0) return cudaSuccess;
+    kern<<<count, SS_BS, smem, stream>>>(items, n, p, r0, out, node0, nullptr, 0);
+    return cudaGetLastError();
+  }
+  // large k: a slice of global scratch per CTA, ordered on the stream
+  auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT, true>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   if (count == 0) return cudaSuccess;
-  kern<<<count, SS_BS, smem, stream>>>(items, n, p, r0, out, node0);
-  return cudaGetLastError();
+  size_t gslice = 0;
+  ss_carve<ItemT, SS_BS, SS_IPT, true>(out.k, nullptr, nullptr, nullptr, &gslice);
+  void* g = nullptr;
+  e = cudaMallocAsync(&g, gslice * count, stream);
+  if (e != cudaSuccess) return e;
+  kern<<<count, SS_BS, smem, stream>>>(items, n, p, r0, out, node0, (unsigned char*)g, gslice);
+  e = cudaGetLastError();
+  cudaError_t f = cudaFreeAsync(g, stream);
+  return e != cudaSuccess ? e : f;
 }
 
 template <typename ItemT>
 cudaError_t launch_summarize_batch(const BatchStream* streams, const BatchTask* tasks,
                                    uint32_t ntasks, uint32_t* counter, uint32_t k, uint32_t grid,
                                    cudaStream_t stream) {
+  if (k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;  // the batch keeps k in shared memory
   const size_t smem = ss_smem_bytes<ItemT>(k);
   auto kern = ss_batch_kernel<ItemT, SS_BS, SS_IPT>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);

@@ -24,7 +24,8 @@ PSS_ECUDA = -4
 PSS_ETIMEOUT = -5
 PSS_EDEVICE = -6
 PSS_ERANGE = -7
-PSS_MAX_K = 4096
+PSS_MAX_K = 8192
+PSS_MAX_K_RESIDENT = 4096
 
 _lock = threading.Lock()
 _lib = None

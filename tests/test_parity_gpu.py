@@ -283,3 +283,35 @@ def test_fuzz_small_universes_cta_kernel(warp_kmax):
     # The fuzz cases again with every block on the window-parallel CTA kernel.
     warp_kmax(0)
     test_fuzz_small_universes()
+
+
+@pytest.mark.parametrize("n,k,p,w,s,log2u,seed", [
+    (120_000, 4097, 3, 4, 0.9, 20, 201),
+    (200_000, 6000, 2, 8, 1.1, 24, 202),
+    (150_000, 8000, 3, 4, 0.6, 32, 203),    # the paper's largest k; nearly every item misses
+    (300_000, 8192, 2, 8, 1.5, 32, 204),
+    (40_000, 8192, 5, 4, 1.0, 12, 205),     # fewer distinct items than k
+])
+def test_large_k_beyond_shared_memory(n, k, p, w, s, log2u, seed):
+    # k > 4096 keeps part of the block and combine state in HBM scratch.
+    x = oracle.gen_zipf(n, seed=seed, s=s, log2u=log2u, width=w)
+    compare_tree(x, k, p)
+
+
+def test_large_k_merge_and_resident_limits():
+    xa = oracle.gen_zipf(100_000, seed=211, s=0.8, log2u=24)
+    xb = oracle.gen_zipf(90_000, seed=212, s=1.2, log2u=24)
+    a = P.summarize(to_dev(xa), 8000, 2)
+    b = P.summarize(to_dev(xb), 8000, 3)
+    ra, _ = oracle.parallel_space_saving(xa, 8000, 2)
+    rb, _ = oracle.parallel_space_saving(xb, 8000, 3)
+    e = P.merge(a, b).export()
+    rc = oracle.combine(ra, rb, 8000)
+    assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == summary_entries(rc)
+    # the batch and server keep every summary in shared memory: k <= 4096
+    with pytest.raises(P.PssError) as ei:
+        P.Batch([to_dev(xa)], [P.PSS_MAX_K_RESIDENT + 1])
+    assert ei.value.code == P.PSS_EINVAL
+    with pytest.raises(P.PssError) as ei:
+        P.Server(2, P.PSS_MAX_K_RESIDENT + 1)
+    assert ei.value.code == P.PSS_EINVAL
