@@ -37,6 +37,12 @@
 // Deletions clear the cell (no tombstones); the bits are recounted at every
 // bucket-list rebuild, so they stay close to exact.
 //
+// Items: the next window is copied into shared memory (cp.async) as soon as
+// the cut fixes where it starts, while the window's last phases run.  Each
+// counter's err is written once, at insertion, into the block's output node.
+// Above SS_SMEM_MAX_K counters the least-touched per-counter arrays live in a
+// per-CTA slice of HBM scratch instead of shared memory.
+//
 // Output: the block's summary sorted by item ascending, with size, minimum m
 // (the minimum count if k counters are in use, else 0) and the block length.
 #include <atomic>
@@ -1034,7 +1040,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     // remaining phases run (nothing reads wbuf from here on)
     if (t0 + cut < len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, t0 + cut, len);
 
-    // ---- P9: log in time order, reset the window scratch, advance
+    // ---- P7: log in time order, reset the window scratch, advance
     const uint32_t log0 = S.log_len;  // read before the scan's barrier: warp 0 rewrites it
     uint32_t nl = 0;
     uint16_t lg[IPT];
