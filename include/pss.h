@@ -308,6 +308,19 @@ int pss_export(const pss_summary* summary, pss_entry* host_out, uint32_t cap, ui
 /* k and item width of a summary. */
 int pss_summary_info(const pss_summary* summary, uint32_t* k, int* item_bytes);
 
+/*
+ * pss_import — a device summary from canonical host entries, the output of
+ * pss_export: entries[0 .. size) with distinct items, the summary's minimum
+ * m and the stream length n_covered it describes.  Summaries are mergeable
+ * (Algorithm 2), so an exported summary with its n_covered is a complete
+ * checkpoint: importing it and merging on (pss_merge) continues a
+ * computation exactly.  size <= k <= PSS_MAX_K; item_bytes 4 (items must fit
+ * in 32 bits) or 8; duplicate items or size > k are PSS_EINVAL.  The entries
+ * are read before the call returns; the summary is ready in stream order.
+ */
+int pss_import(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered, uint32_t k,
+               int item_bytes, void* stream, pss_summary** out);
+
 /* Release a summary (stream-ordered on the stream that created it). */
 void pss_free(pss_summary* summary);
 
@@ -384,6 +397,13 @@ int pss_server_result(pss_server* server, uint64_t id, pss_entry* segment_out, u
  * tenant work enqueued so far). */
 int pss_server_tenant_export(pss_server* server, uint32_t tenant, pss_entry* host_out, uint32_t cap,
                              uint32_t* size, uint64_t* m, uint64_t* n_covered);
+
+/* Restore a tenant's resident summary from a checkpoint (pss_server_tenant_export
+ * of an earlier server with the same k): entries, m and n_covered as pss_import
+ * takes them.  Only before pss_server_start (else PSS_EINVAL); the tenant's
+ * later segments merge into it as if the earlier server had continued. */
+int pss_server_tenant_import(pss_server* server, uint32_t tenant, const pss_entry* entries,
+                             uint32_t size, uint64_t m, uint64_t n_covered);
 
 /* Stop the scheduler (after the current tick) and release everything. */
 void pss_server_destroy(pss_server* server);

@@ -3,6 +3,7 @@
 // Argument checks, device memory of summaries (CUDA stream-ordered
 // allocator) and kernel sequencing.  Every step of the computation runs in
 // the kernels of summarize.cu, merge.cu and canon.cu.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -283,6 +284,33 @@ int canon_out(void* set_mem, uint32_t nodes, uint32_t node, uint32_t k, int w, u
 
 namespace pss {
 
+// Host image of a one-node set (set_layout(1, k, w)) holding the canonical
+// entries in item order; PSS_EINVAL on duplicates, size > k, or items wider
+// than w bytes.
+int summary_image(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered,
+                  uint32_t k, int w, std::vector<char>& image) {
+  if ((size && !entries) || size > k || (w != 4 && w != 8)) return PSS_EINVAL;
+  std::vector<pss_entry> e(entries, entries + size);
+  std::sort(e.begin(), e.end(), [](const pss_entry& a, const pss_entry& b) { return a.item < b.item; });
+  for (uint32_t i = 0; i < size; ++i) {
+    if (i && e[i].item == e[i - 1].item) return PSS_EINVAL;
+    if (w == 4 && e[i].item > 0xFFFFFFFFull) return PSS_EINVAL;
+  }
+  const SetLayout L = set_layout(1, k, w);
+  image.assign(L.total, 0);
+  char* b = image.data();
+  for (uint32_t i = 0; i < size; ++i) {
+    if (w == 4) ((uint32_t*)(b + L.item))[i] = (uint32_t)e[i].item;
+    else ((uint64_t*)(b + L.item))[i] = e[i].item;
+    ((uint64_t*)(b + L.count))[i] = e[i].count;
+    ((uint64_t*)(b + L.err))[i] = e[i].err;
+  }
+  *(uint32_t*)(b + L.size) = size;
+  *(uint64_t*)(b + L.m) = m;
+  *(uint64_t*)(b + L.ncov) = n_covered;
+  return PSS_OK;
+}
+
 // The root set (one node) of the path over d_items, allocated stream-ordered
 // on s (release with cudaFreeAsync); used by the serving runtime.
 int summarize_to_set(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p,
@@ -509,6 +537,40 @@ int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* hos
   if (cap > 0 && !host_out) return PSS_EINVAL;
   return canon_out(summary->mem, 1, 0, summary->k, summary->item_bytes, n, k, 1, host_out, cap,
                    n_out, (cudaStream_t)stream);
+}
+
+int pss_import(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered, uint32_t k,
+               int item_bytes, void* stream, pss_summary** out) {
+  if (!out) return PSS_EINVAL;
+  *out = nullptr;
+  int rc = check_k_width(k, item_bytes);
+  if (rc) return rc;
+  std::vector<char> image;
+  if ((rc = pss::summary_image(entries, size, m, n_covered, k, item_bytes, image))) return rc;
+  cudaError_t e = prepare_device();
+  if (e != cudaSuccess) return from_cuda(e);
+  cudaStream_t s = (cudaStream_t)stream;
+  void* mem = nullptr;
+  e = cudaMallocAsync(&mem, image.size(), s);
+  if (e != cudaSuccess) return from_cuda(e);
+  // pageable source: the call returns once the bytes are staged
+  e = cudaMemcpyAsync(mem, image.data(), image.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(mem, s);
+    return from_cuda(e);
+  }
+  pss_summary* sm = new (std::nothrow) pss_summary;
+  if (!sm) {
+    cudaFreeAsync(mem, s);
+    return PSS_ENOMEM;
+  }
+  sm->k = k;
+  sm->item_bytes = item_bytes;
+  sm->mem = mem;
+  sm->stream = s;
+  *out = sm;
+  return PSS_OK;
 }
 
 int pss_query_mode(const pss_summary* summary, uint64_t n, uint32_t k, int mode, pss_entry* host_out,

@@ -6,6 +6,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pss_internal.cuh"
 #include "pss_kernels.cuh"
 
@@ -44,6 +46,9 @@ void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_rela
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 ProfScope::ProfScope(int cat, cudaStream_t s, uint64_t units) : cat_(cat), s_(s), units_(units) {
+  // a host range per kernel group for timeline tools (no cost without one)
+  static const char* const names[3] = {"pss summarize", "pss merge tree", "pss query"};
+  nvtxRangePushA(names[cat_ >= 0 && cat_ < 3 ? cat_ : 0]);
   if (!g_enabled.load(std::memory_order_relaxed)) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
@@ -57,6 +62,7 @@ ProfScope::ProfScope(int cat, cudaStream_t s, uint64_t units) : cat_(cat), s_(s)
 }
 
 ProfScope::~ProfScope() {
+  nvtxRangePop();
   if (!active_) return;
   std::lock_guard<std::mutex> lock(g_mu);
   cudaEventRecord(end_, s_);

@@ -160,6 +160,10 @@ class ProfScope {
   bool active_ = false;
 };
 
+// Host image of a one-node set holding canonical entries (api.cu).
+int summary_image(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered,
+                  uint32_t k, int w, std::vector<char>& image);
+
 // Adds n (modulo 2^64) to the library's launch counter; launch_count reads it.
 void count_launches(uint64_t n);
 uint64_t launch_count();

@@ -428,6 +428,21 @@ extern "C" int pss_server_result(pss_server* sv, uint64_t id, pss_entry* seg_out
   return PSS_OK;
 }
 
+extern "C" int pss_server_tenant_import(pss_server* sv, uint32_t tenant, const pss_entry* entries,
+                                        uint32_t size, uint64_t m, uint64_t n_covered) {
+  if (!sv || tenant >= sv->cfg.tenants) return PSS_EINVAL;
+  std::vector<char> image;
+  int rc = summary_image(entries, size, m, n_covered, sv->cfg.k, 4, image);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->started) return PSS_EINVAL;
+  cudaError_t e = cudaMemcpy(sv->tenant_mem[sv->tenant_cur[tenant]][tenant], image.data(),
+                             image.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return from_cuda(e);
+  sv->tenant_items[tenant] = n_covered;
+  return PSS_OK;
+}
+
 extern "C" int pss_server_tenant_export(pss_server* sv, uint32_t tenant, pss_entry* host_out,
                                         uint32_t cap, uint32_t* size, uint64_t* m,
                                         uint64_t* n_covered) {

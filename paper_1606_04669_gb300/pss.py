@@ -130,6 +130,9 @@ SIGNATURES = {
     "pss_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), u32, u32p]),
     "pss_server_result": (ctypes.c_int, [vp, u64, ctypes.POINTER(Entry), u32p, ctypes.POINTER(Entry),
                                          u32p]),
+    "pss_import": (ctypes.c_int, [ctypes.POINTER(Entry), u32, u64, u64, u32, ctypes.c_int, vp,
+                                  ctypes.POINTER(vp)]),
+    "pss_server_tenant_import": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u64, u64]),
     "pss_server_tenant_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p,
                                                 u64p]),
     "pss_server_destroy": (None, [vp]),
@@ -371,6 +374,25 @@ def summarize_tree(items, k: int, p: int, stream=None) -> Tree:
     return Tree(h.value)
 
 
+def _entries_from(ex: "Exported"):
+    n = ex.size
+    buf = (Entry * max(n, 1))()
+    for i in range(n):
+        buf[i].item = int(ex.item[i])
+        buf[i].count = int(ex.count[i])
+        buf[i].err = int(ex.err[i])
+    return buf, n
+
+
+def import_summary(ex: "Exported", k: int, item_bytes: int = 4, stream=None) -> Summary:
+    """pss_import: a device summary from an exported one (a checkpoint)."""
+    buf, n = _entries_from(ex)
+    h = vp()
+    _check(load().pss_import(buf, n, int(ex.m), int(ex.n_covered), int(k), int(item_bytes),
+                             vp(_stream_handle(stream)), ctypes.byref(h)), "pss_import")
+    return Summary(h.value)
+
+
 def merge(a: Summary, b: Summary, stream=None) -> Summary:
     """pss_merge: combine(a, b, k) of Algorithm 2."""
     h = vp()
@@ -570,6 +592,12 @@ class Server:
         sa = _entries_to_arrays(a, na.value)
         sb = _entries_to_arrays(b, nb.value)
         return Exported(*sa, 0, 0), Exported(*sb, 0, 0)
+
+    def tenant_import(self, tenant: int, ex: Exported):
+        """pss_server_tenant_import: restore a tenant from a checkpoint (before start)."""
+        buf, n = _entries_from(ex)
+        _check(load().pss_server_tenant_import(self._h, int(tenant), buf, n, int(ex.m),
+                                               int(ex.n_covered)), "pss_server_tenant_import")
 
     def tenant_export(self, tenant: int) -> Exported:
         buf = (Entry * self.k)()
