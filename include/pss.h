@@ -375,7 +375,9 @@ typedef struct {
 int pss_server_create(const pss_server_config* config, pss_server** out);
 
 /* Queue requests (any order; each is released at its arrival time).  May be
- * called before or after pss_server_start. */
+ * called before or after pss_server_start.  Request ids must be unique among
+ * the requests whose results have not been read (or that have not failed):
+ * a repeated id rejects the whole call with PSS_EINVAL. */
 int pss_server_submit(pss_server* server, const pss_request* requests, uint32_t count);
 
 /* Start the clock and the scheduler thread. */
@@ -397,6 +399,12 @@ int pss_server_result(pss_server* server, uint64_t id, pss_entry* segment_out, u
  * tenant work enqueued so far). */
 int pss_server_tenant_export(pss_server* server, uint32_t tenant, pss_entry* host_out, uint32_t cap,
                              uint32_t* size, uint64_t* m, uint64_t* n_covered);
+
+/* Fault injection for tests of the serving layer: the next `count` segment
+ * allocations fail as if the device were out of memory.  Each such request
+ * completes with status PSS_ENOMEM and leaves its tenant untouched; the
+ * other requests of its tick, and every later one, proceed. */
+int pss_server_inject_alloc_failures(pss_server* server, uint32_t count);
 
 /* Restore a tenant's resident summary from a checkpoint (pss_server_tenant_export
  * of an earlier server with the same k): entries, m and n_covered as pss_import

@@ -26,6 +26,7 @@
 #include <new>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "pss_internal.cuh"
@@ -77,6 +78,8 @@ struct pss_server {
   std::deque<Tick> inflight;
   std::vector<pss_completion> completions;
   std::unordered_map<uint64_t, Result> results;
+  std::unordered_set<uint64_t> live;     // ids submitted and not yet read (or failed)
+  std::atomic<uint32_t> fail_allocs{0};  // injected segment allocation failures to come
   uint64_t submitted = 0, completed = 0;
   // device state
   std::vector<void*> tenant_mem[2];
@@ -123,23 +126,36 @@ void launch_tick(pss_server* sv, Tick& t) {
   std::vector<const void*> items(nr);
   std::vector<uint64_t> ns(nr);
   std::vector<uint32_t> ks(nr, k), ps(nr);
+  std::vector<uint32_t> bidx(nr, ~0u);  // request -> its stream in the tick's batch
+  uint32_t nb = 0;
   for (uint32_t i = 0; i < nr; ++i) {
     Admitted& a = t.reqs[i];
-    items[i] = a.r.d_items;
-    ns[i] = a.r.n;
-    ps[i] = a.p;
-    if (!items[i] && a.r.n) {
-      cudaError_t e = cudaMallocAsync(&a.gen, a.r.n * 4, seg);
+    const void* src = a.r.d_items;
+    if (!src && a.r.n) {
+      cudaError_t e = cudaSuccess;
+      uint32_t f = sv->fail_allocs.load();
+      while (f && !sv->fail_allocs.compare_exchange_weak(f, f - 1)) {
+      }
+      if (f) e = cudaErrorMemoryAllocation;  // injected fault
+      if (e == cudaSuccess) e = cudaMallocAsync(&a.gen, a.r.n * 4, seg);
       if (e == cudaSuccess)
         e = launch_gen_zipf(a.gen, a.r.n, 4, a.r.seed, a.r.stream_id, 0, a.r.s, a.r.log2u, seg);
       if (e == cudaSuccess) count_launches(1);
       if (e != cudaSuccess) a.status = from_cuda(e);
-      items[i] = a.gen;
+      src = a.gen;
     }
+    if (a.status != PSS_OK) continue;  // a failed request leaves its tenant untouched
+    bidx[i] = nb++;
+    items[bidx[i]] = src;
+    ns[bidx[i]] = a.r.n;
+    ps[bidx[i]] = a.p;
   }
-  pss_batch_desc desc{nr, 4, items.data(), ns.data(), ks.data(), ps.data(), nullptr};
-  int rc = pss_batch_create(&desc, sv->plan_stream, &t.batch);
-  if (rc == PSS_OK) rc = pss_batch_run(t.batch, 0, seg);
+  int rc = PSS_OK;
+  if (nb) {
+    pss_batch_desc desc{nb, 4, items.data(), ns.data(), ks.data(), ps.data(), nullptr};
+    rc = pss_batch_create(&desc, sv->plan_stream, &t.batch);
+    if (rc == PSS_OK) rc = pss_batch_run(t.batch, 0, seg);
+  }
   if (rc != PSS_OK) {
     for (Admitted& a : t.reqs)
       if (a.status == PSS_OK) a.status = rc;
@@ -157,7 +173,7 @@ void launch_tick(pss_server* sv, Tick& t) {
     const int cur = sv->tenant_cur[T];
     void* in = sv->tenant_mem[cur][T];
     void* out = sv->tenant_mem[cur ^ 1][T];
-    void* root = batch_root(t.batch, i);
+    void* root = batch_root(t.batch, bidx[i]);
     cudaError_t e = launch_merge_pair<uint32_t>(set_view<uint32_t>(in, 1, k), 0,
                                                 set_view<uint32_t>(root, 1, k), 0,
                                                 set_view<uint32_t>(out, 1, k), ts);
@@ -173,7 +189,7 @@ void launch_tick(pss_server* sv, Tick& t) {
     count_launches(1);
     pss_entry* sq;
     uint32_t* sqn;
-    batch_query_device(t.batch, i, &sq, &sqn);
+    batch_query_device(t.batch, bidx[i], &sq, &sqn);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(sv->h_q + (size_t)a.slot * 2 * k, sq, sizeof(pss_entry) * k,
                           cudaMemcpyDeviceToHost, ts);
@@ -221,6 +237,8 @@ void reap(pss_server* sv) {
         res.seg.assign(q, q + std::min(qn[0], k));
         res.ten.assign(q + k, q + k + std::min(qn[2], k));
         sv->results[a.r.id] = std::move(res);
+      } else {
+        sv->live.erase(a.r.id);  // nothing to read
       }
       sv->completions.push_back(c);
       sv->free_slots.push_back(a.slot);
@@ -375,7 +393,14 @@ extern "C" int pss_server_submit(pss_server* sv, const pss_request* reqs, uint32
     if (r.p && (r.n + r.p - 1) / r.p >= (1ull << 32)) return PSS_EINVAL;
   }
   std::lock_guard<std::mutex> lock(sv->mu);
-  for (uint32_t i = 0; i < count; ++i) sv->pending.push_back(reqs[i]);
+  // ids must be unique among the requests not yet read back
+  std::unordered_set<uint64_t> mine;
+  for (uint32_t i = 0; i < count; ++i)
+    if (sv->live.count(reqs[i].id) || !mine.insert(reqs[i].id).second) return PSS_EINVAL;
+  for (uint32_t i = 0; i < count; ++i) {
+    sv->pending.push_back(reqs[i]);
+    sv->live.insert(reqs[i].id);
+  }
   sv->pending_sorted = false;
   sv->submitted += count;
   sv->cv.notify_all();
@@ -425,6 +450,13 @@ extern "C" int pss_server_result(pss_server* sv, uint64_t id, pss_entry* seg_out
   *n_seg = (uint32_t)it->second.seg.size();
   *n_ten = (uint32_t)it->second.ten.size();
   sv->results.erase(it);
+  sv->live.erase(id);
+  return PSS_OK;
+}
+
+extern "C" int pss_server_inject_alloc_failures(pss_server* sv, uint32_t count) {
+  if (!sv) return PSS_EINVAL;
+  sv->fail_allocs.store(count);
   return PSS_OK;
 }
 

@@ -133,6 +133,7 @@ SIGNATURES = {
     "pss_import": (ctypes.c_int, [ctypes.POINTER(Entry), u32, u64, u64, u32, ctypes.c_int, vp,
                                   ctypes.POINTER(vp)]),
     "pss_server_tenant_import": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u64, u64]),
+    "pss_server_inject_alloc_failures": (ctypes.c_int, [vp, u32]),
     "pss_server_tenant_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p,
                                                 u64p]),
     "pss_server_destroy": (None, [vp]),
@@ -592,6 +593,11 @@ class Server:
         sa = _entries_to_arrays(a, na.value)
         sb = _entries_to_arrays(b, nb.value)
         return Exported(*sa, 0, 0), Exported(*sb, 0, 0)
+
+    def inject_alloc_failures(self, count: int):
+        """pss_server_inject_alloc_failures (fault injection for tests)."""
+        _check(load().pss_server_inject_alloc_failures(self._h, int(count)),
+               "pss_server_inject_alloc_failures")
 
     def tenant_import(self, tenant: int, ex: Exported):
         """pss_server_tenant_import: restore a tenant from a checkpoint (before start)."""

@@ -102,3 +102,47 @@ def test_served_tiny_budget_and_caller_segments():
         segq, tq, _ = expect[r["id"]]
         assert ents(res[r["id"]][0]) == summary_entries(segq)
         assert ents(res[r["id"]][1]) == summary_entries(tq)
+
+
+def test_served_duplicate_ids_rejected():
+    srv = P.Server(2, 32, budget_bytes=64 << 20, max_batch=4)
+    reqs = make_requests(4, 2, seed=5, span=0.01)
+    srv.submit(reqs[:2])
+    for bad in ([reqs[1]], [reqs[2], dict(reqs[2])]):  # a live id; a repeat inside one call
+        with pytest.raises(P.PssError) as ei:
+            srv.submit(bad)
+        assert ei.value.code == P.PSS_EINVAL
+    srv.start()
+    srv.wait(120)
+    for r in reqs[:2]:
+        srv.result(r["id"])
+    srv.submit([dict(reqs[0], arrival=0.0)])  # read back: its id is free again
+    srv.wait(120)
+    srv.close()
+
+
+def test_served_injected_allocation_failures():
+    # Host-side fault injection: three segment allocations fail.  Those
+    # requests complete with PSS_ENOMEM and leave their tenants untouched;
+    # everything else equals a run of the trace without them.
+    tenants, k = 4, 48
+    reqs = make_requests(60, tenants, seed=7)
+    srv = P.Server(tenants, k, budget_bytes=64 << 20, max_batch=6)
+    srv.inject_alloc_failures(3)
+    srv.submit(reqs)
+    srv.start()
+    srv.wait(300)
+    comps = {c["id"]: c for c in srv.poll()}
+    assert len(comps) == len(reqs)
+    failed = {i for i, c in comps.items() if c["status"] != 0}
+    assert len(failed) == 3 and all(comps[i]["status"] == P.PSS_ENOMEM for i in failed)
+    res = {r["id"]: srv.result(r["id"]) for r in reqs if r["id"] not in failed}
+    final = {t: srv.tenant_export(t) for t in range(tenants)}
+    srv.close()
+    rest = [r for r in reqs if r["id"] not in failed]
+    _, res2, final2 = run_server(rest, tenants, k, budget_bytes=64 << 20, max_batch=6)
+    for r in rest:
+        assert ents(res[r["id"]][0]) == ents(res2[r["id"]][0]), r["id"]
+        assert ents(res[r["id"]][1]) == ents(res2[r["id"]][1]), r["id"]
+    for t in range(tenants):
+        assert ents(final[t]) == ents(final2[t])
