@@ -194,7 +194,10 @@ typedef struct {
 } pss_batch_desc;
 
 /* The planner's block count for a stream of n items with k counters: a pure
- * function of its arguments (never of load), so a result can be replayed. */
+ * function of its arguments (never of load), so a result can be replayed.
+ * Block lengths come from the autotuner's measured table per (k class:
+ * <= 64, <= 256, <= 1024, larger; skew class: nearest of 0.8, 1.4, 2.0;
+ * skew_hint <= 0 means unknown and takes 1.4). */
 uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint);
 
 /* Plan and allocate a batch (device memory for every stream's tree, task

@@ -8,6 +8,7 @@
 // the same k and p (the tree of Algorithm 1 and the combine of Algorithm 2 are
 // per stream; batching only changes the launch structure).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -96,11 +97,19 @@ struct pss_batch {
 
 extern "C" uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint) {
   (void)item_bytes;
-  (void)skew_hint;
-  // Block length: long enough that the per-block fixed work (table fill,
-  // final sort, summary write of up to k entries) stays small next to the
-  // block's items, short enough to give every SM several blocks.
-  const uint64_t len = k <= 256 ? (1ull << 17) : (k <= 1024 ? (1ull << 18) : (1ull << 19));
+  // Block length per (k class, skew class), measured on a GB300 by the
+  // project's autotuner (one 2^27-item stream per class through the batch
+  // path; paper_1606_04669_gb300/autotune.py holds the same table): short
+  // blocks for small k (more blocks in flight), 2^17 at k = 4096.  An unknown
+  // skew (hint <= 0) takes the middle class.
+  const double sk = skew_hint > 0.0 ? skew_hint : 1.4;
+  static const double classes[3] = {0.8, 1.4, 2.0};
+  int sc = 0;  // the nearest class, ties to the lower one
+  for (int c = 1; c < 3; ++c)
+    if (std::fabs(sk - classes[c]) < std::fabs(sk - classes[sc])) sc = c;
+  static const uint32_t len_log2[4][3] = {{15, 15, 15}, {15, 15, 15}, {15, 16, 16}, {17, 17, 17}};
+  const int kc = k <= 64 ? 0 : (k <= 256 ? 1 : (k <= 1024 ? 2 : 3));
+  const uint64_t len = 1ull << len_log2[kc][sc];
   uint64_t p = (n + len - 1) / len;
   if (p == 0) p = 1;
   while ((n + p - 1) / p >= (1ull << 32)) ++p;

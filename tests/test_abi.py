@@ -45,3 +45,18 @@ def test_strerror_without_gpu():
     assert lib.pss_strerror(0) == b"success"
     assert lib.pss_strerror(-2).startswith(b"summaries have different k")
     assert lib.pss_abi_version() == 1
+
+
+def test_planner_matches_the_autotuned_table():
+    # pss_plan_blocks (host arithmetic, no device) and autotune.plan_blocks
+    # read the same measured table.
+    import random
+
+    import paper_1606_04669_gb300 as P
+    from paper_1606_04669_gb300 import autotune as A
+    rng = random.Random(5)
+    for _ in range(3000):
+        n = rng.randint(0, 10 ** 10)
+        k = rng.choice([2, 64, 65, 256, 257, 1024, 1025, 4096, 8000])
+        s = rng.choice([0.5, 0.8, 1.1, 1.4, 1.7, 2.0, 2.7, rng.uniform(0.3, 3.0)])
+        assert P.plan_blocks(n, k, 4, s) == A.plan_blocks(n, k, s), (n, k, s)
