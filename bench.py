@@ -552,7 +552,8 @@ def main():
         ems, eitems = replica_aggregate(e0.elapsed_time(e1) / esteps, n, dist, "cuda")
         e2e = {"value": eitems / (ems / 1e3), "unit": "items/s", "ms_per_step": ems,
                "h2d_bytes_per_step": n * w, "d2h_bytes_per_step": 8 + 24 * qq.size,
-               "api": "pss_summarize_host + pss_query (pinned host input)"}
+               "api": "pss_summarize_host + pss_query (pinned host input, read in place by the "
+                      "kernels over the CPU-GPU link; pss_set_host_direct(0) stages copies)"}
         del hx
 
     cpu = None

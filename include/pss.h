@@ -95,14 +95,21 @@ int pss_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k, u
                   void* stream, pss_summary** out);
 
 /*
- * pss_summarize_host — pss_summarize for items in HOST memory: the blocks
- * are copied to the device in up to 16 slabs on a library-owned copy stream,
- * each slab's block summaries starting as soon as it has landed (copies
- * overlap the summarize kernel).  h_items should be pinned
- * (cudaHostAlloc/cudaHostRegister) for the copies to be asynchronous; it
- * must stay valid until the work enqueued on stream has completed.
- * Asynchronous on stream.
+ * pss_summarize_host — pss_summarize for items in HOST memory.  Pinned memory
+ * that the device can address (cudaHostAlloc / cudaHostRegister memory is
+ * mapped into the unified address space; on a coherent CPU-GPU link such as
+ * NVLink-C2C the kernels read it at link bandwidth) is read in place by the
+ * summarize kernel.  Other host memory, or every call after
+ * pss_set_host_direct(0), is copied to the device in up to 16 slabs on a
+ * library-owned copy stream, each slab's block summaries starting as soon as
+ * it has landed.  h_items must stay valid until the work enqueued on stream
+ * has completed.  Asynchronous on stream.
  */
+/* Whether pss_summarize_host reads mapped pinned host memory in place (1,
+ * the default) or always stages copies (0).  Results are the same either way.
+ * Process-wide; returns the previous value. */
+int pss_set_host_direct(int on);
+
 int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
                        void* stream, pss_summary** out);
 

@@ -9,4 +9,4 @@ from .pss import (  # noqa: F401
     Exported,
     PssError, Server, Summary, Tree, gen_zipf, lib_path, load, merge, profile_enable, profile_read, strerror,
     plan_blocks, set_warp_kmax, summarize, summarize_host, summarize_tree, exact_counts,
-    QUERY_CANDIDATES, QUERY_GUARANTEED, import_summary)
+    QUERY_CANDIDATES, QUERY_GUARANTEED, import_summary, set_host_direct)

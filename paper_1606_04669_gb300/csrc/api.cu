@@ -4,6 +4,7 @@
 // allocator) and kernel sequencing.  Every step of the computation runs in
 // the kernels of summarize.cu, merge.cu and canon.cu.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -30,6 +31,8 @@ struct pss_tree {
 };
 
 namespace {
+
+std::atomic<int> g_host_direct{1};  // pss_set_host_direct
 
 int from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return PSS_OK;
@@ -366,6 +369,8 @@ int pss_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k, u
   return PSS_OK;
 }
 
+int pss_set_host_direct(int on) { return g_host_direct.exchange(on ? 1 : 0); }
+
 int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t k, uint32_t p,
                        void* stream, pss_summary** out) {
   if (!out) return PSS_EINVAL;
@@ -377,8 +382,24 @@ int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t
   if (rc) return rc;
   std::vector<void*> mems;
   std::vector<uint32_t> nodes;
-  rc = item_bytes == 4 ? run_tree_host<uint32_t>(h_items, n, k, p, s, mems, nodes)
-                       : run_tree_host<u64>(h_items, n, k, p, s, mems, nodes);
+  // Pinned host memory mapped into the device's address space (a coherent
+  // CPU-GPU link): the kernels read the items in place, each block's windows
+  // copied into shared memory one window ahead as for device input.
+  const void* mapped = nullptr;
+  if (n && g_host_direct.load()) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, h_items) == cudaSuccess &&
+        attr.type == cudaMemoryTypeHost && attr.devicePointer)
+      mapped = attr.devicePointer;
+    else
+      cudaGetLastError();  // an unregistered pointer is not an error here
+  }
+  if (mapped)
+    rc = item_bytes == 4 ? run_tree_device<uint32_t>(mapped, n, k, p, s, false, mems, nodes)
+                         : run_tree_device<u64>(mapped, n, k, p, s, false, mems, nodes);
+  else
+    rc = item_bytes == 4 ? run_tree_host<uint32_t>(h_items, n, k, p, s, mems, nodes)
+                         : run_tree_host<u64>(h_items, n, k, p, s, mems, nodes);
   if (rc) return rc;
   pss_summary* sm = new (std::nothrow) pss_summary;
   if (!sm) {

@@ -138,6 +138,7 @@ SIGNATURES = {
                                                 u64p]),
     "pss_server_destroy": (None, [vp]),
     "pss_set_warp_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
+    "pss_set_host_direct": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
     "pss_gen_zipf": (ctypes.c_int, [vp, u64, ctypes.c_int, u64, u32, u64, ctypes.c_double,
@@ -431,6 +432,12 @@ def exact_counts(items, log2u: int, out=None, stream=None):
     _check(load().pss_exact_counts(vp(items.data_ptr()), int(items.numel()), int(w), int(log2u),
                                    vp(out.data_ptr()), vp(_stream_handle(stream))), "pss_exact_counts")
     return out
+
+
+def set_host_direct(on: bool) -> int:
+    """pss_summarize_host reads mapped pinned host memory in place (True) or
+    stages copies (False).  Returns the previous setting."""
+    return int(load().pss_set_host_direct(1 if on else 0))
 
 
 def set_warp_kmax(kmax: int) -> int:

@@ -192,15 +192,24 @@ def test_config2_sampled_blocks_and_full_size_properties():
     tree.close()
 
 
-def test_host_input_path():
-    # pss_summarize_host: slab copies from pinned host memory overlapping the kernels.
-    for (n, k, p, w) in ((500_000, 300, 37, 4), (300_000, 1000, 16, 8), (1000, 50, 40, 4)):
-        x = oracle.gen_zipf(n, seed=21 + k, s=1.1, log2u=20, width=w)
-        h = torch.from_numpy(x.view(np.int32 if w == 4 else np.int64)).pin_memory()
-        e = P.summarize_host(h, k, p).export()
-        r, q = oracle.parallel_space_saving(x, k, p)
-        assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == summary_entries(r)
-        assert (e.m, e.n_covered) == (r.m, r.n_covered)
+@pytest.mark.parametrize("direct,pinned", [(True, True), (False, True), (True, False)])
+def test_host_input_path(direct, pinned):
+    # pss_summarize_host: pinned memory read in place by the kernels, or slab
+    # copies overlapping the kernels (direct reads off, or pageable memory).
+    prev = P.set_host_direct(direct)
+    try:
+        for (n, k, p, w) in ((500_000, 300, 37, 4), (300_000, 1000, 16, 8), (1000, 50, 40, 4),
+                             (200_000, 6000, 3, 4)):
+            x = oracle.gen_zipf(n, seed=21 + k, s=1.1, log2u=20, width=w)
+            h = torch.from_numpy(x.view(np.int32 if w == 4 else np.int64))
+            if pinned:
+                h = h.pin_memory()
+            e = P.summarize_host(h, k, p).export()
+            r, q = oracle.parallel_space_saving(x, k, p)
+            assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == summary_entries(r)
+            assert (e.m, e.n_covered) == (r.m, r.n_covered)
+    finally:
+        P.set_host_direct(bool(prev))
 
 
 def test_fuzz_small_universes():
