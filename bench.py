@@ -53,11 +53,11 @@ WORKLOADS = {
 
 # DRAM traffic of the summarize kernel from one ncu capture (profiles/
 # ss_block_kernel_wave_k2000.md: 304 blocks of 262144 u32 items, k = 2000 ->
-# 319.28 MB read + 4.10 MB written).  Traffic grows with the number of blocks,
+# 319.05 MB read + 4.10 MB written).  Traffic grows with the number of blocks,
 # so a launch of p such blocks moves p times the per-block bytes.  The figure
 # is only valid for the kernel source it was measured on.
-TRAFFIC = {"summarize_sha1": "108605c14537d5b3a1d38d5b430f5571c2899cc0",
-           "bytes_per_block": (319.28e6 + 4.10e6) / 304, "block_items": 262144, "k": 2000, "w": 4}
+TRAFFIC = {"summarize_sha1": "e8319d649e0d817a7b8a581bc51ef6329f1343c4",
+           "bytes_per_block": (319.05e6 + 4.10e6) / 304, "block_items": 262144, "k": 2000, "w": 4}
 
 
 def traffic_per_launch(wl):
