@@ -17,7 +17,7 @@
 //   * Pruned(global, n, k): Algorithm 1 with the k-majority threshold of
 //     Section 3 (frequency >= floor(n/k) + 1, i.e. count * k > n).
 //
-// Readings of points the paper leaves open (each also listed in the design doc):
+// Readings of points the paper leaves open:
 //   * every counter also carries an error err (Metwally et al.'s Space
 //     Saving): on eviction err := the evicted count; combine adds to err the
 //     same quantity it adds to the count;
