@@ -20,9 +20,14 @@ __global__ void exact_counts_kernel(const ItemT* __restrict__ items, u64 n, int 
                                     uint32_t* counts) {
   const u64 u = 1ull << log2u;
   const u64 stride = (u64)gridDim.x * blockDim.x;
-  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const u64 x = (u64)items[i];
-    atomicAdd(&counts[x < u ? x : u], 1u);
+  // whole warps iterate together; equal items of a warp add with one atomic
+  const u64 n_round = (n + 31) / 32 * 32;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+    const u64 x = i < n ? (u64)items[i] : ~0ull;
+    const u64 c = i < n ? (x < u ? x : u) : ~0ull;
+    const unsigned grp = __match_any_sync(0xffffffffu, c);
+    if (c != ~0ull && (threadIdx.x & 31) == (unsigned)(__ffs(grp) - 1))
+      atomicAdd(&counts[c], (uint32_t)__popc(grp));
   }
 }
 
