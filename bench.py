@@ -85,6 +85,31 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def host_info() -> dict:
+    """The host the oracle runs on: logical CPUs and the CPU model."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":", 1)[0].strip().lower()
+                if key in ("model name", "hardware", "cpu model") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu_model": model or "unknown"}
+
+
 def replica_aggregate(local_ms: float, local_items: int, dist=None, device="cpu"):
     """Whole-job figures of N independent replicas: the slowest rank's time
     and the items of all ranks (value = items / time).  With dist=None (one
@@ -183,7 +208,7 @@ def cpu_baseline(wl, budget_s: float, seed_offset: int = 0):
     return {"value": hi / dt, "unit": "items/s", "cores": 1, "kind": "oracle",
             "sample": f"blocks 0..{blocks - 1} of the {p} blocks ({hi} items): block summaries, "
                       f"their binary combine tree and the query, single-threaded C++",
-            "seconds": dt}
+            "seconds": dt, "host": host_info()}
 
 
 def run_reference(args, wl, rank):
@@ -216,7 +241,8 @@ def run_reference(args, wl, rank):
         "config": {"workload": wl["desc"], "n": n, "k": k, "p": p},
         "cpu_baseline": {"value": value, "unit": "items/s", "cores": 1, "kind": "oracle",
                          "sample": f"per step: blocks 0..{blocks - 1} of {p} ({hi} items), "
-                                   "block summaries + combine tree + query"},
+                                   "block summaries + combine tree + query",
+                         "host": host_info()},
         "e2e": {"value": value, "unit": "items/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
