@@ -36,14 +36,28 @@ inline cudaError_t ensure_kernel_attrs(const void* kern) {
 }
 
 constexpr uint32_t SS_SMEM_MAX_K = 4096;  // larger k keep part of the summarize and merge state in HBM
-constexpr int SS_BS = 512;     // threads per CTA of the summarize kernel
+constexpr int SS_BS = 512;     // threads per CTA of the summarize kernel (wide shape)
 constexpr int SS_IPT = 2;      // items per thread per window (window = SS_BS * SS_IPT)
+// Narrow shape: the same 1024-item window on half the threads, for k whose
+// state is small enough that twice as many CTAs (independent blocks) fit on
+// an SM.  The result does not depend on the shape.
+constexpr int SS_BS_NARROW = 256;
+constexpr int SS_IPT_NARROW = 4;
+static_assert(SS_BS * SS_IPT == SS_BS_NARROW * SS_IPT_NARROW, "both shapes use one window size");
 constexpr int MERGE_BS = 512;  // threads per CTA of the combine kernel
 constexpr int CANON_BS = 1024; // threads per CTA of the query/export kernel
 
-// Shared memory of one summarize CTA for k counters.
+// Shared memory of one summarize CTA for k counters (the wide shape, the
+// larger of the two).
 template <typename ItemT>
 size_t ss_smem_bytes(uint32_t k);
+
+// Threads per CTA of the summarize kernel for k counters (SS_BS or
+// SS_BS_NARROW; `batch`: the persistent batch kernel): the narrow shape when
+// it keeps at least as many threads resident per SM as the wide one.
+// Decided once per (item type, k, kernel) by the occupancy calculator.
+template <typename ItemT>
+int ss_shape_bs(uint32_t k, bool batch);
 
 // Blocks r0 .. r0+count-1 of p (Algorithm 1 bounds over n items) into nodes
 // node0 .. node0+count-1 of `out`.
@@ -116,8 +130,8 @@ cudaError_t launch_summarize_warp_batch(const BatchStream* streams, const BatchT
 template <typename ItemT>
 int summarize_warp_ctas_per_sm(uint32_t k);
 
-// Resident CTAs per SM of the persistent CTA kernel for k counters (0 if it
-// cannot run).
+// Resident CTAs per SM of the persistent CTA kernel for k counters, in the
+// shape ss_shape_bs(k, true) picks (0 if it cannot run).
 template <typename ItemT>
 int summarize_ctas_per_sm(uint32_t k);
 

@@ -1137,11 +1137,11 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   }
 }
 
+// Register budget for 1024 threads per SM: two CTAs of 512 or four of 256.
 template <typename ItemT, int BS, int IPT, bool BIG>
-__global__ void __launch_bounds__(BS, 2) ss_block_kernel(const ItemT* __restrict__ items, u64 n,
-                                                      uint32_t p, uint32_t r0,
-                                                      SetView<ItemT> out, uint32_t node0,
-                                                      unsigned char* gscratch, size_t gslice) {
+__global__ void __launch_bounds__(BS, 1024 / BS)
+    ss_block_kernel(const ItemT* __restrict__ items, u64 n, uint32_t p, uint32_t r0,
+                    SetView<ItemT> out, uint32_t node0, unsigned char* gscratch, size_t gslice) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SSState S;
   summarize_block<ItemT, BS, IPT, BIG>(items, n, p, r0 + blockIdx.x, out, node0 + blockIdx.x,
@@ -1153,9 +1153,9 @@ __global__ void __launch_bounds__(BS, 2) ss_block_kernel(const ItemT* __restrict
 // a shared counter until the list is exhausted.  Tasks are listed longest
 // block first so that the last wave is short.
 template <typename ItemT, int BS, int IPT>
-__global__ void __launch_bounds__(BS, 2) ss_batch_kernel(const BatchStream* __restrict__ streams,
-                                                      const BatchTask* __restrict__ tasks,
-                                                      uint32_t ntasks, uint32_t* counter) {
+__global__ void __launch_bounds__(BS, 1024 / BS)
+    ss_batch_kernel(const BatchStream* __restrict__ streams, const BatchTask* __restrict__ tasks,
+                    uint32_t ntasks, uint32_t* counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SSState S;
   __shared__ uint32_t next;
@@ -1188,22 +1188,82 @@ size_t ss_smem_bytes(uint32_t k) {
                            : ss_carve<ItemT, SS_BS, SS_IPT, false>(k, nullptr, nullptr, nullptr);
 }
 
+namespace {
+
+// Resident CTAs per SM of one kernel shape (0 if it cannot run).
+int resident_ctas(const void* kern, int bs, size_t smem) {
+  if (ensure_kernel_attrs(kern) != cudaSuccess) return 0;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, bs, smem) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+template <typename ItemT>
+size_t shape_smem(uint32_t k, int bs) {
+  return bs == SS_BS_NARROW
+             ? ss_carve<ItemT, SS_BS_NARROW, SS_IPT_NARROW, false>(k, nullptr, nullptr, nullptr)
+             : ss_smem_bytes<ItemT>(k);
+}
+
+template <typename ItemT>
+const void* block_kernel_of(int bs) {
+  return bs == SS_BS_NARROW
+             ? (const void*)ss_block_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW, false>
+             : (const void*)ss_block_kernel<ItemT, SS_BS, SS_IPT, false>;
+}
+
+template <typename ItemT>
+const void* batch_kernel_of(int bs) {
+  return bs == SS_BS_NARROW ? (const void*)ss_batch_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW>
+                            : (const void*)ss_batch_kernel<ItemT, SS_BS, SS_IPT>;
+}
+
+}  // namespace
+
+template <typename ItemT>
+int ss_shape_bs(uint32_t k, bool batch) {
+  if (k > SS_SMEM_MAX_K) return SS_BS;
+  // 0 = not decided yet; decided on the first device that asks (one kind of
+  // GPU per process), so that later launches and stream captures only read it
+  static std::atomic<int> memo[2][SS_SMEM_MAX_K + 1];
+  std::atomic<int>& m = memo[batch ? 1 : 0][k];
+  int bs = m.load(std::memory_order_relaxed);
+  if (bs) return bs;
+  const void* narrow =
+      batch ? batch_kernel_of<ItemT>(SS_BS_NARROW) : block_kernel_of<ItemT>(SS_BS_NARROW);
+  const void* wide = batch ? batch_kernel_of<ItemT>(SS_BS) : block_kernel_of<ItemT>(SS_BS);
+  const int tn =
+      resident_ctas(narrow, SS_BS_NARROW, shape_smem<ItemT>(k, SS_BS_NARROW)) * SS_BS_NARROW;
+  const int tw = resident_ctas(wide, SS_BS, shape_smem<ItemT>(k, SS_BS)) * SS_BS;
+  bs = (tn > 0 && tn >= tw) ? SS_BS_NARROW : SS_BS;
+  m.store(bs, std::memory_order_relaxed);
+  return bs;
+}
+
 template <typename ItemT>
 cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
                                     uint32_t count, SetView<ItemT> out, uint32_t node0,
                                     cudaStream_t stream) {
   if (out.k <= warp_kmax())
     return launch_summarize_warp_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
-  const size_t smem = ss_smem_bytes<ItemT>(out.k);
   if (out.k <= SS_SMEM_MAX_K) {
-    auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT, false>;
-    cudaError_t e = ensure_kernel_attrs((const void*)kern);
+    const int bs = ss_shape_bs<ItemT>(out.k, false);
+    const void* kern = block_kernel_of<ItemT>(bs);
+    cudaError_t e = ensure_kernel_attrs(kern);
     if (e != cudaSuccess) return e;
     if (count == 0) return cudaSuccess;
-    kern<<<count, SS_BS, smem, stream>>>(items, n, p, r0, out, node0, nullptr, 0);
+    const size_t smem = shape_smem<ItemT>(out.k, bs);
+    if (bs == SS_BS_NARROW)
+      ss_block_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW, false>
+          <<<count, SS_BS_NARROW, smem, stream>>>(items, n, p, r0, out, node0, nullptr, 0);
+    else
+      ss_block_kernel<ItemT, SS_BS, SS_IPT, false>
+          <<<count, SS_BS, smem, stream>>>(items, n, p, r0, out, node0, nullptr, 0);
     return cudaGetLastError();
   }
   // large k: a slice of global scratch per CTA, ordered on the stream
+  const size_t smem = ss_smem_bytes<ItemT>(out.k);
   auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT, true>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
@@ -1224,24 +1284,25 @@ cudaError_t launch_summarize_batch(const BatchStream* streams, const BatchTask* 
                                    uint32_t ntasks, uint32_t* counter, uint32_t k, uint32_t grid,
                                    cudaStream_t stream) {
   if (k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;  // the batch keeps k in shared memory
-  const size_t smem = ss_smem_bytes<ItemT>(k);
-  auto kern = ss_batch_kernel<ItemT, SS_BS, SS_IPT>;
-  cudaError_t e = ensure_kernel_attrs((const void*)kern);
+  const int bs = ss_shape_bs<ItemT>(k, true);
+  cudaError_t e = ensure_kernel_attrs(batch_kernel_of<ItemT>(bs));
   if (e != cudaSuccess) return e;
   if (ntasks == 0 || grid == 0) return cudaSuccess;
-  kern<<<grid, SS_BS, smem, stream>>>(streams, tasks, ntasks, counter);
+  const size_t smem = shape_smem<ItemT>(k, bs);
+  if (bs == SS_BS_NARROW)
+    ss_batch_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW>
+        <<<grid, SS_BS_NARROW, smem, stream>>>(streams, tasks, ntasks, counter);
+  else
+    ss_batch_kernel<ItemT, SS_BS, SS_IPT>
+        <<<grid, SS_BS, smem, stream>>>(streams, tasks, ntasks, counter);
   return cudaGetLastError();
 }
 
 template <typename ItemT>
 int summarize_ctas_per_sm(uint32_t k) {
-  const size_t smem = ss_smem_bytes<ItemT>(k);
-  auto kern = ss_batch_kernel<ItemT, SS_BS, SS_IPT>;
-  if (ensure_kernel_attrs((const void*)kern) != cudaSuccess) return 0;
-  int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, SS_BS, smem) != cudaSuccess)
-    return 0;
-  return blocks;
+  if (k > SS_SMEM_MAX_K) return 0;
+  const int bs = ss_shape_bs<ItemT>(k, true);
+  return resident_ctas(batch_kernel_of<ItemT>(bs), bs, shape_smem<ItemT>(k, bs));
 }
 
 template cudaError_t launch_summarize_batch<uint32_t>(const BatchStream*, const BatchTask*, uint32_t,
@@ -1252,6 +1313,8 @@ template int summarize_ctas_per_sm<uint32_t>(uint32_t);
 template int summarize_ctas_per_sm<u64>(uint32_t);
 template size_t ss_smem_bytes<uint32_t>(uint32_t);
 template size_t ss_smem_bytes<u64>(uint32_t);
+template int ss_shape_bs<uint32_t>(uint32_t, bool);
+template int ss_shape_bs<u64>(uint32_t, bool);
 template cudaError_t launch_summarize_blocks<uint32_t>(const uint32_t*, u64, uint32_t, uint32_t,
                                                        uint32_t, SetView<uint32_t>, uint32_t,
                                                        cudaStream_t);

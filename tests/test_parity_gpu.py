@@ -89,6 +89,17 @@ def test_random_configs(n, k, p, w, s, log2u, seed):
     compare_tree(x, k, p)
 
 
+@pytest.mark.parametrize("k,w", [(544, 4), (545, 4), (304, 8), (305, 8)])
+def test_cta_shape_boundaries(k, w):
+    # The CTA kernel runs 256 threads x 4 items when that keeps as many threads
+    # resident as 512 x 2 (small state); on GB300 the switch falls between
+    # these k (u32: 544 | 545, u64: 304 | 305).  Both sides, with cut windows.
+    x = oracle.gen_zipf(180_000 + k, seed=900 + k, s=0.9, log2u=32, width=w)
+    compare_tree(x, k, 3)
+    y = oracle.gen_zipf(120_000, seed=950 + k, s=1.8, log2u=18, width=w)
+    compare_tree(y, k, 2)
+
+
 def test_edge_empty_and_tiny():
     compare_tree(np.zeros(0, np.uint32), 5, 4)            # n = 0
     compare_tree(np.array([7, 7, 9], np.uint32), 4, 8)     # n < p: empty blocks
