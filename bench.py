@@ -44,6 +44,11 @@ WORKLOADS = {
              "[0,2^24), seed 2; k=2000; p=304 blocks of 262144 items (the block shape of the "
              "2^30 stream); binary merge tree; query n/k",
         n=304 * 262144, w=4, s=1.1, log2u=24, seed=2, k=2000, p=304),
+    "wave_k500": dict(
+        desc="one wave of narrow-shape blocks: n=608*262144 uint32 Zipf(s=1.0) over [0,2^32), "
+             "seed 2; k=500; p=608 blocks of 262144 items (4 CTAs of 256 threads on each of 152 "
+             "SMs); binary merge tree; query n/k",
+        n=608 * 262144, w=4, s=1.0, log2u=32, seed=2, k=500, p=608),
     "small": dict(
         desc="plain single stream: n=2^20 uint32 Zipf(s=1.1) over [0,2^20), seed 1; k=100; p=8; "
              "binary merge tree; query n/k",
@@ -53,11 +58,11 @@ WORKLOADS = {
 
 # DRAM traffic of the summarize kernel from one ncu capture (profiles/
 # ss_block_kernel_wave_k2000.md: 304 blocks of 262144 u32 items, k = 2000 ->
-# 319.05 MB read + 4.10 MB written).  Traffic grows with the number of blocks,
+# 318.87 MB read + 3.37 MB written).  Traffic grows with the number of blocks,
 # so a launch of p such blocks moves p times the per-block bytes.  The figure
 # is only valid for the kernel source it was measured on.
-TRAFFIC = {"summarize_sha1": "e8319d649e0d817a7b8a581bc51ef6329f1343c4",
-           "bytes_per_block": (319.05e6 + 4.10e6) / 304, "block_items": 262144, "k": 2000, "w": 4}
+TRAFFIC = {"summarize_sha1": "f34a6510834efe750b50d521d53c776477dc093f",
+           "bytes_per_block": (318.87e6 + 3.37e6) / 304, "block_items": 262144, "k": 2000, "w": 4}
 
 
 def traffic_per_launch(wl):
