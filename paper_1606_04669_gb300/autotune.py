@@ -12,7 +12,9 @@ What is tuned and what is not:
   * summarize kernel (window-parallel CTA kernel, or one warp per block with
     the counters in registers, for k <= 256): the result does not depend on
     it, so the library picks it per stream from k and the skew hint; the
-    crossovers it uses are measured by `sweep_kernels()`;
+    skew bands it uses are measured by `sweep_kernels()`;
+  * CTA shape of the window-parallel kernel (512 or 256 threads): picked per
+    k by the library from the occupancy calculator, not tuned here;
   * CTA count: the persistent kernels run SMs x resident CTAs per SM (from the
     occupancy calculator for the k's shared memory), not tuned;
   * table load factor: fixed at <= 1/2 (k counters plus one window of pending
@@ -105,10 +107,15 @@ def sweep(n: int = 1 << 27, item_bytes: int = 8, steps: int = 3, seed: int = 77)
     return results, table
 
 
-def sweep_kernels(n: int = 1 << 29, item_bytes: int = 8, steps: int = 3, seed: int = 9):
+KERNEL_KS = (32, 64, 96, 128, 160, 192, 224, 256)
+KERNEL_SKEWS = (0.5, 0.7, 0.9, 1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6, 1.7, 1.8, 1.9)
+
+
+def sweep_kernels(n: int = 1 << 28, item_bytes: int = 8, length: int = 1 << 15, steps: int = 4,
+                  seed: int = 11):
     """Items/s of the two summarize kernels for k <= 256 at full occupancy
-    (many blocks), per (skew, k, block length): the data behind the
-    library's per-stream kernel choice."""
+    (n / length blocks), per (skew, k): the data behind the skew bands in
+    which the batch runs a stream on the warp kernel."""
     import torch
 
     import paper_1606_04669_gb300 as P
@@ -129,17 +136,17 @@ def sweep_kernels(n: int = 1 << 29, item_bytes: int = 8, steps: int = 3, seed: i
     out = []
     prev = P.set_warp_kmax(256)
     try:
-        for zs in SKEW_CLASSES:
+        for zs in KERNEL_SKEWS:
             x = P.gen_zipf(n, seed=seed, s=zs, log2u=32, item_bytes=item_bytes)
-            for k in (64, 128, 256):
-                for length in (1 << 13, 1 << 15, 1 << 17):
-                    p = n // length
-                    row = {"skew": zs, "k": k, "block_length": length, "p": p}
-                    for name, kmax in (("warp", 256), ("cta", 0)):
-                        P.set_warp_kmax(kmax)
-                        row[name + "_items_per_s"] = n / (timeit(x, k, p) / 1e3)
-                    P.set_warp_kmax(256)
-                    out.append(row)
+            for k in KERNEL_KS:
+                p = n // length
+                row = {"skew": zs, "k": k, "block_length": length, "p": p}
+                for name, kmax in (("warp", 256), ("cta", 0)):
+                    P.set_warp_kmax(kmax)
+                    row[name + "_items_per_s"] = n / (timeit(x, k, p) / 1e3)
+                P.set_warp_kmax(256)
+                row["warp_over_cta"] = row["warp_items_per_s"] / row["cta_items_per_s"]
+                out.append(row)
             del x
     finally:
         P.set_warp_kmax(prev)

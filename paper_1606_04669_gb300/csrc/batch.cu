@@ -32,18 +32,28 @@ struct StreamPlan {
 
 // Kernel for a stream's block summaries.  Both kernels compute the same
 // summaries; the warp kernel (counters in registers, one item at a time)
-// wins where misses dominate, the window-parallel CTA kernel where hits do.
-// Crossovers measured on a GB300 at full occupancy (u64 items, 2^29 items
-// in 4096..65536 blocks, 1e9 items/s warp vs CTA): k = 64: 14.5 vs 2.1 at
-// s = 0.8, 22 vs 5.6 at 1.4, 26 vs 35 at 2.0; k = 128: 9.9 vs 3.8, 15 vs
-// 14, 17 vs 52; k = 256: 5.8 vs 6.9, 10 vs 23, 11 vs 64.  An unknown skew
-// (hint <= 0) counts as weak.
+// wins where misses dominate, the window-parallel CTA kernel where hits do,
+// and its cost rises with k.  The skew band [lo, hi) in which the warp
+// kernel is faster, per k class, measured on a GB300 at full occupancy (u64
+// items, 2^28 items in blocks of 2^15; warp / CTA items/s): k = 32: 11.9 at
+// s = 0.5, 1.27 at 1.9; k = 64: 1.04 at 1.7, 0.80 at 1.8; k = 96: 1.28 at
+// 1.4, 0.85 at 1.5; k = 128: 1.38 at 1.3, 0.88 at 1.4; k = 160: 1.03 at
+// 1.2, 0.71 at 1.3; k = 192: 0.88 at 0.7, 1.13 at 0.9 and 1.1, 0.84 at 1.2;
+// k = 224: <= 1.08 (at 1.0 only); k = 256: <= 0.93.  An unknown skew (hint
+// <= 0) counts as weak.
+struct WarpBand {
+  uint32_t kmax;
+  double lo, hi;
+};
+constexpr WarpBand WARP_BANDS[] = {{32, 0.0, 1.95},  {64, 0.0, 1.75},  {96, 0.0, 1.45},
+                                   {128, 0.0, 1.35}, {160, 0.0, 1.25}, {192, 0.85, 1.15}};
+
 bool use_warp_kernel(uint32_t k, double skew) {
   if (warp_kmax() == 0 || k > WARP_SS_MAX_K) return false;
   if (skew <= 0.0) return k <= 64;
-  if (k <= 64) return skew < 1.8;
-  if (k <= 128) return skew < 1.45;
-  return skew < 0.7;
+  for (const WarpBand& b : WARP_BANDS)
+    if (k <= b.kmax) return skew >= b.lo && skew < b.hi;
+  return false;
 }
 
 struct LevelLaunch {

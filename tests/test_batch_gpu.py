@@ -86,8 +86,8 @@ def test_batch_kernel_choice_by_skew(kmax):
     # every result against the oracle.
     prev = P.set_warp_kmax(kmax)
     try:
-        ks = [64, 128, 256, 64, 128, 256, 2, 100, 1024]
-        skews = [0.6, 0.9, 0.5, 2.5, 1.9, 1.2, 1.0, 0.0, 0.8]
+        ks = [64, 128, 256, 64, 128, 256, 2, 100, 1024, 192, 192, 160, 32]
+        skews = [0.6, 0.9, 0.5, 2.5, 1.9, 1.2, 1.0, 0.0, 0.8, 1.0, 0.6, 1.2, 1.9]
         items = [P.gen_zipf(60_000 + 1000 * i, seed=11, s=max(sk, 0.7), log2u=20, item_bytes=8,
                             stream_id=i) for i, sk in enumerate(skews)]
         ps = [1 + i % 4 for i in range(len(ks))]
