@@ -4,9 +4,11 @@ TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  The product path never
 imports this package.
 
-Thin ctypes wrapper over ``pss_oracle.cpp`` (plain single-threaded C++; see
-that file for the paper passages each function follows).  Summaries are
-returned in canonical order: count descending, item ascending.
+Thin ctypes wrapper over ``pss_oracle.cpp`` (Space Saving) and
+``frequent_oracle.cpp`` (the Frequent / Misra–Gries summary), plain
+single-threaded C++; see those files for the passages and published
+definitions each function follows.  Summaries are returned in canonical
+order: count descending, item ascending.
 """
 from __future__ import annotations
 
@@ -19,7 +21,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "pss_oracle.cpp")
+_SRCS = [os.path.join(_HERE, "pss_oracle.cpp"), os.path.join(_HERE, "frequent_oracle.cpp")]
 _GEN = os.path.join(_HERE, "..", "paper_1606_04669_gb300", "gen", "pss_zipf.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
@@ -31,14 +33,14 @@ u32p = ctypes.POINTER(ctypes.c_uint32)
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with g++ (single translation unit, a few seconds)."""
+    """Compile liboracle.so with g++ (two translation units, a few seconds)."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest_src = max(os.path.getmtime(_SRC), os.path.getmtime(_GEN))
+    newest_src = max([os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(_GEN)])
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest_src:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           "-pthread", "-o", tmp, _SRC]
+           "-pthread", "-o", tmp, *_SRCS]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -96,6 +98,20 @@ def _load():
         for name in ("oracle_gen_log_t", "oracle_gen_exp_t"):
             getattr(lib, name).restype = ctypes.c_double
             getattr(lib, name).argtypes = [ctypes.c_double]
+        lib.oracle_frequent.restype = ctypes.c_uint32
+        lib.oracle_frequent.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.c_uint32, u64p, u64p]
+        lib.oracle_frequent_combine.restype = ctypes.c_uint32
+        lib.oracle_frequent_combine.argtypes = ([u64p, u64p, ctypes.c_uint32, ctypes.c_uint64] * 2
+                                                + [ctypes.c_uint32, u64p, u64p, u64p])
+        lib.oracle_frequent_tree.restype = ctypes.c_int
+        lib.oracle_frequent_tree.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                             ctypes.c_uint32, ctypes.c_uint32, u64p, u64p, u32p,
+                                             u64p]
+        lib.oracle_frequent_query.restype = ctypes.c_uint32
+        lib.oracle_frequent_query.argtypes = [u64p, u64p, ctypes.c_uint32, ctypes.c_uint64,
+                                              ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                              u64p, u64p, u64p]
         _lib = lib
         return lib
 
@@ -272,6 +288,81 @@ def accuracy(s: Summary, counts: np.ndarray, n: int, k: int) -> dict:
             "are": (sum(rel) / r) if r else 0.0,
             "precision": (tp / r) if r else 1.0,
             "recall": (tp / true_frequent) if true_frequent else 1.0}
+
+
+# ------------------------------------------- Frequent (Misra–Gries) summary
+
+def _frequent_summary(it, ct, size, n_covered) -> Summary:
+    return Summary(it[:size].copy(), ct[:size].copy(), np.zeros(size, np.uint64), 0,
+                   int(n_covered))
+
+
+def frequent(items, k: int) -> Summary:
+    """Misra–Gries with k - 1 counters over the whole array (err and m are 0;
+    the bound is frequent_delta)."""
+    lib = _load()
+    a, w = _items_array(items)
+    it = np.zeros(max(k - 1, 1), np.uint64); ct = np.zeros(max(k - 1, 1), np.uint64)
+    sz = lib.oracle_frequent(a.ctypes.data_as(ctypes.c_void_p), a.shape[0], w, k, _p64(it), _p64(ct))
+    return _frequent_summary(it, ct, sz, a.shape[0])
+
+
+def frequent_combine(a: Summary, b: Summary, k: int) -> Summary:
+    """The merge of two Misra–Gries summaries (k - 1 counters each)."""
+    lib = _load()
+    ai = np.ascontiguousarray(a.item, np.uint64); ac = np.ascontiguousarray(a.count, np.uint64)
+    bi = np.ascontiguousarray(b.item, np.uint64); bc = np.ascontiguousarray(b.count, np.uint64)
+    it = np.zeros(max(k - 1, 1), np.uint64); ct = np.zeros(max(k - 1, 1), np.uint64)
+    cov = np.zeros(1, np.uint64)
+    sz = lib.oracle_frequent_combine(_p64(ai), _p64(ac), a.size, a.n_covered, _p64(bi), _p64(bc),
+                                     b.size, b.n_covered, k, _p64(it), _p64(ct), _p64(cov))
+    return _frequent_summary(it, ct, sz, int(cov[0]))
+
+
+def frequent_tree(items, k: int, p: int) -> list[list[Summary]]:
+    """p Misra–Gries block summaries and every level of the binary merge tree."""
+    lib = _load()
+    a, w = _items_array(items)
+    nodes = int(lib.oracle_tree_nodes(p))
+    stride = k - 1
+    it = np.zeros(nodes * stride, np.uint64); ct = np.zeros(nodes * stride, np.uint64)
+    sz = np.zeros(nodes, np.uint32); cov = np.zeros(nodes, np.uint64)
+    lib.oracle_frequent_tree(a.ctypes.data_as(ctypes.c_void_p), a.shape[0], w, k, p, _p64(it),
+                             _p64(ct), _p32(sz), _p64(cov))
+    levels, node = [], 0
+    for width in tree_level_sizes(p):
+        level = []
+        for _ in range(width):
+            base = node * stride
+            level.append(_frequent_summary(it[base:base + stride], ct[base:base + stride],
+                                           int(sz[node]), int(cov[node])))
+            node += 1
+        levels.append(level)
+    return levels
+
+
+def frequent_delta(s: Summary, k: int) -> int:
+    """floor((n_covered - sum of counts) / k): count <= f <= count + delta."""
+    return (s.n_covered - int(np.asarray(s.count, np.uint64).sum())) // k
+
+
+def frequent_query(s: Summary, n: int, k: int, guaranteed: bool = False) -> Summary:
+    """Entries with (count + delta) * k > n (guaranteed: count * k > n), err =
+    delta, canonical order."""
+    lib = _load()
+    si = np.ascontiguousarray(s.item, np.uint64); sc = np.ascontiguousarray(s.count, np.uint64)
+    cap = max(s.size, 1)
+    it = np.zeros(cap, np.uint64); ct = np.zeros(cap, np.uint64); er = np.zeros(cap, np.uint64)
+    sz = lib.oracle_frequent_query(_p64(si), _p64(sc), s.size, s.n_covered, n, k,
+                                   1 if guaranteed else 0, _p64(it), _p64(ct), _p64(er))
+    return Summary(it[:sz].copy(), ct[:sz].copy(), er[:sz].copy(), 0, s.n_covered)
+
+
+def parallel_frequent(items, k: int, p: int) -> tuple[Summary, Summary]:
+    """p block summaries, the merge tree and the query: (root, candidates)."""
+    root = frequent_tree(items, k, p)[-1][0]
+    n = int(np.asarray(items).shape[0])
+    return root, frequent_query(root, n, k)
 
 
 # ---------------------------------------------------------------- generator
