@@ -50,7 +50,7 @@ extern "C" {
 
 #define PSS_OK 0
 #define PSS_EINVAL (-1)    /* bad argument: null pointer, k < 2, k > PSS_MAX_K, width not 4/8 ... */
-#define PSS_EMISMATCH (-2) /* merging summaries of different k or item width */
+#define PSS_EMISMATCH (-2) /* merging summaries of different k, item width or kind */
 #define PSS_ENOMEM (-3)    /* device allocation failed */
 #define PSS_ECUDA (-4)     /* a CUDA runtime call failed (launch, copy, sync) */
 #define PSS_ETIMEOUT (-5)  /* a bounded device wait expired */
@@ -163,10 +163,10 @@ int pss_tree_level_nodes(const pss_tree* tree, uint32_t level, uint32_t* nodes);
 
 /*
  * pss_tree_read_level — copy every summary of one tree level to the host,
- * in the device layout: node j's entries are at [j*k, j*k + sizes[j]) of
- * items/counts/errs, sorted by item ascending (items widened to 64 bits).
- * Arrays items, counts, errs hold nodes*k values; sizes, m, n_covered hold
- * nodes values.  Synchronizes stream.  PSS_EDEVICE if a kernel recorded an
+ * in the device layout: node j's entries are at [j*c, j*c + sizes[j]) of
+ * items/counts/errs, sorted by item ascending (items widened to 64 bits);
+ * c = k for a Space Saving tree, k - 1 for a Frequent one.  Arrays items,
+ * counts, errs hold nodes*c values; sizes, m, n_covered hold nodes values.  Synchronizes stream.  PSS_EDEVICE if a kernel recorded an
  * error in that level.
  */
 int pss_tree_read_level(const pss_tree* tree, uint32_t level, uint64_t* items, uint64_t* counts,
@@ -178,6 +178,51 @@ int pss_tree_root(const pss_tree* tree, void* stream, pss_summary** out);
 
 /* Release a tree (stream-ordered on the stream that created it). */
 void pss_tree_free(pss_tree* tree);
+
+/*
+ * Frequent (Misra–Gries) summaries: the second counter-based summary the
+ * paper discusses (Section 2, related work: Misra and Gries; Frequent of
+ * Demaine et al.; the parallel merge of Frequent summaries), on the same
+ * blocks and reduction tree as Space Saving.  The paper names the algorithm
+ * and its merge but does not define them; the library follows the published
+ * definitions:
+ *   - block summary (Misra and Gries, 1982) with k - 1 counters: an item
+ *     already counted adds 1; an item not counted takes a free counter with
+ *     count 1; when no counter is free every counter loses 1, counters that
+ *     reach 0 are freed and the item is not stored;
+ *   - merge (Agarwal et al., "Mergeable summaries", 2012): counts of equal
+ *     items add (absent = 0); when more than k - 1 items remain, the k-th
+ *     largest count is subtracted from every count and only positive counts
+ *     stay.
+ * A Frequent summary holds at most k - 1 entries with err = 0 and minimum 0.
+ * Its counts are lower bounds: with delta = floor((n_covered - sum of
+ * counts) / k), every stored item satisfies count <= f <= count + delta and
+ * every other item f <= delta, so every item with f * k > n is stored.
+ * The same calls read and combine both kinds of summary: pss_merge (both
+ * arguments of one kind, else PSS_EMISMATCH), pss_query / pss_query_mode,
+ * pss_export, pss_free, and pss_tree_levels / _level_nodes / _read_level /
+ * _root / _free for trees.  Not available for Frequent summaries:
+ * pss_accuracy_of (PSS_EINVAL), pss_import (always Space Saving), the batch,
+ * server and allocation-free forms, host input.
+ *
+ * pss_frequent_summarize — p Misra–Gries block summaries (Algorithm 1
+ * bounds) merged in the binary tree over adjacent pairs (an odd last summary
+ * carried up).  2 <= k <= PSS_MAX_K_RESIDENT; otherwise as pss_summarize.
+ * Asynchronous on stream.
+ */
+#define PSS_KIND_SPACE_SAVING 0
+#define PSS_KIND_FREQUENT 1
+int pss_frequent_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k,
+                           uint32_t p, void* stream, pss_summary** out);
+
+/* pss_frequent_summarize keeping every level of the tree (nodes hold k - 1
+ * entries: pss_tree_read_level's stride is k - 1).  Asynchronous. */
+int pss_frequent_summarize_tree(const void* d_items, uint64_t n, int item_bytes, uint32_t k,
+                                uint32_t p, void* stream, pss_tree** out);
+
+/* PSS_KIND_SPACE_SAVING or PSS_KIND_FREQUENT. */
+int pss_summary_kind(const pss_summary* summary, int* kind);
+int pss_tree_kind(const pss_tree* tree, int* kind);
 
 /*
  * Batched form: many independent streams, each with its own k and p, in one
@@ -241,7 +286,8 @@ void pss_batch_free(pss_batch* batch);
  * in both gets count1 + count2 (err1 + err2); an item in one only gets the
  * other summary's minimum added to its count and to its err; Prune(k) keeps
  * the k largest by (count descending, item ascending).  Both summaries must
- * have the same k and item width (else PSS_EMISMATCH).  Asynchronous.
+ * have the same k, item width and kind (else PSS_EMISMATCH).  Two Frequent
+ * summaries are merged by the Frequent merge instead.  Asynchronous.
  */
 int pss_merge(const pss_summary* a, const pss_summary* b, void* stream, pss_summary** out);
 
@@ -252,6 +298,9 @@ int pss_merge(const pss_summary* a, const pss_summary* b, void* stream, pss_summ
  * ascending.  n is the length of the stream the summary describes.
  *   host_out    array of cap entries; *n_out receives the number reported.
  * PSS_ERANGE if more than cap entries qualify (nothing is written).
+ * A Frequent summary reports the entries whose upper bound exceeds n / k,
+ * (count + delta) * k > n (no k-majority item is missed), each with
+ * err = delta (count <= f <= count + err).
  * Synchronizes stream.
  */
 int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* host_out, uint32_t cap,
@@ -264,8 +313,9 @@ int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* hos
  * lower bound already exceeds the threshold, (count - err) * k > n: since
  * count - err <= f, each of them is a true k-majority item (no false
  * positive).  The paper reports only the first; the second is its
- * counterpart from the same error bound.  Same order, arguments and errors as
- * pss_query; any other mode is PSS_EINVAL.
+ * counterpart from the same error bound.  For a Frequent summary the
+ * guaranteed entries are count * k > n (count <= f), each with err = delta.
+ * Same order, arguments and errors as pss_query; any other mode is PSS_EINVAL.
  */
 #define PSS_QUERY_CANDIDATES 0
 #define PSS_QUERY_GUARANTEED 1
@@ -310,7 +360,10 @@ int pss_accuracy_of(const pss_summary* summary, const uint32_t* d_counts, int lo
  * pss_export — copy a whole summary to the host in canonical order (count
  * descending, item ascending) with its minimum m and the number of stream
  * items it describes.  host_out holds cap >= k entries (PSS_ERANGE if the
- * summary holds more than cap).  Synchronizes stream.
+ * summary holds more than cap).  For a Frequent summary *m receives delta =
+ * floor((n_covered - sum of counts) / k) (every stored item has count <= f
+ * <= count + delta, every other item f <= delta) and every err is 0.
+ * Synchronizes stream.
  */
 int pss_export(const pss_summary* summary, pss_entry* host_out, uint32_t cap, uint32_t* size,
                uint64_t* m, uint64_t* n_covered, void* stream);

@@ -16,14 +16,17 @@
 using namespace pss;
 
 struct pss_summary {
-  uint32_t k;
+  uint32_t k;           // the k of the k-majority problem
+  uint32_t cap;         // entries per node: k (Space Saving) or k - 1 (Frequent)
+  int kind;             // PSS_KIND_*
   int item_bytes;
   void* mem;            // one set of one node (set_layout)
   cudaStream_t stream;  // stream of the creating call; frees are ordered on it
 };
 
 struct pss_tree {
-  uint32_t k, p;
+  uint32_t k, cap, p;
+  int kind;
   int item_bytes;
   cudaStream_t stream;
   std::vector<void*> mem;       // one set per level
@@ -91,10 +94,11 @@ int check_k_width(uint32_t k, int w) {
   return PSS_OK;
 }
 
-// Level 0 (the block summaries, enqueued by `level0`) and the merge levels.
+// Level 0 (the block summaries, enqueued by `level0`) and the merge levels;
+// k is the capacity of a node, mg selects the Frequent merge.
 template <typename ItemT, typename Level0>
 int run_tree(uint32_t k, uint32_t p, cudaStream_t s, bool keep, std::vector<void*>& mems,
-             std::vector<uint32_t>& nodes, Level0 level0) {
+             std::vector<uint32_t>& nodes, Level0 level0, bool mg = false) {
   const int w = (int)sizeof(ItemT);
   auto fail = [&](cudaError_t e) {
     for (void* m : mems)
@@ -122,7 +126,7 @@ int run_tree(uint32_t k, uint32_t p, cudaStream_t s, bool keep, std::vector<void
     e = alloc_set(nxt, k, w, s, &mm);
     if (e != cudaSuccess) return fail(e);
     e = launch_merge_level<ItemT>(set_view<ItemT>(mems.back(), cur, k), set_view<ItemT>(mm, nxt, k),
-                                  s);
+                                  s, mg);
     count_launches(1);
     if (e != cudaSuccess) {
       cudaFreeAsync(mm, s);
@@ -145,6 +149,21 @@ int run_tree_device(const void* d_items, uint64_t n, uint32_t k, uint32_t p, cud
     count_launches(1);
     return launch_summarize_blocks<ItemT>((const ItemT*)d_items, n, p, 0, p, v0, 0, s);
   });
+}
+
+// The Frequent path: nodes of k - 1 counters, Misra–Gries block summaries and
+// the Frequent merge.
+template <typename ItemT>
+int run_frequent_tree_device(const void* d_items, uint64_t n, uint32_t k, uint32_t p,
+                             cudaStream_t s, bool keep, std::vector<void*>& mems,
+                             std::vector<uint32_t>& nodes) {
+  return run_tree<ItemT>(
+      k - 1, p, s, keep, mems, nodes,
+      [&](SetView<ItemT> v0) {
+        count_launches(1);
+        return launch_frequent_blocks<ItemT>((const ItemT*)d_items, n, p, 0, p, v0, 0, s);
+      },
+      true);
 }
 
 // One non-blocking copy stream per device for host-input calls.
@@ -246,6 +265,35 @@ int tree_common(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p, 
   if (rc) return rc;
   return w == 4 ? run_tree_device<uint32_t>(d_items, n, k, p, s, keep, mems, nodes)
                 : run_tree_device<u64>(d_items, n, k, p, s, keep, mems, nodes);
+}
+
+int frequent_tree_common(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p,
+                         cudaStream_t s, bool keep, std::vector<void*>& mems,
+                         std::vector<uint32_t>& nodes) {
+  if ((w != 4 && w != 8) || k < 2 || k > PSS_MAX_K_RESIDENT || p == 0) return PSS_EINVAL;
+  if (n > 0 && d_items == nullptr) return PSS_EINVAL;
+  if ((n + p - 1) / p >= (1ull << 32)) return PSS_EINVAL;
+  cudaError_t e = prepare_device();
+  if (e != cudaSuccess) return from_cuda(e);
+  const size_t have = max_optin_smem();
+  const size_t need_m = w == 4 ? merge_smem_bytes<uint32_t>(k - 1) : merge_smem_bytes<u64>(k - 1);
+  if (frequent_warp_bytes(k - 1, w) > have || need_m > have) return PSS_EINVAL;
+  return w == 4 ? run_frequent_tree_device<uint32_t>(d_items, n, k, p, s, keep, mems, nodes)
+                : run_frequent_tree_device<u64>(d_items, n, k, p, s, keep, mems, nodes);
+}
+
+// A summary object for one-node set `mem` (nullptr when out of host memory;
+// the caller then frees mem).
+pss_summary* new_summary(uint32_t k, int kind, int w, void* mem, cudaStream_t s) {
+  pss_summary* sm = new (std::nothrow) pss_summary;
+  if (!sm) return nullptr;
+  sm->k = k;
+  sm->cap = kind == PSS_KIND_FREQUENT ? k - 1 : k;
+  sm->kind = kind;
+  sm->item_bytes = w;
+  sm->mem = mem;
+  sm->stream = s;
+  return sm;
 }
 
 // Canonical copy-out of one node; filter selects the query.
@@ -356,15 +404,29 @@ int pss_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k, u
   std::vector<uint32_t> nodes;
   int rc = tree_common(d_items, n, item_bytes, k, p, s, false, mems, nodes);
   if (rc) return rc;
-  pss_summary* sm = new (std::nothrow) pss_summary;
+  pss_summary* sm = new_summary(k, PSS_KIND_SPACE_SAVING, item_bytes, mems.back(), s);
   if (!sm) {
     cudaFreeAsync(mems.back(), s);
     return PSS_ENOMEM;
   }
-  sm->k = k;
-  sm->item_bytes = item_bytes;
-  sm->mem = mems.back();
-  sm->stream = s;
+  *out = sm;
+  return PSS_OK;
+}
+
+int pss_frequent_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k,
+                           uint32_t p, void* stream, pss_summary** out) {
+  if (!out) return PSS_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<void*> mems;
+  std::vector<uint32_t> nodes;
+  int rc = frequent_tree_common(d_items, n, item_bytes, k, p, s, false, mems, nodes);
+  if (rc) return rc;
+  pss_summary* sm = new_summary(k, PSS_KIND_FREQUENT, item_bytes, mems.back(), s);
+  if (!sm) {
+    cudaFreeAsync(mems.back(), s);
+    return PSS_ENOMEM;
+  }
   *out = sm;
   return PSS_OK;
 }
@@ -401,15 +463,11 @@ int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t
     rc = item_bytes == 4 ? run_tree_host<uint32_t>(h_items, n, k, p, s, mems, nodes)
                          : run_tree_host<u64>(h_items, n, k, p, s, mems, nodes);
   if (rc) return rc;
-  pss_summary* sm = new (std::nothrow) pss_summary;
+  pss_summary* sm = new_summary(k, PSS_KIND_SPACE_SAVING, item_bytes, mems.back(), s);
   if (!sm) {
     cudaFreeAsync(mems.back(), s);
     return PSS_ENOMEM;
   }
-  sm->k = k;
-  sm->item_bytes = item_bytes;
-  sm->mem = mems.back();
-  sm->stream = s;
   *out = sm;
   return PSS_OK;
 }
@@ -427,6 +485,30 @@ int pss_summarize_tree(const void* d_items, uint64_t n, int item_bytes, uint32_t
     return rc;
   }
   t->k = k;
+  t->cap = k;
+  t->kind = PSS_KIND_SPACE_SAVING;
+  t->p = p;
+  t->item_bytes = item_bytes;
+  t->stream = s;
+  *out = t;
+  return PSS_OK;
+}
+
+int pss_frequent_summarize_tree(const void* d_items, uint64_t n, int item_bytes, uint32_t k,
+                                uint32_t p, void* stream, pss_tree** out) {
+  if (!out) return PSS_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  pss_tree* t = new (std::nothrow) pss_tree;
+  if (!t) return PSS_ENOMEM;
+  int rc = frequent_tree_common(d_items, n, item_bytes, k, p, s, true, t->mem, t->nodes);
+  if (rc) {
+    delete t;
+    return rc;
+  }
+  t->k = k;
+  t->cap = k - 1;
+  t->kind = PSS_KIND_FREQUENT;
   t->p = p;
   t->item_bytes = item_bytes;
   t->stream = s;
@@ -452,7 +534,7 @@ int pss_tree_read_level(const pss_tree* tree, uint32_t level, uint64_t* items, u
   if (!tree || level >= tree->nodes.size()) return PSS_EINVAL;
   if (!items || !counts || !errs || !sizes || !m || !n_covered) return PSS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const uint32_t nodes = tree->nodes[level], k = tree->k;
+  const uint32_t nodes = tree->nodes[level], k = tree->cap;
   const int w = tree->item_bytes;
   const SetLayout L = set_layout(nodes, k, w);
   const char* base = (const char*)tree->mem[level];
@@ -483,9 +565,8 @@ int pss_tree_root(const pss_tree* tree, void* stream, pss_summary** out) {
   if (!tree || !out) return PSS_EINVAL;
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
-  const uint32_t k = tree->k;
   const int w = tree->item_bytes;
-  const SetLayout L = set_layout(1, k, w);
+  const SetLayout L = set_layout(1, tree->cap, w);
   void* mem = nullptr;
   cudaError_t e = cudaMallocAsync(&mem, L.total, s);
   if (e != cudaSuccess) return from_cuda(e);
@@ -494,16 +575,18 @@ int pss_tree_root(const pss_tree* tree, void* stream, pss_summary** out) {
     cudaFreeAsync(mem, s);
     return from_cuda(e);
   }
-  pss_summary* sm = new (std::nothrow) pss_summary;
+  pss_summary* sm = new_summary(tree->k, tree->kind, w, mem, s);
   if (!sm) {
     cudaFreeAsync(mem, s);
     return PSS_ENOMEM;
   }
-  sm->k = k;
-  sm->item_bytes = w;
-  sm->mem = mem;
-  sm->stream = s;
   *out = sm;
+  return PSS_OK;
+}
+
+int pss_tree_kind(const pss_tree* tree, int* kind) {
+  if (!tree || !kind) return PSS_EINVAL;
+  *kind = tree->kind;
   return PSS_OK;
 }
 
@@ -517,11 +600,12 @@ void pss_tree_free(pss_tree* tree) {
 int pss_merge(const pss_summary* a, const pss_summary* b, void* stream, pss_summary** out) {
   if (!a || !b || !out) return PSS_EINVAL;
   *out = nullptr;
-  if (a->k != b->k || a->item_bytes != b->item_bytes) return PSS_EMISMATCH;
+  if (a->k != b->k || a->item_bytes != b->item_bytes || a->kind != b->kind) return PSS_EMISMATCH;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = prepare_device();
   if (e != cudaSuccess) return from_cuda(e);
-  const uint32_t k = a->k;
+  const uint32_t k = a->cap;
+  const bool mg = a->kind == PSS_KIND_FREQUENT;
   const int w = a->item_bytes;
   void* mem = nullptr;
   e = alloc_set(1, k, w, s, &mem);
@@ -531,23 +615,19 @@ int pss_merge(const pss_summary* a, const pss_summary* b, void* stream, pss_summ
   if (w == 4)
     e = launch_merge_pair<uint32_t>(set_view<uint32_t>(a->mem, 1, k), 0,
                                     set_view<uint32_t>(b->mem, 1, k), 0,
-                                    set_view<uint32_t>(mem, 1, k), s);
+                                    set_view<uint32_t>(mem, 1, k), s, mg);
   else
     e = launch_merge_pair<u64>(set_view<u64>(a->mem, 1, k), 0, set_view<u64>(b->mem, 1, k), 0,
-                               set_view<u64>(mem, 1, k), s);
+                               set_view<u64>(mem, 1, k), s, mg);
   if (e != cudaSuccess) {
     cudaFreeAsync(mem, s);
     return from_cuda(e);
   }
-  pss_summary* sm = new (std::nothrow) pss_summary;
+  pss_summary* sm = new_summary(a->k, a->kind, w, mem, s);
   if (!sm) {
     cudaFreeAsync(mem, s);
     return PSS_ENOMEM;
   }
-  sm->k = k;
-  sm->item_bytes = w;
-  sm->mem = mem;
-  sm->stream = s;
   *out = sm;
   return PSS_OK;
 }
@@ -556,8 +636,9 @@ int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* hos
               uint32_t* n_out, void* stream) {
   if (!summary || !n_out || k < 2) return PSS_EINVAL;
   if (cap > 0 && !host_out) return PSS_EINVAL;
-  return canon_out(summary->mem, 1, 0, summary->k, summary->item_bytes, n, k, 1, host_out, cap,
-                   n_out, (cudaStream_t)stream);
+  const int filter = summary->kind == PSS_KIND_FREQUENT ? 3 : 1;
+  return canon_out(summary->mem, 1, 0, summary->cap, summary->item_bytes, n, k, filter, host_out,
+                   cap, n_out, (cudaStream_t)stream);
 }
 
 int pss_import(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered, uint32_t k,
@@ -581,15 +662,11 @@ int pss_import(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_c
     cudaFreeAsync(mem, s);
     return from_cuda(e);
   }
-  pss_summary* sm = new (std::nothrow) pss_summary;
+  pss_summary* sm = new_summary(k, PSS_KIND_SPACE_SAVING, item_bytes, mem, s);
   if (!sm) {
     cudaFreeAsync(mem, s);
     return PSS_ENOMEM;
   }
-  sm->k = k;
-  sm->item_bytes = item_bytes;
-  sm->mem = mem;
-  sm->stream = s;
   *out = sm;
   return PSS_OK;
 }
@@ -599,8 +676,10 @@ int pss_query_mode(const pss_summary* summary, uint64_t n, uint32_t k, int mode,
   if (mode != PSS_QUERY_CANDIDATES && mode != PSS_QUERY_GUARANTEED) return PSS_EINVAL;
   if (!summary || !n_out || k < 2) return PSS_EINVAL;
   if (cap > 0 && !host_out) return PSS_EINVAL;
-  return canon_out(summary->mem, 1, 0, summary->k, summary->item_bytes, n, k,
-                   mode == PSS_QUERY_GUARANTEED ? 2 : 1, host_out, cap, n_out, (cudaStream_t)stream);
+  const bool g = mode == PSS_QUERY_GUARANTEED;
+  const int filter = summary->kind == PSS_KIND_FREQUENT ? (g ? 4 : 3) : (g ? 2 : 1);
+  return canon_out(summary->mem, 1, 0, summary->cap, summary->item_bytes, n, k, filter, host_out,
+                   cap, n_out, (cudaStream_t)stream);
 }
 
 int pss_exact_counts(const void* d_items, uint64_t n, int item_bytes, int log2u, uint32_t* d_counts,
@@ -616,15 +695,16 @@ int pss_exact_counts(const void* d_items, uint64_t n, int item_bytes, int log2u,
 int pss_accuracy_of(const pss_summary* summary, const uint32_t* d_counts, int log2u, uint64_t n,
                     uint32_t k, pss_accuracy* out, void* stream) {
   if (!summary || !d_counts || !out || k < 2 || log2u < 1 || log2u > 32) return PSS_EINVAL;
+  if (summary->kind != PSS_KIND_SPACE_SAVING) return PSS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   void* dmem = nullptr;
   cudaError_t e = cudaMallocAsync(&dmem, sizeof(pss::AccOut), s);
   if (e != cudaSuccess) return from_cuda(e);
   pss::AccOut* d = (pss::AccOut*)dmem;
   e = summary->item_bytes == 4
-          ? pss::launch_accuracy<uint32_t>(set_view<uint32_t>(summary->mem, 1, summary->k), d_counts,
+          ? pss::launch_accuracy<uint32_t>(set_view<uint32_t>(summary->mem, 1, summary->cap), d_counts,
                                            log2u, n, k, d, s)
-          : pss::launch_accuracy<u64>(set_view<u64>(summary->mem, 1, summary->k), d_counts, log2u, n,
+          : pss::launch_accuracy<u64>(set_view<u64>(summary->mem, 1, summary->cap), d_counts, log2u, n,
                                       k, d, s);
   pss::AccOut h{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -647,15 +727,21 @@ int pss_export(const pss_summary* summary, pss_entry* host_out, uint32_t cap, ui
   if (!summary || !size) return PSS_EINVAL;
   if (cap > 0 && !host_out) return PSS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = canon_out(summary->mem, 1, 0, summary->k, summary->item_bytes, 0, 1, 0, host_out, cap,
+  int rc = canon_out(summary->mem, 1, 0, summary->cap, summary->item_bytes, 0, 1, 0, host_out, cap,
                      size, s);
   if (rc) return rc;
-  const SetLayout L = set_layout(1, summary->k, summary->item_bytes);
+  const SetLayout L = set_layout(1, summary->cap, summary->item_bytes);
   uint64_t hm = 0, hc = 0;
   cudaError_t e = cudaMemcpyAsync(&hm, (char*)summary->mem + L.m, 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, (char*)summary->mem + L.ncov, 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return from_cuda(e);
+  if (summary->kind == PSS_KIND_FREQUENT) {
+    // delta = floor((n_covered - sum of counts) / k): the bound on every count
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < *size; ++i) total += host_out[i].count;
+    hm = (hc - total) / summary->k;
+  }
   if (m) *m = hm;
   if (n_covered) *n_covered = hc;
   return PSS_OK;
@@ -665,6 +751,12 @@ int pss_summary_info(const pss_summary* summary, uint32_t* k, int* item_bytes) {
   if (!summary) return PSS_EINVAL;
   if (k) *k = summary->k;
   if (item_bytes) *item_bytes = summary->item_bytes;
+  return PSS_OK;
+}
+
+int pss_summary_kind(const pss_summary* summary, int* kind) {
+  if (!summary || !kind) return PSS_EINVAL;
+  *kind = summary->kind;
   return PSS_OK;
 }
 

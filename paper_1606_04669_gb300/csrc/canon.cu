@@ -61,6 +61,21 @@ __device__ void canon_node(const SetView<ItemT>& in, uint32_t node, u64 n, uint3
   const uint32_t tid = threadIdx.x;
   const uint32_t size = in.size[node];
   const size_t base = (size_t)node * k;
+  // Frequent summaries: delta = floor((n_covered - sum of counts) / kq)
+  const bool mg = filter >= 3;
+  u64 delta = 0;
+  if (mg) {
+    __shared__ u64 part[BS / 32];
+    u64 sum = 0;
+    for (uint32_t i = tid; i < size; i += BS) sum += in.count[base + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((tid & 31) == 0) part[tid >> 5] = sum;
+    __syncthreads();
+    sum = 0;
+    for (int w = 0; w < BS / 32; ++w) sum += part[w];
+    delta = (in.ncov[node] - sum) / kq;
+  }
   uint32_t nk = 0, par = 0;
   for (uint32_t b0 = 0; b0 < size; b0 += BS) {
     const uint32_t i = b0 + tid;
@@ -69,8 +84,10 @@ __device__ void canon_node(const SetView<ItemT>& in, uint32_t node, u64 n, uint3
     if (i < size) {
       c = in.count[base + i];
       // filter 1: count k > n (candidates); 2: (count - err) k > n (guaranteed,
-      // since count - err <= f)
-      const u64 t = filter == 2 ? c - in.err[base + i] : c;
+      // since count - err <= f); 3: (count + delta) k > n (Frequent
+      // candidates: count <= f <= count + delta); 4: count k > n (Frequent
+      // guaranteed)
+      const u64 t = filter == 2 ? c - in.err[base + i] : (filter == 3 ? c + delta : c);
       keep = !filter || __umul64hi(t, (u64)kq) != 0 || t * (u64)kq > n;
     }
     uint32_t tot;
@@ -95,7 +112,7 @@ __device__ void canon_node(const SetView<ItemT>& in, uint32_t node, u64 n, uint3
     pss_entry e;
     e.item = k2[i];
     e.count = ~k1[i];
-    e.err = in.err[base + pay[i]];
+    e.err = mg ? delta : in.err[base + pay[i]];
     out[i] = e;
   }
   if (tid == 0) {

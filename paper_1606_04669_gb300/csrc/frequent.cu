@@ -1,0 +1,333 @@
+// frequent.cu — Frequent (Misra–Gries) block summaries, the second
+// counter-based summary the paper discusses next to Space Saving (Section 2).
+//
+// With k - 1 counters (the k-majority problem): an item already counted adds
+// 1 to its counter; an item not counted takes a free counter with count 1;
+// when no counter is free every counter loses 1, the counters that reach 0
+// are freed, and the item is not stored (Misra and Gries, 1982).  Unlike
+// Space Saving the result is a set with no tie to break: which free counter
+// an item takes does not change it.
+//
+// One warp per block of Algorithm 1, sequential over the block's items like
+// the definition.  The warp's k - 1 counters (item, u32 count) and a
+// linear-probe hash table of 32-bit cells (16-bit tag | slot + 1) at most
+// half full live in its own slice of shared memory; the 32 lanes probe 32
+// consecutive cells of an item at once (one ballot for a match, one for the
+// first empty cell).  A decrement step is one pass of the lanes over the
+// counters; when it frees counters the warp compacts the live ones to the
+// front and rebuilds the table (freed counters leave no holes in the probe
+// runs).  A decrement step follows at least k - 1 increments, so this work
+// adds O(1) per item.  The output node is sorted by item (a bitonic sort over
+// the warp's slice), the layout the combine kernel reads; err and m are 0.
+#include <atomic>
+
+#include "pss_internal.cuh"
+#include "pss_kernels.cuh"
+
+namespace pss {
+
+namespace {
+
+constexpr uint32_t FULL_MASK = 0xffffffffu;
+
+template <typename ItemT>
+struct FHash;
+template <>
+struct FHash<uint32_t> {
+  __device__ static __forceinline__ uint32_t h(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+  }
+};
+template <>
+struct FHash<u64> {
+  __device__ static __forceinline__ uint32_t h(u64 x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return (uint32_t)x;
+  }
+};
+
+// One warp's slice: key[cap], cnt[cap], cell[nb].
+struct FLayout {
+  uint32_t cap, nb, shift;
+  size_t cnt, cell, bytes;
+};
+
+__host__ __device__ inline FLayout f_layout(uint32_t kc, int item_bytes) {
+  FLayout L;
+  L.cap = next_pow2(kc < 32 ? 32 : kc);
+  L.nb = next_pow2(2 * kc < 64 ? 64 : 2 * kc);
+  uint32_t lg = 0;
+  while ((1u << lg) < L.nb) ++lg;
+  L.shift = 32 - lg;
+  auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  L.cnt = up((size_t)item_bytes * L.cap);
+  L.cell = L.cnt + up(4ull * L.cap);
+  L.bytes = L.cell + up(4ull * L.nb);
+  return L;
+}
+
+__device__ __forceinline__ uint32_t f_tag(uint32_t h) {
+  const uint32_t t = h & 0xFFFFu;
+  return t ? t : 1u;
+}
+
+template <typename ItemT>
+struct FWarp {
+  ItemT* key;
+  uint32_t* cnt;
+  uint32_t* cell;
+  uint32_t kc, cap, nbmask, shift, lane;
+  uint32_t used;     // counters in use, slots [0, used) (warp-uniform)
+  uint32_t status;   // ST_* bits seen by this lane
+
+  __device__ __forceinline__ uint32_t home(uint32_t h) const { return h >> shift; }
+
+  // Slot of x, or -1 with *epos = the first empty cell of its probe run.
+  // Cells are only added between rebuilds, so a stored x sits before the
+  // first empty cell from its home.
+  __device__ __forceinline__ int find(ItemT x, uint32_t h, uint32_t* epos) {
+    const uint32_t tag = f_tag(h), b = home(h);
+    for (uint32_t base = 0; base <= nbmask; base += 32) {
+      const uint32_t c = cell[(b + base + lane) & nbmask];
+      const bool m = (c >> 16) == tag && key[(c & 0xFFFFu) - 1] == x;
+      const unsigned bm = __ballot_sync(FULL_MASK, m);
+      const unsigned be = __ballot_sync(FULL_MASK, c == 0u);
+      if (bm) return (int)((__shfl_sync(FULL_MASK, c, __ffs(bm) - 1) & 0xFFFFu) - 1);
+      if (be) {
+        *epos = (b + base + (uint32_t)__ffs(be) - 1) & nbmask;
+        return -1;
+      }
+    }
+    status |= ST_PROBE;  // cannot happen: the table is at most half full
+    *epos = 0xFFFFFFFFu;
+    return -1;
+  }
+
+  // Table insert of slot s (one lane; lanes insert concurrently).
+  __device__ __forceinline__ void insert(uint32_t s) {
+    const uint32_t h = FHash<ItemT>::h(key[s]);
+    const uint32_t val = (f_tag(h) << 16) | (s + 1);
+    uint32_t pos = home(h);
+    for (uint32_t step = 0; step <= nbmask; ++step) {
+      if (atomicCAS(&cell[pos], 0u, val) == 0u) return;
+      pos = (pos + 1) & nbmask;
+    }
+    status |= ST_PROBE;
+  }
+
+  // Live counters to the front (in slot order), then a fresh table.
+  __device__ void compact_and_rebuild() {
+    uint32_t live = 0;
+    for (uint32_t b0 = 0; b0 < used; b0 += 32) {
+      const uint32_t i = b0 + lane;
+      const uint32_t c = i < used ? cnt[i] : 0u;
+      const ItemT kx = i < used ? key[i] : (ItemT)0;
+      const unsigned bl = __ballot_sync(FULL_MASK, c != 0u);
+      __syncwarp();  // every lane has read its slot before any write
+      if (c != 0u) {
+        const uint32_t d = live + (uint32_t)__popc(bl & ((1u << lane) - 1u));
+        key[d] = kx;
+        cnt[d] = c;
+      }
+      live += (uint32_t)__popc(bl);
+      __syncwarp();
+    }
+    used = live;
+    for (uint32_t i = lane; i <= nbmask; i += 32) cell[i] = 0u;
+    __syncwarp();
+    for (uint32_t i = lane; i < used; i += 32) insert(i);
+    __syncwarp();
+  }
+
+  // No free counter: every counter loses 1.
+  __device__ void decrement_all() {
+    bool freed = false;
+    for (uint32_t i = lane; i < used; i += 32) {
+      const uint32_t c = cnt[i] - 1u;
+      cnt[i] = c;
+      freed |= c == 0u;
+    }
+    if (__any_sync(FULL_MASK, freed)) {
+      __syncwarp();
+      compact_and_rebuild();
+    }
+  }
+
+  // Slots [0, cap) in item order, the used ones first (unused: count 0).
+  __device__ void sort_by_item() {
+    for (uint32_t i = used + lane; i < cap; i += 32) cnt[i] = 0u;
+    __syncwarp();
+    for (uint32_t size = 2; size <= cap; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t i = lane; i < (cap >> 1); i += 32) {
+          const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+          const bool asc = (lo & size) == 0;
+          const ItemT ka = key[lo], kb = key[hi];
+          const uint32_t ca = cnt[lo], cb = cnt[hi];
+          const bool greater = ca == 0u ? cb != 0u : (cb != 0u && ka > kb);
+          if (greater == asc) {
+            key[lo] = kb; key[hi] = ka;
+            cnt[lo] = cb; cnt[hi] = ca;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+};
+
+template <typename ItemT>
+__device__ void frequent_block(const ItemT* __restrict__ xs, uint32_t len, uint32_t kc,
+                               unsigned char* slice, const SetView<ItemT>& out, uint32_t node) {
+  const FLayout L = f_layout(kc, (int)sizeof(ItemT));
+  FWarp<ItemT> W;
+  W.key = (ItemT*)slice;
+  W.cnt = (uint32_t*)(slice + L.cnt);
+  W.cell = (uint32_t*)(slice + L.cell);
+  W.kc = kc;
+  W.cap = L.cap;
+  W.nbmask = L.nb - 1;
+  W.shift = L.shift;
+  W.lane = threadIdx.x & 31;
+  W.used = 0;
+  W.status = 0;
+  for (uint32_t i = W.lane; i < L.nb; i += 32) W.cell[i] = 0u;
+  __syncwarp();
+
+  // 32 items per coalesced load, the next 32 in flight meanwhile
+  ItemT nxt = W.lane < len ? xs[W.lane] : (ItemT)0;
+  for (uint32_t t0 = 0; t0 < len; t0 += 32) {
+    const ItemT cur = nxt;
+    const uint32_t here = min(32u, len - t0);
+    if (t0 + 32 + W.lane < len) nxt = xs[t0 + 32 + W.lane];
+    for (uint32_t j = 0; j < here; ++j) {
+      const ItemT x = __shfl_sync(FULL_MASK, cur, (int)j);
+      const uint32_t h = FHash<ItemT>::h(x);
+      uint32_t epos;
+      const int s = W.find(x, h, &epos);
+      if (s >= 0) {
+        if (W.lane == 0) W.cnt[s] += 1u;
+      } else if (W.used < kc) {
+        if (epos != 0xFFFFFFFFu) {
+          if (W.lane == 0) {
+            W.key[W.used] = x;
+            W.cnt[W.used] = 1u;
+            W.cell[epos] = (f_tag(h) << 16) | (W.used + 1);
+          }
+          ++W.used;
+        }
+      } else {
+        W.decrement_all();
+      }
+      __syncwarp();
+    }
+  }
+
+  W.sort_by_item();
+  const size_t base = (size_t)node * out.k;
+  for (uint32_t i = W.lane; i < W.used; i += 32) {
+    out.item[base + i] = W.key[i];
+    out.count[base + i] = W.cnt[i];
+    out.err[base + i] = 0ull;
+  }
+  const uint32_t st = __reduce_or_sync(FULL_MASK, W.status);
+  if (W.lane == 0) {
+    out.size[node] = W.used;
+    out.m[node] = 0ull;
+    out.ncov[node] = len;
+    if (st) atomicOr(out.status, st);
+  }
+}
+
+// Warp w of CTA b summarizes block r0 + b * warps + w of p into node
+// node0 + b * warps + w; each warp owns `wbytes` of shared memory.
+template <typename ItemT>
+__global__ void __launch_bounds__(256) frequent_block_kernel(const ItemT* __restrict__ items,
+                                                             u64 n, uint32_t p, uint32_t r0,
+                                                             uint32_t count, SetView<ItemT> out,
+                                                             uint32_t node0, uint32_t kc,
+                                                             uint32_t wbytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t j = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (j >= count) return;  // the whole warp
+  const uint32_t r = r0 + j, node = node0 + j;
+  const u64 left = block_bound(r, n, p), right = block_bound((u64)r + 1, n, p);
+  if (right - left >= (1ull << 32)) {
+    if (lane == 0) {
+      out.size[node] = 0;
+      out.m[node] = 0;
+      out.ncov[node] = right - left;
+      atomicOr(out.status, (uint32_t)ST_CHUNK);
+    }
+    return;
+  }
+  frequent_block<ItemT>(items + left, (uint32_t)(right - left), kc, smem + (size_t)warp * wbytes,
+                        out, node);
+}
+
+// Warps per CTA with the most warps resident per SM (ties: fewer), per k.
+template <typename ItemT>
+int frequent_warps_per_cta(uint32_t kc) {
+  static std::atomic<int> memo[PSS_MAX_K_RESIDENT + 1];
+  if (kc > PSS_MAX_K_RESIDENT) return 0;
+  int v = memo[kc].load(std::memory_order_relaxed);
+  if (v) return v;
+  const void* kern = (const void*)frequent_block_kernel<ItemT>;
+  if (ensure_kernel_attrs(kern) != cudaSuccess) return 0;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  const size_t wb = f_layout(kc, (int)sizeof(ItemT)).bytes;
+  int best = 0, best_warps = 0;
+  for (int wpc = 1; wpc <= 8; wpc *= 2) {
+    if ((size_t)wpc * wb > (size_t)optin) break;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * wpc, (size_t)wpc * wb) !=
+        cudaSuccess)
+      return 0;
+    if (blocks * wpc > best_warps) {
+      best_warps = blocks * wpc;
+      best = wpc;
+    }
+  }
+  if (best) memo[kc].store(best, std::memory_order_relaxed);
+  return best;
+}
+
+}  // namespace
+
+size_t frequent_warp_bytes(uint32_t kc, int item_bytes) { return f_layout(kc, item_bytes).bytes; }
+
+template <typename ItemT>
+cudaError_t launch_frequent_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
+                                   uint32_t count, SetView<ItemT> out, uint32_t node0,
+                                   cudaStream_t stream) {
+  const uint32_t kc = out.k;
+  const int wpc = frequent_warps_per_cta<ItemT>(kc);
+  if (wpc <= 0) return cudaErrorInvalidConfiguration;
+  if (count == 0) return cudaSuccess;
+  const size_t wb = f_layout(kc, (int)sizeof(ItemT)).bytes;
+  const uint32_t grid = (count + (uint32_t)wpc - 1) / (uint32_t)wpc;
+  frequent_block_kernel<ItemT><<<grid, 32 * wpc, (size_t)wpc * wb, stream>>>(
+      items, n, p, r0, count, out, node0, kc, (uint32_t)wb);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_frequent_blocks<uint32_t>(const uint32_t*, u64, uint32_t, uint32_t,
+                                                      uint32_t, SetView<uint32_t>, uint32_t,
+                                                      cudaStream_t);
+template cudaError_t launch_frequent_blocks<u64>(const u64*, u64, uint32_t, uint32_t, uint32_t,
+                                                 SetView<u64>, uint32_t, cudaStream_t);
+
+}  // namespace pss

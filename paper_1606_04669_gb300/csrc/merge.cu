@@ -94,8 +94,12 @@ __device__ __forceinline__ u64 block_reduce_u64(u64 v, u64* scratch, bool is_max
   return r;
 }
 
-// out node `no` = combine(A node na, B node nb).
-template <typename ItemT, int BS, bool BIG>
+// out node `no` = combine(A node na, B node nb).  MG: the merge of two
+// Frequent (Misra–Gries) summaries of capacity k instead: both minima are 0,
+// so the union adds the counts of equal items; when more than k items remain,
+// the (k+1)-th largest count c* is subtracted from every count and only the
+// counts above c* stay (their minimum and errors stay 0).
+template <typename ItemT, int BS, bool BIG, bool MG = false>
 __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<ItemT>& B,
                             uint32_t nb, const SetView<ItemT>& O, uint32_t no,
                             unsigned char* smem, unsigned char* gslice) {
@@ -159,7 +163,8 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
   }
   __syncthreads();
 
-  // Prune(k): the k-th largest count c*, and how many entries equal to c* to keep.
+  // Prune(k): the k-th largest count c*, and how many entries equal to c* to
+  // keep (MG: the (k+1)-th largest, none kept).
   const bool cut = U > k;
   u64 cstar = 0;
   uint32_t need = 0;
@@ -169,7 +174,7 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     mx = block_reduce_u64<BS>(mx, s.red, true);
     int shift = ((63 - __clzll((long long)mx)) / 8) * 8;
     u64 prefix = 0, pmask = 0;
-    need = k;
+    need = MG ? k + 1 : k;
     for (; shift >= 0; shift -= 8) {
       for (uint32_t i = tid; i < 256; i += BS) s.hist[i] = 0;
       __syncthreads();
@@ -206,21 +211,23 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     const bool eq = in && cut && c == cstar;
     uint32_t te;
     const uint32_t ee = scan(eq ? 1u : 0u, &te);
-    const bool keep = in && (!cut || c > cstar || (eq && run_eq + ee < need));
+    const bool keep = in && (!cut || c > cstar || (!MG && eq && run_eq + ee < need));
     uint32_t tk;
     const uint32_t ek = scan(keep ? 1u : 0u, &tk);
     if (keep) {
       const uint32_t o = run_keep + ek;
       const uint16_t a = s.srcA[u], b = s.srcB[u];
       O.item[bo + o] = (a != NONE) ? s.ia[a] : s.ib[b];
-      O.count[bo + o] = c;
+      O.count[bo + o] = (MG && cut) ? c - cstar : c;
       O.err[bo + o] = ((a != NONE) ? A.err[ba + a] : mA) + ((b != NONE) ? B.err[bb + b] : mB);
     }
     run_eq += te;
     run_keep += tk;
   }
   u64 mout = 0;
-  if (cut) {
+  if (MG) {
+    mout = 0;
+  } else if (cut) {
     mout = cstar;
   } else if (U == k) {
     u64 mn = ~0ull;
@@ -254,7 +261,7 @@ __device__ void copy_node(const SetView<ItemT>& in, uint32_t ni, const SetView<I
   }
 }
 
-template <typename ItemT, int BS, bool BIG>
+template <typename ItemT, int BS, bool BIG, bool MG>
 __global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out,
                                                          unsigned char* gscratch, size_t gslice) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -263,16 +270,16 @@ __global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetV
     copy_node<ItemT, BS>(in, 2 * j, out, j);
     return;
   }
-  merge_nodes<ItemT, BS, BIG>(in, 2 * j, in, 2 * j + 1, out, j, smem,
-                              BIG ? gscratch + (size_t)j * gslice : nullptr);
+  merge_nodes<ItemT, BS, BIG, MG>(in, 2 * j, in, 2 * j + 1, out, j, smem,
+                                  BIG ? gscratch + (size_t)j * gslice : nullptr);
 }
 
-template <typename ItemT, int BS, bool BIG>
+template <typename ItemT, int BS, bool BIG, bool MG>
 __global__ void __launch_bounds__(BS) merge_pair_kernel(SetView<ItemT> a, uint32_t ia,
                                                         SetView<ItemT> b, uint32_t ib,
                                                         SetView<ItemT> out, unsigned char* gscratch) {
   extern __shared__ __align__(16) unsigned char smem[];
-  merge_nodes<ItemT, BS, BIG>(a, ia, b, ib, out, 0, smem, gscratch);
+  merge_nodes<ItemT, BS, BIG, MG>(a, ia, b, ib, out, 0, smem, gscratch);
 }
 
 // Batch form: task (d, j) builds node j of the next level of descriptor d.
@@ -318,16 +325,25 @@ cudaError_t merge_scratch(uint32_t k, uint32_t ctas, cudaStream_t stream, void**
 }  // namespace
 
 template <typename ItemT>
-cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream) {
+cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream,
+                               bool mg) {
   const size_t smem = merge_smem_bytes<ItemT>(in.k);
-  if (in.k <= SS_SMEM_MAX_K) {
-    auto kern = merge_level_kernel<ItemT, MERGE_BS, false>;
+  if (mg) {
+    if (in.k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;
+    auto kern = merge_level_kernel<ItemT, MERGE_BS, false, true>;
     cudaError_t e = ensure_kernel_attrs((const void*)kern);
     if (e != cudaSuccess) return e;
     kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out, nullptr, 0);
     return cudaGetLastError();
   }
-  auto kern = merge_level_kernel<ItemT, MERGE_BS, true>;
+  if (in.k <= SS_SMEM_MAX_K) {
+    auto kern = merge_level_kernel<ItemT, MERGE_BS, false, false>;
+    cudaError_t e = ensure_kernel_attrs((const void*)kern);
+    if (e != cudaSuccess) return e;
+    kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out, nullptr, 0);
+    return cudaGetLastError();
+  }
+  auto kern = merge_level_kernel<ItemT, MERGE_BS, true, false>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   void* g = nullptr;
@@ -341,16 +357,24 @@ cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream
 
 template <typename ItemT>
 cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, uint32_t ib,
-                              SetView<ItemT> out, cudaStream_t stream) {
+                              SetView<ItemT> out, cudaStream_t stream, bool mg) {
   const size_t smem = merge_smem_bytes<ItemT>(out.k);
-  if (out.k <= SS_SMEM_MAX_K) {
-    auto kern = merge_pair_kernel<ItemT, MERGE_BS, false>;
+  if (mg) {
+    if (out.k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;
+    auto kern = merge_pair_kernel<ItemT, MERGE_BS, false, true>;
     cudaError_t e = ensure_kernel_attrs((const void*)kern);
     if (e != cudaSuccess) return e;
     kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out, nullptr);
     return cudaGetLastError();
   }
-  auto kern = merge_pair_kernel<ItemT, MERGE_BS, true>;
+  if (out.k <= SS_SMEM_MAX_K) {
+    auto kern = merge_pair_kernel<ItemT, MERGE_BS, false, false>;
+    cudaError_t e = ensure_kernel_attrs((const void*)kern);
+    if (e != cudaSuccess) return e;
+    kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out, nullptr);
+    return cudaGetLastError();
+  }
+  auto kern = merge_pair_kernel<ItemT, MERGE_BS, true, false>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   void* g = nullptr;
@@ -388,12 +412,13 @@ template cudaError_t launch_merge_tasks<u64>(const MergeDesc*, const BatchTask*,
                                              cudaStream_t);
 template size_t merge_smem_bytes<uint32_t>(uint32_t);
 template size_t merge_smem_bytes<u64>(uint32_t);
-template cudaError_t launch_merge_level<uint32_t>(SetView<uint32_t>, SetView<uint32_t>, cudaStream_t);
-template cudaError_t launch_merge_level<u64>(SetView<u64>, SetView<u64>, cudaStream_t);
+template cudaError_t launch_merge_level<uint32_t>(SetView<uint32_t>, SetView<uint32_t>, cudaStream_t,
+                                                  bool);
+template cudaError_t launch_merge_level<u64>(SetView<u64>, SetView<u64>, cudaStream_t, bool);
 template cudaError_t launch_merge_pair<uint32_t>(SetView<uint32_t>, uint32_t, SetView<uint32_t>,
-                                                 uint32_t, SetView<uint32_t>, cudaStream_t);
+                                                 uint32_t, SetView<uint32_t>, cudaStream_t, bool);
 template cudaError_t launch_merge_pair<u64>(SetView<u64>, uint32_t, SetView<u64>, uint32_t,
-                                            SetView<u64>, cudaStream_t);
+                                            SetView<u64>, cudaStream_t, bool);
 template cudaError_t launch_copy_node<uint32_t>(SetView<uint32_t>, uint32_t, SetView<uint32_t>,
                                                 uint32_t, cudaStream_t);
 template cudaError_t launch_copy_node<u64>(SetView<u64>, uint32_t, SetView<u64>, uint32_t,

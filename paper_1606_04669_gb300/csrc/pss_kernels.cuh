@@ -70,18 +70,33 @@ template <typename ItemT>
 size_t merge_smem_bytes(uint32_t k);
 
 // One level of the reduction tree: out node j = combine(in node 2j, in node
-// 2j+1), or a copy of in node 2j when it has no partner.
+// 2j+1), or a copy of in node 2j when it has no partner.  mg: the merge of
+// Frequent (Misra–Gries) summaries of capacity in.k instead.
 template <typename ItemT>
-cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream);
+cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream,
+                               bool mg = false);
 
 // Merge of two single summaries (node ia of a, node ib of b) into node 0 of out.
 template <typename ItemT>
 cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, uint32_t ib,
-                              SetView<ItemT> out, cudaStream_t stream);
+                              SetView<ItemT> out, cudaStream_t stream, bool mg = false);
+
+// Frequent (Misra–Gries) summaries with out.k counters (frequent.cu): blocks
+// r0 .. r0+count-1 of p into nodes node0 .. node0+count-1, one warp each.
+template <typename ItemT>
+cudaError_t launch_frequent_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
+                                   uint32_t count, SetView<ItemT> out, uint32_t node0,
+                                   cudaStream_t stream);
+
+// Shared memory of one Frequent warp with kc counters.
+size_t frequent_warp_bytes(uint32_t kc, int item_bytes);
 
 // Canonical export of node `node`: every entry (filter 0), entries with
 // count * kq > n (filter 1) or (count - err) * kq > n (filter 2), sorted by
-// (count desc, item asc), written to out[0..*out_n).
+// (count desc, item asc), written to out[0..*out_n).  Frequent summaries:
+// with delta = floor((n_covered - sum of counts) / kq), entries with
+// (count + delta) * kq > n (filter 3) or count * kq > n (filter 4), each with
+// err = delta.
 template <typename ItemT>
 cudaError_t launch_canon(SetView<ItemT> in, uint32_t node, u64 n, uint32_t kq, int filter,
                          pss_entry* out, uint32_t* out_n, cudaStream_t stream);

@@ -70,6 +70,8 @@ class Accuracy(ctypes.Structure):
 
 QUERY_CANDIDATES = 0
 QUERY_GUARANTEED = 1
+KIND_SPACE_SAVING = 0
+KIND_FREQUENT = 1
 
 
 class ServerConfig(ctypes.Structure):
@@ -102,6 +104,12 @@ SIGNATURES = {
     "pss_summarize_noalloc": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, u64p, u64p, u64p,
                                              vp]),
     "pss_summarize_tree": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp, ctypes.POINTER(vp)]),
+    "pss_frequent_summarize": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp,
+                                              ctypes.POINTER(vp)]),
+    "pss_frequent_summarize_tree": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp,
+                                                   ctypes.POINTER(vp)]),
+    "pss_summary_kind": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+    "pss_tree_kind": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
     "pss_tree_levels": (ctypes.c_int, [vp, u32p]),
     "pss_tree_level_nodes": (ctypes.c_int, [vp, u32, u32p]),
     "pss_tree_read_level": (ctypes.c_int, [vp, u32, u64p, u64p, u64p, u32p, u64p, u64p, vp]),
@@ -228,15 +236,21 @@ def _entries_to_arrays(buf, n):
 
 
 class Summary:
-    """A device-resident summary owned by libpss (freed on close / GC)."""
+    """A device-resident summary owned by libpss (freed on close / GC):
+    Space Saving (kind KIND_SPACE_SAVING) or Frequent / Misra–Gries
+    (KIND_FREQUENT: at most k - 1 entries, counts are lower bounds, export's
+    m is delta and the queries report err = delta)."""
 
     def __init__(self, handle: int, stream=None):
         self._h = vp(handle)
         k = u32()
         w = ctypes.c_int()
+        kind = ctypes.c_int()
         _check(load().pss_summary_info(self._h, ctypes.byref(k), ctypes.byref(w)), "pss_summary_info")
+        _check(load().pss_summary_kind(self._h, ctypes.byref(kind)), "pss_summary_kind")
         self.k = int(k.value)
         self.item_bytes = int(w.value)
+        self.kind = int(kind.value)
 
     @property
     def handle(self):
@@ -293,20 +307,27 @@ class Summary:
 class Tree:
     """Every level of one reduction tree (level 0 = block summaries)."""
 
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, k: int | None = None):
         self._h = vp(handle)
         lv = u32()
+        kind = ctypes.c_int()
         _check(load().pss_tree_levels(self._h, ctypes.byref(lv)), "pss_tree_levels")
+        _check(load().pss_tree_kind(self._h, ctypes.byref(kind)), "pss_tree_kind")
         self.levels = int(lv.value)
+        self.kind = int(kind.value)
+        self.k = k
 
     def nodes(self, level: int) -> int:
         n = u32()
         _check(load().pss_tree_level_nodes(self._h, level, ctypes.byref(n)), "pss_tree_level_nodes")
         return int(n.value)
 
-    def read_level(self, level: int, k: int, stream=None):
+    def read_level(self, level: int, k: int | None = None, stream=None):
         """Raw device layout of one level: list of (items, counts, errs, m, n_covered) per node,
-        entries sorted by item ascending."""
+        entries sorted by item ascending (a Frequent tree's nodes hold k - 1 entries)."""
+        k = self.k if k is None else int(k)
+        if self.kind == KIND_FREQUENT:
+            k -= 1
         nodes = self.nodes(level)
         it = np.zeros(nodes * k, np.uint64)
         ct = np.zeros(nodes * k, np.uint64)
@@ -373,7 +394,28 @@ def summarize_tree(items, k: int, p: int, stream=None) -> Tree:
     _check(load().pss_summarize_tree(vp(items.data_ptr()), items.numel(), w, int(k), int(p),
                                      vp(_stream_handle(stream)), ctypes.byref(h)),
            "pss_summarize_tree")
-    return Tree(h.value)
+    return Tree(h.value, int(k))
+
+
+def frequent(items, k: int, p: int, stream=None) -> Summary:
+    """pss_frequent_summarize: Misra–Gries summaries (k - 1 counters) of p
+    blocks merged by the binary tree of Frequent merges."""
+    w = _check_items(items)
+    h = vp()
+    _check(load().pss_frequent_summarize(vp(items.data_ptr()), items.numel(), w, int(k), int(p),
+                                         vp(_stream_handle(stream)), ctypes.byref(h)),
+           "pss_frequent_summarize")
+    return Summary(h.value)
+
+
+def frequent_tree(items, k: int, p: int, stream=None) -> Tree:
+    """pss_frequent_summarize_tree: as frequent, keeping every tree level."""
+    w = _check_items(items)
+    h = vp()
+    _check(load().pss_frequent_summarize_tree(vp(items.data_ptr()), items.numel(), w, int(k),
+                                              int(p), vp(_stream_handle(stream)), ctypes.byref(h)),
+           "pss_frequent_summarize_tree")
+    return Tree(h.value, int(k))
 
 
 def _entries_from(ex: "Exported"):
