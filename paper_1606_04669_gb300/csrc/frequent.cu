@@ -8,16 +8,19 @@
 // Space Saving the result is a set with no tie to break: which free counter
 // an item takes does not change it.
 //
-// One warp per block of Algorithm 1, sequential over the block's items like
-// the definition.  The warp's k - 1 counters (item, u32 count) and a
-// linear-probe hash table of 32-bit cells (16-bit tag | slot + 1) at most
-// half full live in its own slice of shared memory; the 32 lanes probe 32
-// consecutive cells of an item at once (one ballot for a match, one for the
-// first empty cell).  A decrement step is one pass of the lanes over the
-// counters; when it frees counters the warp compacts the live ones to the
-// front and rebuilds the table (freed counters leave no holes in the probe
-// runs).  A decrement step follows at least k - 1 increments, so this work
-// adds O(1) per item.  The output node is sorted by item (a bitonic sort over
+// One warp per block of Algorithm 1.  The warp's k - 1 counters (item, u32
+// count) and a linear-probe hash table of 32-bit cells (16-bit tag | slot +
+// 1) at most half full live in its own slice of shared memory.  The warp
+// takes 32 items at a time, one per lane, in stream order: every lane probes
+// its item; the hits before the first miss only add to counters, which
+// commute with each other and change no cell, so they are applied at once
+// (shared-memory atomics); the first miss is then applied by the whole warp
+// (a free counter, or a decrement step) and the lanes after it probe again.
+// A decrement step is one pass of the lanes over the counters; when it frees
+// counters the warp compacts the live ones to the front and rebuilds the
+// table (freed counters leave no holes in the probe runs).  There are at most
+// n / k decrement steps in a block of n items, so this work adds O(1) per
+// item.  The output node is sorted by item (a bitonic sort over
 // the warp's slice), the layout the combine kernel reads; err and m are 0.
 #include <atomic>
 
@@ -83,38 +86,38 @@ __device__ __forceinline__ uint32_t f_tag(uint32_t h) {
 template <typename ItemT>
 struct FWarp {
   ItemT* key;
-  uint32_t* cnt;
+  uint32_t* sc;      // stored counts: count + base
   uint32_t* cell;
   uint32_t kc, cap, nbmask, shift, lane;
   uint32_t used;     // counters in use, slots [0, used) (warp-uniform)
+  uint32_t base;     // decrement steps so far (warp-uniform)
+  uint32_t minc;     // full table: a lower bound on the smallest count (warp-uniform)
   uint32_t status;   // ST_* bits seen by this lane
 
   __device__ __forceinline__ uint32_t home(uint32_t h) const { return h >> shift; }
 
-  // Slot of x, or -1 with *epos = the first empty cell of its probe run.
-  // Cells are only added between rebuilds, so a stored x sits before the
-  // first empty cell from its home.
+  // This lane's probe for x: its slot, or -1 with *epos = the first empty
+  // cell of its probe run.  Cells are only added between rebuilds, so a
+  // stored x sits before the first empty cell from its home.
   __device__ __forceinline__ int find(ItemT x, uint32_t h, uint32_t* epos) {
-    const uint32_t tag = f_tag(h), b = home(h);
-    for (uint32_t base = 0; base <= nbmask; base += 32) {
-      const uint32_t c = cell[(b + base + lane) & nbmask];
-      const bool m = (c >> 16) == tag && key[(c & 0xFFFFu) - 1] == x;
-      const unsigned bm = __ballot_sync(FULL_MASK, m);
-      const unsigned be = __ballot_sync(FULL_MASK, c == 0u);
-      if (bm) return (int)((__shfl_sync(FULL_MASK, c, __ffs(bm) - 1) & 0xFFFFu) - 1);
-      if (be) {
-        *epos = (b + base + (uint32_t)__ffs(be) - 1) & nbmask;
+    const uint32_t tag = f_tag(h);
+    uint32_t pos = home(h);
+    for (uint32_t step = 0; step <= nbmask; ++step) {
+      const uint32_t c = cell[pos];
+      if (c == 0u) {
+        *epos = pos;
         return -1;
       }
+      if ((c >> 16) == tag && key[(c & 0xFFFFu) - 1] == x) return (int)(c & 0xFFFFu) - 1;
+      pos = (pos + 1) & nbmask;
     }
     status |= ST_PROBE;  // cannot happen: the table is at most half full
     *epos = 0xFFFFFFFFu;
     return -1;
   }
 
-  // Table insert of slot s (one lane; lanes insert concurrently).
-  __device__ __forceinline__ void insert(uint32_t s) {
-    const uint32_t h = FHash<ItemT>::h(key[s]);
+  // Table insert of slot s with hash h (lanes insert concurrently).
+  __device__ __forceinline__ void insert(uint32_t s, uint32_t h) {
     const uint32_t val = (f_tag(h) << 16) | (s + 1);
     uint32_t pos = home(h);
     for (uint32_t step = 0; step <= nbmask; ++step) {
@@ -124,19 +127,34 @@ struct FWarp {
     status |= ST_PROBE;
   }
 
-  // Live counters to the front (in slot order), then a fresh table.
-  __device__ void compact_and_rebuild() {
+  // The smallest count of the used counters (all lanes; warp-uniform result).
+  __device__ uint32_t min_count() const {
+    uint32_t mn = 0xFFFFFFFFu;
+    for (uint32_t i = lane; i < used; i += 32) mn = min(mn, sc[i] - base);
+    return __reduce_min_sync(FULL_MASK, mn);
+  }
+
+  // After a decrement step that may have brought counts to 0: free those
+  // counters (live ones compacted to the front in slot order, then a fresh
+  // table), else tighten the bound on the smallest count.
+  __device__ void settle() {
+    bool zero = false;
+    for (uint32_t i = lane; i < used; i += 32) zero |= sc[i] == base;
+    if (!__any_sync(FULL_MASK, zero)) {
+      minc = min_count();
+      return;
+    }
     uint32_t live = 0;
     for (uint32_t b0 = 0; b0 < used; b0 += 32) {
       const uint32_t i = b0 + lane;
-      const uint32_t c = i < used ? cnt[i] : 0u;
+      const uint32_t c = i < used ? sc[i] : base;
       const ItemT kx = i < used ? key[i] : (ItemT)0;
-      const unsigned bl = __ballot_sync(FULL_MASK, c != 0u);
+      const unsigned bl = __ballot_sync(FULL_MASK, c != base);
       __syncwarp();  // every lane has read its slot before any write
-      if (c != 0u) {
+      if (c != base) {
         const uint32_t d = live + (uint32_t)__popc(bl & ((1u << lane) - 1u));
         key[d] = kx;
-        cnt[d] = c;
+        sc[d] = c;
       }
       live += (uint32_t)__popc(bl);
       __syncwarp();
@@ -144,27 +162,14 @@ struct FWarp {
     used = live;
     for (uint32_t i = lane; i <= nbmask; i += 32) cell[i] = 0u;
     __syncwarp();
-    for (uint32_t i = lane; i < used; i += 32) insert(i);
+    for (uint32_t i = lane; i < used; i += 32) insert(i, FHash<ItemT>::h(key[i]));
     __syncwarp();
   }
 
-  // No free counter: every counter loses 1.
-  __device__ void decrement_all() {
-    bool freed = false;
-    for (uint32_t i = lane; i < used; i += 32) {
-      const uint32_t c = cnt[i] - 1u;
-      cnt[i] = c;
-      freed |= c == 0u;
-    }
-    if (__any_sync(FULL_MASK, freed)) {
-      __syncwarp();
-      compact_and_rebuild();
-    }
-  }
-
-  // Slots [0, cap) in item order, the used ones first (unused: count 0).
+  // Slots [0, cap) in item order, the used ones first with their counts
+  // (unused: count 0).
   __device__ void sort_by_item() {
-    for (uint32_t i = used + lane; i < cap; i += 32) cnt[i] = 0u;
+    for (uint32_t i = lane; i < cap; i += 32) sc[i] = i < used ? sc[i] - base : 0u;
     __syncwarp();
     for (uint32_t size = 2; size <= cap; size <<= 1) {
       for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
@@ -172,11 +177,11 @@ struct FWarp {
           const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
           const bool asc = (lo & size) == 0;
           const ItemT ka = key[lo], kb = key[hi];
-          const uint32_t ca = cnt[lo], cb = cnt[hi];
+          const uint32_t ca = sc[lo], cb = sc[hi];
           const bool greater = ca == 0u ? cb != 0u : (cb != 0u && ka > kb);
           if (greater == asc) {
             key[lo] = kb; key[hi] = ka;
-            cnt[lo] = cb; cnt[hi] = ca;
+            sc[lo] = cb; sc[hi] = ca;
           }
         }
         __syncwarp();
@@ -191,7 +196,7 @@ __device__ void frequent_block(const ItemT* __restrict__ xs, uint32_t len, uint3
   const FLayout L = f_layout(kc, (int)sizeof(ItemT));
   FWarp<ItemT> W;
   W.key = (ItemT*)slice;
-  W.cnt = (uint32_t*)(slice + L.cnt);
+  W.sc = (uint32_t*)(slice + L.cnt);
   W.cell = (uint32_t*)(slice + L.cell);
   W.kc = kc;
   W.cap = L.cap;
@@ -199,44 +204,87 @@ __device__ void frequent_block(const ItemT* __restrict__ xs, uint32_t len, uint3
   W.shift = L.shift;
   W.lane = threadIdx.x & 31;
   W.used = 0;
+  W.base = 0;
+  W.minc = 0;
   W.status = 0;
   for (uint32_t i = W.lane; i < L.nb; i += 32) W.cell[i] = 0u;
   __syncwarp();
+  const unsigned below = (1u << W.lane) - 1u;
 
-  // 32 items per coalesced load, the next 32 in flight meanwhile
+  // 32 items per coalesced load (lane i holds item t0 + i), the next 32 in
+  // flight meanwhile.  Lanes [start, here) are still to be applied; each
+  // round applies a prefix of them whose effects commute and probes the rest
+  // again.
   ItemT nxt = W.lane < len ? xs[W.lane] : (ItemT)0;
   for (uint32_t t0 = 0; t0 < len; t0 += 32) {
-    const ItemT cur = nxt;
+    const ItemT x = nxt;
     const uint32_t here = min(32u, len - t0);
     if (t0 + 32 + W.lane < len) nxt = xs[t0 + 32 + W.lane];
-    for (uint32_t j = 0; j < here; ++j) {
-      const ItemT x = __shfl_sync(FULL_MASK, cur, (int)j);
-      const uint32_t h = FHash<ItemT>::h(x);
-      uint32_t epos;
-      const int s = W.find(x, h, &epos);
-      if (s >= 0) {
-        if (W.lane == 0) W.cnt[s] += 1u;
-      } else if (W.used < kc) {
-        if (epos != 0xFFFFFFFFu) {
-          if (W.lane == 0) {
-            W.key[W.used] = x;
-            W.cnt[W.used] = 1u;
-            W.cell[epos] = (f_tag(h) << 16) | (W.used + 1);
+    const uint32_t h = FHash<ItemT>::h(x);
+    uint32_t start = 0;
+    while (start < here) {
+      const bool act = W.lane >= start && W.lane < here;
+      int s = -1;
+      uint32_t epos = 0xFFFFFFFFu;
+      if (act) s = W.find(x, h, &epos);
+      const bool miss = act && s < 0;
+      const unsigned mm = __ballot_sync(FULL_MASK, miss);
+      if (W.used < kc) {
+        // Free counters: the first occurrence (leader) of each missing item
+        // takes one; its later occurrences in the prefix add to it.  The
+        // prefix ends at the first leader that finds no free counter.
+        unsigned grp = 0;
+        if (miss) grp = __match_any_sync(mm, x);
+        const bool leader = miss && (grp & below) == 0;
+        const unsigned lead = __ballot_sync(FULL_MASK, leader);
+        const uint32_t free_n = kc - W.used;
+        const uint32_t end = (uint32_t)__popc(lead) <= free_n
+                                 ? here
+                                 : (uint32_t)__fns(lead, 0, (int)free_n + 1);
+        if (W.lane < end) {
+          if (leader) {
+            const uint32_t slot = W.used + (uint32_t)__popc(lead & below);
+            W.key[slot] = x;
+            W.sc[slot] = W.base + 1u;
+            W.insert(slot, h);
           }
-          ++W.used;
         }
+        __syncwarp();
+        if (W.lane < end) {
+          if (act && !miss) {
+            atomicAdd(&W.sc[s], 1u);
+          } else if (miss && !leader) {
+            const uint32_t lo = (uint32_t)__ffs(grp) - 1;  // its leader, before it
+            atomicAdd(&W.sc[W.used + (uint32_t)__popc(lead & ((1u << lo) - 1u))], 1u);
+          }
+        }
+        W.used += (uint32_t)__popc(lead & (end >= 32 ? FULL_MASK : (1u << end) - 1u));
+        if (W.used == kc) W.minc = 1;  // new counters hold 1
+        __syncwarp();
+        start = end;
       } else {
-        W.decrement_all();
+        // Full table: a miss is a decrement step.  While fewer steps than the
+        // smallest count have run, no count reaches 0, so the table's
+        // membership is fixed and hits and steps commute.
+        const uint32_t nm = (uint32_t)__popc(mm);
+        const uint32_t take = nm < W.minc ? nm : W.minc;  // steps applied now
+        const uint32_t end = nm < W.minc ? here : (uint32_t)__fns(mm, 0, (int)W.minc) + 1;
+        if (act && !miss && W.lane < end) atomicAdd(&W.sc[s], 1u);
+        W.base += take;
+        W.minc -= take;
+        __syncwarp();
+        if (W.minc == 0) W.settle();
+        start = end;
       }
-      __syncwarp();
     }
+    __syncwarp();
   }
 
   W.sort_by_item();
   const size_t base = (size_t)node * out.k;
   for (uint32_t i = W.lane; i < W.used; i += 32) {
     out.item[base + i] = W.key[i];
-    out.count[base + i] = W.cnt[i];
+    out.count[base + i] = W.sc[i];
     out.err[base + i] = 0ull;
   }
   const uint32_t st = __reduce_or_sync(FULL_MASK, W.status);
