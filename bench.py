@@ -49,6 +49,10 @@ WORKLOADS = {
              "seed 2; k=500; p=608 blocks of 262144 items (4 CTAs of 256 threads on each of 152 "
              "SMs); binary merge tree; query n/k",
         n=608 * 262144, w=4, s=1.0, log2u=32, seed=2, k=500, p=608),
+    "frequent_wave": dict(
+        desc="one wave of Frequent warps at k=2000: n=1368*262144 uint32 Zipf(s=1.1) over "
+             "[0,2^24), seed 2; p=1368 blocks of 262144 items (9 warps on each of 152 SMs)",
+        n=1368 * 262144, w=4, s=1.1, log2u=24, seed=2, k=2000, p=1368),
     "small": dict(
         desc="plain single stream: n=2^20 uint32 Zipf(s=1.1) over [0,2^20), seed 1; k=100; p=8; "
              "binary merge tree; query n/k",
@@ -458,25 +462,177 @@ def run_served(args):
     return 0
 
 
+FREQUENT_K = (2000, 500, 64)
+
+
+def run_frequent(args):
+    """The Frequent (Misra-Gries) summary with its merge tree and query on the
+    data of workload --base (default the plain one: n = 2^30 uint32 Zipf(1.1)
+    over [0, 2^24), seed 2, p = 4096), one JSON line per k (2000, 500, 64)."""
+    import numpy as np
+    import torch
+
+    import paper_1606_04669_gb300 as P
+    wl = WORKLOADS[args.base]
+    hbm, peak_kind = peaks()
+    n, p, w = wl["n"], wl["p"], wl["w"]
+    stream = torch.cuda.current_stream()
+    x = P.gen_zipf(n, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], item_bytes=w)
+    counts = P.exact_counts(x, wl["log2u"], stream=stream).cpu().numpy().view(np.uint32)
+    counts = counts.astype(np.int64)
+    torch.cuda.synchronize()
+    points = [int(v) for v in args.points.split(",")] if args.points else FREQUENT_K
+    for k in points:
+        def step():
+            sm = P.frequent(x, k, p, stream=stream)
+            q = sm.query(n, k, stream=stream)
+            sm.close()
+            return q
+
+        for _ in range(max(args.warmup, 1)):
+            q = step()
+        torch.cuda.synchronize()
+        P.profile_read(reset=True)
+        P.profile_enable(True)
+        clocks = ClockSampler(0)
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            q = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        prof = P.profile_read(reset=True)
+        P.profile_enable(False)
+        ms = e0.elapsed_time(e1) / args.steps
+        sum_ms = prof["summarize_ms"] / max(prof["summarize_calls"], 1)
+        merge_ms = prof["merge_ms"] / max(args.steps, 1)
+        # block summaries: read n*w input bytes once, write p*(k-1) entries and
+        # p block headers
+        alg = n * w + p * (k - 1) * (w + 16) + p * 24
+
+        # accuracy of the candidates against exact counts (outside the timed region)
+        f = counts[q.item.astype(np.int64)]
+        true_frequent = int((counts[:-1] * k > n).sum())
+        tp = int((f * k > n).sum())
+        rep = int(q.size)
+        accuracy = {"reported": rep, "true_frequent": true_frequent, "true_positive": tp,
+                    "guaranteed": int((q.count.astype(np.int64) * k > n).sum()),
+                    "are": float(np.mean(np.abs(f - q.count.astype(np.int64)) / f)) if rep else 0.0,
+                    "precision": tp / rep if rep else 1.0,
+                    "recall": tp / true_frequent if true_frequent else 1.0,
+                    "delta": int(q.err[0]) if rep else None,
+                    "reported_as": "query (count + delta) * k > n; ARE over the reported items"}
+
+        e2e = None
+        if not args.no_e2e:
+            hx = torch.empty(n, dtype=x.dtype, pin_memory=True)
+            hx.copy_(x)
+            dx = torch.empty_like(x)
+            torch.cuda.synchronize()
+
+            def estep():
+                dx.copy_(hx, non_blocking=True)
+                sm = P.frequent(dx, k, p, stream=stream)
+                qq = sm.query(n, k, stream=stream)
+                sm.close()
+                return qq
+
+            for _ in range(max(args.warmup, 1)):
+                qq = estep()
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            esteps = max(1, args.steps // 2)
+            a0.record(stream)
+            for _ in range(esteps):
+                qq = estep()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ems = a0.elapsed_time(a1) / esteps
+            e2e = {"value": n / (ems / 1e3), "unit": "items/s", "ms_per_step": ems,
+                   "h2d_bytes_per_step": n * w, "d2h_bytes_per_step": 8 + 24 * qq.size,
+                   "api": "pinned host -> device copy, pss_frequent_summarize + pss_query"}
+            del hx, dx
+
+        cpu = None
+        if not args.no_cpu:
+            cpu = cpu_baseline_frequent(wl, k, args.cpu_seconds)
+        line = {
+            "metric": METRIC, "workload": "frequent", "k": k, "value": n / (ms / 1e3),
+            "unit": "items/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "Frequent (Misra-Gries, k - 1 counters) summaries, merge tree "
+                                   "and query on " + wl["desc"].split("; k=")[0],
+                       "n": n, "k": k, "p": p, "item_bytes": w},
+            "input_gbs": n * w / (ms / 1e3) / 1e9,
+            "hbm_frac": n * w / (ms / 1e3) / 1e9 / hbm,
+            "roofline": {"bound": "hbm", "kernel": "frequent_block_kernel (block summaries)",
+                         "achieved": alg / (sum_ms / 1e3) / 1e9, "peak": hbm,
+                         "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": alg / (sum_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                         "avg_launch_ms": sum_ms, "algorithmic_bytes": alg},
+            "breakdown": {"summarize_ms": sum_ms, "merge_tree_ms": merge_ms},
+            "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(prof["launches"]), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_frequent(wl, k: int, budget_s: float):
+    """The Frequent oracle, single-threaded, over the first B blocks of the
+    workload (block summaries + merge tree + query), B sized to about
+    budget_s seconds."""
+    import oracle
+    n, p, w = wl["n"], wl["p"], wl["w"]
+    threads = os.cpu_count() or 1
+    lo0, hi0 = oracle.block_bounds(n, p, 0)
+    x0 = oracle.gen_zipf(hi0 - lo0, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w,
+                         threads=threads)
+    t = time.perf_counter()
+    oracle.frequent(x0, k)
+    per_block = max(time.perf_counter() - t, 1e-6)
+    blocks = int(max(2, min(p, budget_s / per_block)))
+    hi = oracle.block_bounds(n, p, blocks - 1)[1]
+    x = oracle.gen_zipf(hi, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], width=w,
+                        threads=threads)
+    t = time.perf_counter()
+    levels = oracle.frequent_tree(x, k, blocks)
+    oracle.frequent_query(levels[-1][0], hi, k)
+    dt = time.perf_counter() - t
+    return {"value": hi / dt, "unit": "items/s", "cores": 1, "kind": "oracle",
+            "sample": f"blocks 0..{blocks - 1} of the {p} blocks ({hi} items): Misra-Gries block "
+                      f"summaries, their merge tree and the query, single-threaded C++",
+            "seconds": dt, "host": host_info()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["sweep", "batched", "served"],
+    ap.add_argument("--workload",
+                    choices=sorted(WORKLOADS) + ["sweep", "batched", "served", "frequent"],
                     default="plain")
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
     ap.add_argument("--nstreams", type=int, default=1024)
-    ap.add_argument("--points", default="", help="sweep points to run, e.g. 0.5:500,1.1:2000")
+    ap.add_argument("--points", default="",
+                    help="sweep points to run, e.g. 0.5:500,1.1:2000; frequent: k values, e.g. 2000,64")
+    ap.add_argument("--base", choices=sorted(WORKLOADS), default="plain",
+                    help="frequent: the workload whose data, n and p it runs on")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
-    if args.workload in ("sweep", "batched", "served"):
+    if args.workload in ("sweep", "batched", "served", "frequent"):
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        return {"sweep": run_sweep, "batched": run_batched, "served": run_served}[args.workload](args)
+        return {"sweep": run_sweep, "batched": run_batched, "served": run_served,
+                "frequent": run_frequent}[args.workload](args)
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -9,8 +9,9 @@
 // an item takes does not change it.
 //
 // One warp per block of Algorithm 1.  The warp's k - 1 counters (item, u32
-// count) and a linear-probe hash table of 32-bit cells (16-bit tag | slot +
-// 1) at most half full live in its own slice of shared memory.  The warp
+// count) and a linear-probe hash table of 16-bit cells (slot + 1) at most
+// half full live in its own slice of shared memory (24 KB at k = 2000, so
+// that 9 warps share an SM).  The warp
 // takes 32 items at a time, one per lane, in stream order: every lane probes
 // its item; the hits before the first miss only add to counters, which
 // commute with each other and change no cell, so they are applied at once
@@ -74,20 +75,15 @@ __host__ __device__ inline FLayout f_layout(uint32_t kc, int item_bytes) {
   auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
   L.cnt = up((size_t)item_bytes * L.cap);
   L.cell = L.cnt + up(4ull * L.cap);
-  L.bytes = L.cell + up(4ull * L.nb);
+  L.bytes = L.cell + up(2ull * L.nb);
   return L;
-}
-
-__device__ __forceinline__ uint32_t f_tag(uint32_t h) {
-  const uint32_t t = h & 0xFFFFu;
-  return t ? t : 1u;
 }
 
 template <typename ItemT>
 struct FWarp {
   ItemT* key;
   uint32_t* sc;      // stored counts: count + base
-  uint32_t* cell;
+  unsigned short* cell;  // slot + 1, 0 = empty
   uint32_t kc, cap, nbmask, shift, lane;
   uint32_t used;     // counters in use, slots [0, used) (warp-uniform)
   uint32_t base;     // decrement steps so far (warp-uniform)
@@ -100,7 +96,6 @@ struct FWarp {
   // cell of its probe run.  Cells are only added between rebuilds, so a
   // stored x sits before the first empty cell from its home.
   __device__ __forceinline__ int find(ItemT x, uint32_t h, uint32_t* epos) {
-    const uint32_t tag = f_tag(h);
     uint32_t pos = home(h);
     for (uint32_t step = 0; step <= nbmask; ++step) {
       const uint32_t c = cell[pos];
@@ -108,7 +103,7 @@ struct FWarp {
         *epos = pos;
         return -1;
       }
-      if ((c >> 16) == tag && key[(c & 0xFFFFu) - 1] == x) return (int)(c & 0xFFFFu) - 1;
+      if (key[c - 1] == x) return (int)c - 1;
       pos = (pos + 1) & nbmask;
     }
     status |= ST_PROBE;  // cannot happen: the table is at most half full
@@ -116,13 +111,21 @@ struct FWarp {
     return -1;
   }
 
-  // Table insert of slot s with hash h (lanes insert concurrently).
+  // Table insert of slot s with hash h (lanes insert concurrently): a 32-bit
+  // compare-and-swap on the word holding the cell claims it when empty (a
+  // failed swap because the other cell of the word changed retries).
   __device__ __forceinline__ void insert(uint32_t s, uint32_t h) {
-    const uint32_t val = (f_tag(h) << 16) | (s + 1);
+    uint32_t* words = reinterpret_cast<uint32_t*>(cell);
     uint32_t pos = home(h);
-    for (uint32_t step = 0; step <= nbmask; ++step) {
-      if (atomicCAS(&cell[pos], 0u, val) == 0u) return;
-      pos = (pos + 1) & nbmask;
+    for (uint32_t tries = 0; tries <= 3 * nbmask + 3; ++tries) {
+      const uint32_t sh = (pos & 1u) * 16u;
+      uint32_t* wp = &words[pos >> 1];
+      const uint32_t old = *(volatile uint32_t*)wp;
+      if ((old >> sh) & 0xFFFFu) {
+        pos = (pos + 1) & nbmask;  // taken: next cell
+        continue;
+      }
+      if (atomicCAS(wp, old, old | ((s + 1) << sh)) == old) return;
     }
     status |= ST_PROBE;
   }
@@ -160,7 +163,7 @@ struct FWarp {
       __syncwarp();
     }
     used = live;
-    for (uint32_t i = lane; i <= nbmask; i += 32) cell[i] = 0u;
+    for (uint32_t i = lane; i <= nbmask; i += 32) cell[i] = 0;
     __syncwarp();
     for (uint32_t i = lane; i < used; i += 32) insert(i, FHash<ItemT>::h(key[i]));
     __syncwarp();
@@ -197,7 +200,7 @@ __device__ void frequent_block(const ItemT* __restrict__ xs, uint32_t len, uint3
   FWarp<ItemT> W;
   W.key = (ItemT*)slice;
   W.sc = (uint32_t*)(slice + L.cnt);
-  W.cell = (uint32_t*)(slice + L.cell);
+  W.cell = (unsigned short*)(slice + L.cell);
   W.kc = kc;
   W.cap = L.cap;
   W.nbmask = L.nb - 1;
@@ -207,7 +210,7 @@ __device__ void frequent_block(const ItemT* __restrict__ xs, uint32_t len, uint3
   W.base = 0;
   W.minc = 0;
   W.status = 0;
-  for (uint32_t i = W.lane; i < L.nb; i += 32) W.cell[i] = 0u;
+  for (uint32_t i = W.lane; i < L.nb; i += 32) W.cell[i] = 0;
   __syncwarp();
   const unsigned below = (1u << W.lane) - 1u;
 
