@@ -69,6 +69,27 @@ TRAFFIC = {"summarize_sha1": "f34a6510834efe750b50d521d53c776477dc093f",
            "bytes_per_block": (318.87e6 + 3.37e6) / 304, "block_items": 262144, "k": 2000, "w": 4}
 
 
+# DRAM traffic of the Frequent block kernel from one ncu capture (profiles/
+# frequent_block_kernel_wave_k2000.md: 1368 blocks of 262144 u32 items,
+# k = 2000 -> 1436.86 MB read + 3.54 MB written), valid for that source only.
+FREQ_TRAFFIC = {"frequent_sha1": "a1e03c216fc8fb285d92842dacf89b62eb9dc5ce",
+                "bytes_per_block": (1436.86e6 + 3.54e6) / 1368, "block_items": 262144, "k": 2000,
+                "w": 4}
+
+
+def frequent_traffic_per_launch(n, k, p, w):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1606_04669_gb300", "csrc", "frequent.cu")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    t = FREQ_TRAFFIC
+    if sha != t["frequent_sha1"] or k != t["k"] or w != t["w"] or n // p != t["block_items"]:
+        return None
+    return t["bytes_per_block"] * p
+
+
 def traffic_per_launch(wl):
     import hashlib
     src = os.path.join(ROOT, "paper_1606_04669_gb300", "csrc", "summarize.cu")
@@ -572,7 +593,8 @@ def run_frequent(args):
             "roofline": {"bound": "hbm", "kernel": "frequent_block_kernel (block summaries)",
                          "achieved": alg / (sum_ms / 1e3) / 1e9, "peak": hbm,
                          "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": alg / (sum_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                         "frac": alg / (sum_ms / 1e3) / 1e9 / hbm,
+                         "traffic": frequent_traffic_per_launch(n, k, p, w),
                          "avg_launch_ms": sum_ms, "algorithmic_bytes": alg},
             "breakdown": {"summarize_ms": sum_ms, "merge_tree_ms": merge_ms},
             "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e,
