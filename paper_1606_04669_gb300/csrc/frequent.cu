@@ -12,11 +12,12 @@
 // count) and a linear-probe hash table of 16-bit cells (slot + 1) at most
 // half full live in its own slice of shared memory (24 KB at k = 2000, so
 // that 9 warps share an SM).  The warp
-// takes 32 items at a time, one per lane, in stream order: every lane probes
-// its item; the hits before the first miss only add to counters, which
-// commute with each other and change no cell, so they are applied at once
-// (shared-memory atomics); the first miss is then applied by the whole warp
-// (a free counter, or a decrement step) and the lanes after it probe again.
+// takes 32 items at a time, one per lane, in stream order, in rounds: every
+// lane probes its item, and the round applies at once the longest prefix
+// whose effects commute (additions to counters; new items taking free
+// counters; decrement steps that cannot bring a count to 0), each distinct
+// item's occurrences by one lane (__match_any_sync groups); the lanes after
+// the prefix probe again in the next round.
 // A decrement step is one pass of the lanes over the counters; when it frees
 // counters the warp compacts the live ones to the front and rebuilds the
 // table (freed counters leave no holes in the probe runs).  There are at most
@@ -111,12 +112,14 @@ struct FWarp {
     return -1;
   }
 
-  // Table insert of slot s with hash h (lanes insert concurrently): a 32-bit
-  // compare-and-swap on the word holding the cell claims it when empty (a
-  // failed swap because the other cell of the word changed retries).
-  __device__ __forceinline__ void insert(uint32_t s, uint32_t h) {
+  // Table insert of slot s (lanes insert concurrently), walking its probe
+  // run from cell pos (its home, or the first empty cell a probe of this
+  // table found): a 32-bit compare-and-swap on the word holding a cell claims
+  // it when empty (a failed swap because the other cell of the word changed
+  // retries).
+  __device__ __forceinline__ void insert(uint32_t s, uint32_t pos) {
     uint32_t* words = reinterpret_cast<uint32_t*>(cell);
-    uint32_t pos = home(h);
+    pos &= nbmask;
     for (uint32_t tries = 0; tries <= 3 * nbmask + 3; ++tries) {
       const uint32_t sh = (pos & 1u) * 16u;
       uint32_t* wp = &words[pos >> 1];
@@ -165,7 +168,7 @@ struct FWarp {
     used = live;
     for (uint32_t i = lane; i <= nbmask; i += 32) cell[i] = 0;
     __syncwarp();
-    for (uint32_t i = lane; i < used; i += 32) insert(i, FHash<ItemT>::h(key[i]));
+    for (uint32_t i = lane; i < used; i += 32) insert(i, home(FHash<ItemT>::h(key[i])));
     __syncwarp();
   }
 
@@ -232,53 +235,49 @@ __device__ void frequent_block(const ItemT* __restrict__ xs, uint32_t len, uint3
       if (act) s = W.find(x, h, &epos);
       const bool miss = act && s < 0;
       const unsigned mm = __ballot_sync(FULL_MASK, miss);
+      // Occurrences of one item in the round form a group, led by its lowest
+      // lane; the leader applies every occurrence of its group before the
+      // round's end at once (distinct items touch distinct counters).
+      const unsigned am = __ballot_sync(FULL_MASK, act);
+      unsigned grp = 0;
+      if (act) grp = __match_any_sync(am, x);
+      const bool leader = act && (grp & below) == 0;
+      uint32_t end;
       if (W.used < kc) {
-        // Free counters: the first occurrence (leader) of each missing item
-        // takes one; its later occurrences in the prefix add to it.  The
-        // prefix ends at the first leader that finds no free counter.
-        unsigned grp = 0;
-        if (miss) grp = __match_any_sync(mm, x);
-        const bool leader = miss && (grp & below) == 0;
-        const unsigned lead = __ballot_sync(FULL_MASK, leader);
+        // Free counters: each missing item's leader takes one.  The round
+        // ends at the first missing leader that finds no free counter.
+        const unsigned lead = __ballot_sync(FULL_MASK, leader && miss);
         const uint32_t free_n = kc - W.used;
-        const uint32_t end = (uint32_t)__popc(lead) <= free_n
-                                 ? here
-                                 : (uint32_t)__fns(lead, 0, (int)free_n + 1);
-        if (W.lane < end) {
-          if (leader) {
+        end = (uint32_t)__popc(lead) <= free_n ? here : (uint32_t)__fns(lead, 0, (int)free_n + 1);
+        const unsigned before = end >= 32 ? FULL_MASK : (1u << end) - 1u;
+        if (leader && W.lane < end) {
+          const uint32_t c = (uint32_t)__popc(grp & before);
+          if (miss) {
             const uint32_t slot = W.used + (uint32_t)__popc(lead & below);
             W.key[slot] = x;
-            W.sc[slot] = W.base + 1u;
-            W.insert(slot, h);
+            W.sc[slot] = W.base + c;
+            W.insert(slot, epos);  // cells before it in the run stay taken
+          } else {
+            W.sc[s] += c;
           }
         }
-        __syncwarp();
-        if (W.lane < end) {
-          if (act && !miss) {
-            atomicAdd(&W.sc[s], 1u);
-          } else if (miss && !leader) {
-            const uint32_t lo = (uint32_t)__ffs(grp) - 1;  // its leader, before it
-            atomicAdd(&W.sc[W.used + (uint32_t)__popc(lead & ((1u << lo) - 1u))], 1u);
-          }
-        }
-        W.used += (uint32_t)__popc(lead & (end >= 32 ? FULL_MASK : (1u << end) - 1u));
-        if (W.used == kc) W.minc = 1;  // new counters hold 1
-        __syncwarp();
-        start = end;
+        W.used += (uint32_t)__popc(lead & before);
+        if (W.used == kc) W.minc = 1;  // every count is at least 1
       } else {
-        // Full table: a miss is a decrement step.  While fewer steps than the
-        // smallest count have run, no count reaches 0, so the table's
-        // membership is fixed and hits and steps commute.
+        // Full table: every missing occurrence is a decrement step.  While
+        // fewer steps than the smallest count have run, no count reaches 0,
+        // so the table's membership is fixed and hits and steps commute.
         const uint32_t nm = (uint32_t)__popc(mm);
         const uint32_t take = nm < W.minc ? nm : W.minc;  // steps applied now
-        const uint32_t end = nm < W.minc ? here : (uint32_t)__fns(mm, 0, (int)W.minc) + 1;
-        if (act && !miss && W.lane < end) atomicAdd(&W.sc[s], 1u);
+        end = nm < W.minc ? here : (uint32_t)__fns(mm, 0, (int)W.minc) + 1;
+        const unsigned before = end >= 32 ? FULL_MASK : (1u << end) - 1u;
+        if (leader && !miss && W.lane < end) W.sc[s] += (uint32_t)__popc(grp & before);
         W.base += take;
         W.minc -= take;
-        __syncwarp();
-        if (W.minc == 0) W.settle();
-        start = end;
       }
+      __syncwarp();
+      if (W.used == kc && W.minc == 0) W.settle();
+      start = end;
     }
     __syncwarp();
   }
