@@ -14,10 +14,10 @@
 // that 9 warps share an SM).  The warp
 // takes 32 items at a time, one per lane, in stream order, in rounds: every
 // lane probes its item, and the round applies at once the longest prefix
-// whose effects commute (additions to counters; new items taking free
-// counters; decrement steps that cannot bring a count to 0), each distinct
-// item's occurrences by one lane (__match_any_sync groups); the lanes after
-// the prefix probe again in the next round.
+// whose effects commute (additions to counters, by shared-memory atomics;
+// new items taking free counters, the first occurrence of each found with
+// __match_any_sync; decrement steps that cannot bring a count to 0); the
+// lanes after the prefix probe again in the next round.
 // A decrement step is one pass of the lanes over the counters; when it frees
 // counters the warp compacts the live ones to the front and rebuilds the
 // table (freed counters leave no holes in the probe runs).  There are at most
@@ -235,34 +235,34 @@ __device__ void frequent_block(const ItemT* __restrict__ xs, uint32_t len, uint3
       if (act) s = W.find(x, h, &epos);
       const bool miss = act && s < 0;
       const unsigned mm = __ballot_sync(FULL_MASK, miss);
-      // Occurrences of one item in the round form a group, led by its lowest
-      // lane; the leader applies every occurrence of its group before the
-      // round's end at once (distinct items touch distinct counters).
-      const unsigned am = __ballot_sync(FULL_MASK, act);
-      unsigned grp = 0;
-      if (act) grp = __match_any_sync(am, x);
-      const bool leader = act && (grp & below) == 0;
       uint32_t end;
       if (W.used < kc) {
-        // Free counters: each missing item's leader takes one.  The round
-        // ends at the first missing leader that finds no free counter.
-        const unsigned lead = __ballot_sync(FULL_MASK, leader && miss);
+        // Free counters: the first occurrence (leader) of each missing item
+        // takes one, its later occurrences in the round add to it.  The round
+        // ends at the first leader that finds no free counter.
+        unsigned grp = 0;
+        if (miss) grp = __match_any_sync(mm, x);
+        const bool leader = miss && (grp & below) == 0;
+        const unsigned lead = __ballot_sync(FULL_MASK, leader);
         const uint32_t free_n = kc - W.used;
         end = (uint32_t)__popc(lead) <= free_n ? here : (uint32_t)__fns(lead, 0, (int)free_n + 1);
-        const unsigned before = end >= 32 ? FULL_MASK : (1u << end) - 1u;
         if (leader && W.lane < end) {
-          const uint32_t c = (uint32_t)__popc(grp & before);
-          if (miss) {
-            const uint32_t slot = W.used + (uint32_t)__popc(lead & below);
-            W.key[slot] = x;
-            W.sc[slot] = W.base + c;
-            W.insert(slot, epos);  // cells before it in the run stay taken
-          } else {
-            W.sc[s] += c;
+          const uint32_t slot = W.used + (uint32_t)__popc(lead & below);
+          W.key[slot] = x;
+          W.sc[slot] = W.base + 1u;
+          W.insert(slot, epos);  // cells before it in the run stay taken
+        }
+        __syncwarp();
+        if (W.lane < end) {
+          if (act && !miss) {
+            atomicAdd(&W.sc[s], 1u);
+          } else if (miss && !leader) {
+            const uint32_t lo = (uint32_t)__ffs(grp) - 1;
+            atomicAdd(&W.sc[W.used + (uint32_t)__popc(lead & ((1u << lo) - 1u))], 1u);
           }
         }
-        W.used += (uint32_t)__popc(lead & before);
-        if (W.used == kc) W.minc = 1;  // every count is at least 1
+        W.used += (uint32_t)__popc(lead & (end >= 32 ? FULL_MASK : (1u << end) - 1u));
+        if (W.used == kc) W.minc = 1;  // new counters hold 1
       } else {
         // Full table: every missing occurrence is a decrement step.  While
         // fewer steps than the smallest count have run, no count reaches 0,
@@ -270,8 +270,7 @@ __device__ void frequent_block(const ItemT* __restrict__ xs, uint32_t len, uint3
         const uint32_t nm = (uint32_t)__popc(mm);
         const uint32_t take = nm < W.minc ? nm : W.minc;  // steps applied now
         end = nm < W.minc ? here : (uint32_t)__fns(mm, 0, (int)W.minc) + 1;
-        const unsigned before = end >= 32 ? FULL_MASK : (1u << end) - 1u;
-        if (leader && !miss && W.lane < end) W.sc[s] += (uint32_t)__popc(grp & before);
+        if (act && !miss && W.lane < end) atomicAdd(&W.sc[s], 1u);
         W.base += take;
         W.minc -= take;
       }
