@@ -71,9 +71,9 @@ TRAFFIC = {"summarize_sha1": "f34a6510834efe750b50d521d53c776477dc093f",
 
 # DRAM traffic of the Frequent block kernel from one ncu capture (profiles/
 # frequent_block_kernel_wave_k2000.md: 1368 blocks of 262144 u32 items,
-# k = 2000 -> 1436.86 MB read + 3.54 MB written), valid for that source only.
-FREQ_TRAFFIC = {"frequent_sha1": "a1e03c216fc8fb285d92842dacf89b62eb9dc5ce",
-                "bytes_per_block": (1436.86e6 + 3.54e6) / 1368, "block_items": 262144, "k": 2000,
+# k = 2000 -> 1434.75 MB read + 3.48 MB written), valid for that source only.
+FREQ_TRAFFIC = {"frequent_sha1": "936320a285ffb8ea4737aa15e0872cdb515a8279",
+                "bytes_per_block": (1434.75e6 + 3.48e6) / 1368, "block_items": 262144, "k": 2000,
                 "w": 4}
 
 
