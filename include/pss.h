@@ -202,8 +202,9 @@ void pss_tree_free(pss_tree* tree);
  * arguments of one kind, else PSS_EMISMATCH), pss_query / pss_query_mode,
  * pss_export, pss_free, and pss_tree_levels / _level_nodes / _read_level /
  * _root / _free for trees.  Not available for Frequent summaries:
- * pss_accuracy_of (PSS_EINVAL), pss_import (always Space Saving), the batch,
- * server and allocation-free forms, host input.
+ * pss_accuracy_of (PSS_EINVAL), pss_import (always Space Saving), the
+ * server and allocation-free forms, host input.  The batched form is
+ * pss_frequent_batch_create.
  *
  * pss_frequent_summarize — p Misra–Gries block summaries (Algorithm 1
  * bounds) merged in the binary tree over adjacent pairs (an odd last summary
@@ -256,6 +257,14 @@ uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hin
  * lists, results).  The streams' item buffers are borrowed for the batch's
  * lifetime.  Synchronizes stream. */
 int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out);
+
+/* The batched form of the Frequent (Misra–Gries) summary: every stream of
+ * desc is summarized with pss_frequent_summarize's blocks, merges and query
+ * (k - 1 counters; each stream's result equals pss_frequent_summarize +
+ * pss_query with the same k and p).  The block count comes from the same
+ * planner.  pss_batch_run, _results, _export (m receives delta), _plan,
+ * _info and _free apply unchanged. */
+int pss_frequent_batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out);
 
 /* The block count used for each stream (nstreams values). */
 int pss_batch_plan(const pss_batch* batch, uint32_t* p);

@@ -24,6 +24,7 @@ struct StreamPlan {
   const void* items;
   uint64_t n;
   uint32_t k, p;
+  uint32_t cap;                      // entries per node: k, or k - 1 (Frequent)
   std::vector<size_t> level_off;     // arena offset of each level's set
   std::vector<uint32_t> level_nodes;
   uint32_t out_off;                  // first result entry of this stream
@@ -89,6 +90,7 @@ __global__ void zero_words_kernel(char* arena, const size_t* offs, uint32_t coun
 struct pss_batch {
   uint32_t nstreams = 0;
   int w = 4;
+  int kind = PSS_KIND_SPACE_SAVING;
   std::vector<StreamPlan> s;
   std::vector<KClass> kc;
   char* arena = nullptr;
@@ -142,7 +144,9 @@ int enqueue(pss_batch* b, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return from_cuda(e);
   e = cudaEventRecord(b->kc[0].join, b->kc[0].side);
   if (e != cudaSuccess) return from_cuda(e);
+  const bool mg = b->kind == PSS_KIND_FREQUENT;
   for (KClass& c : b->kc) {
+    const uint32_t cap = mg ? c.k - 1 : c.k;
     e = cudaStreamWaitEvent(c.side, b->kc[0].join, 0);
     if (e != cudaSuccess) return from_cuda(e);
     e = cudaMemsetAsync(b->arena + c.counter_off, 0, 4, c.side);
@@ -160,10 +164,16 @@ int enqueue(pss_batch* b, cudaStream_t s) {
       }
       if (c.ntasks) {
         count_launches(1);
-        e = launch_summarize_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
-                                          (const BatchTask*)(b->arena + c.tasks_off), c.ntasks,
-                                          (uint32_t*)(b->arena + c.counter_off), c.k, c.grid,
-                                          c.side);
+        if (mg)
+          e = launch_frequent_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
+                                           (const BatchTask*)(b->arena + c.tasks_off), c.ntasks,
+                                           (uint32_t*)(b->arena + c.counter_off), cap, c.grid,
+                                           c.side);
+        else
+          e = launch_summarize_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
+                                            (const BatchTask*)(b->arena + c.tasks_off), c.ntasks,
+                                            (uint32_t*)(b->arena + c.counter_off), c.k, c.grid,
+                                            c.side);
       }
     }
     if (e != cudaSuccess) return from_cuda(e);
@@ -172,8 +182,8 @@ int enqueue(pss_batch* b, cudaStream_t s) {
       for (const LevelLaunch& L : c.levels) {
         count_launches(1);
         e = launch_merge_tasks<ItemT>((const MergeDesc*)(b->arena + L.descs_off),
-                                      (const BatchTask*)(b->arena + L.tasks_off), L.ntasks, c.k,
-                                      c.side);
+                                      (const BatchTask*)(b->arena + L.tasks_off), L.ntasks, cap,
+                                      c.side, mg);
         if (e != cudaSuccess) return from_cuda(e);
       }
     }
@@ -182,7 +192,7 @@ int enqueue(pss_batch* b, cudaStream_t s) {
       count_launches(1);
       e = launch_query_batch<ItemT>((const QueryDesc*)(b->arena + b->qdesc_off),
                                     (const uint32_t*)(b->arena + c.qids_off),
-                                    (uint32_t)c.sids.size(), c.k,
+                                    (uint32_t)c.sids.size(), cap,
                                     (pss_entry*)(b->arena + b->results_off),
                                     (uint32_t*)(b->arena + b->nout_off), c.side);
     }
@@ -216,7 +226,9 @@ void destroy(pss_batch* b) {
 
 }  // namespace
 
-extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out) {
+namespace {
+
+int batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out, int kind) {
   if (!desc || !out) return PSS_EINVAL;
   *out = nullptr;
   const uint32_t ns = desc->nstreams;
@@ -232,7 +244,9 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
   if (!b) return PSS_ENOMEM;
   b->nstreams = ns;
   b->w = w;
+  b->kind = kind;
   b->owner = s;
+  const bool mg = kind == PSS_KIND_FREQUENT;
   b->s.resize(ns);
   // ---- plan every stream and lay out its tree levels
   size_t off = 0;
@@ -249,21 +263,24 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
     sp.k = desc->k[i];
     const double skew = desc->skew_hint ? desc->skew_hint[i] : 0.0;
     sp.p = (desc->p && desc->p[i]) ? desc->p[i] : pss_plan_blocks(sp.n, sp.k, w, skew);
-    sp.warp = use_warp_kernel(sp.k, skew);
+    sp.warp = !mg && use_warp_kernel(sp.k, skew);
     if (sp.k < 2 || sp.k > PSS_MAX_K_RESIDENT || sp.p == 0 || (sp.n > 0 && !sp.items) ||
         (sp.n + sp.p - 1) / sp.p >= (1ull << 32)) {
       destroy(b);
       return PSS_EINVAL;
     }
-    const size_t need = w == 4 ? ss_smem_bytes<uint32_t>(sp.k) : ss_smem_bytes<u64>(sp.k);
-    const size_t need_m = w == 4 ? merge_smem_bytes<uint32_t>(sp.k) : merge_smem_bytes<u64>(sp.k);
+    sp.cap = mg ? sp.k - 1 : sp.k;
+    const size_t need = mg ? frequent_warp_bytes(sp.cap, w)
+                           : (w == 4 ? ss_smem_bytes<uint32_t>(sp.k) : ss_smem_bytes<u64>(sp.k));
+    const size_t need_m =
+        w == 4 ? merge_smem_bytes<uint32_t>(sp.cap) : merge_smem_bytes<u64>(sp.cap);
     if (need > (size_t)optin || need_m > (size_t)optin) {
       destroy(b);
       return PSS_EINVAL;
     }
     for (uint32_t nodes = sp.p;; nodes = (nodes + 1) / 2) {
       sp.level_nodes.push_back(nodes);
-      sp.level_off.push_back(take(set_layout(nodes, sp.k, w).total));
+      sp.level_off.push_back(take(set_layout(nodes, sp.cap, w).total));
       if (nodes == 1) break;
     }
     sp.out_off = (uint32_t)b->total_k;
@@ -320,7 +337,14 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
     };
     plan_tasks(false, &c.tasks_off, &c.counter_off, &c.ntasks);
     plan_tasks(true, &c.wtasks_off, &c.wcounter_off, &c.wntasks);
-    if (c.ntasks) {
+    if (c.ntasks && mg) {
+      c.grid = w == 4 ? frequent_batch_grid<uint32_t>(c.k - 1, c.ntasks, sms)
+                      : frequent_batch_grid<u64>(c.k - 1, c.ntasks, sms);
+      if (c.grid == 0) {
+        destroy(b);
+        return PSS_EINVAL;
+      }
+    } else if (c.ntasks) {
       const int per_sm = w == 4 ? summarize_ctas_per_sm<uint32_t>(c.k) : summarize_ctas_per_sm<u64>(c.k);
       if (per_sm <= 0) {
         destroy(b);
@@ -346,7 +370,7 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
         const StreamPlan& sp = b->s[i];
         if (l + 1 >= sp.level_nodes.size()) continue;
         const uint32_t d = (uint32_t)descs.size();
-        descs.push_back(MergeDesc{nullptr, nullptr, sp.level_nodes[l], sp.k});
+        descs.push_back(MergeDesc{nullptr, nullptr, sp.level_nodes[l], sp.cap});
         // pointers are fixed once the arena exists; record offsets for now
         descs.back().in = (void*)(uintptr_t)sp.level_off[l];
         descs.back().out = (void*)(uintptr_t)sp.level_off[l + 1];
@@ -368,7 +392,7 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
   std::vector<size_t> status_offs;
   for (const StreamPlan& sp : b->s)
     for (size_t l = 0; l < sp.level_off.size(); ++l)
-      status_offs.push_back(sp.level_off[l] + set_layout(sp.level_nodes[l], sp.k, w).status);
+      status_offs.push_back(sp.level_off[l] + set_layout(sp.level_nodes[l], sp.cap, w).status);
   b->nstatus = (uint32_t)status_offs.size();
   b->status_offs_off = take(sizeof(size_t) * status_offs.size());
   b->arena_bytes = align_up(off, 256);
@@ -384,8 +408,8 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
   std::vector<QueryDesc> qd(ns);
   for (uint32_t i = 0; i < ns && e == cudaSuccess; ++i) {
     const StreamPlan& sp = b->s[i];
-    bs[i] = BatchStream{sp.items, sp.n, sp.p, sp.k, b->arena + sp.level_off[0]};
-    qd[i] = QueryDesc{b->arena + sp.level_off.back(), sp.n, sp.k, sp.out_off};
+    bs[i] = BatchStream{sp.items, sp.n, sp.p, sp.cap, b->arena + sp.level_off[0]};
+    qd[i] = QueryDesc{b->arena + sp.level_off.back(), sp.n, sp.cap, sp.out_off, sp.k, mg ? 3 : 1};
   }
   for (Pending& pd : uploads) {  // merge descriptors: offsets -> pointers
     for (KClass& c : b->kc)
@@ -412,12 +436,13 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming);
     // set kernel attributes outside any capture
+    const uint32_t cap = mg ? c.k - 1 : c.k;
     if (e == cudaSuccess)
-      e = w == 4 ? launch_merge_tasks<uint32_t>(nullptr, nullptr, 0, c.k, c.side)
-                 : launch_merge_tasks<u64>(nullptr, nullptr, 0, c.k, c.side);
+      e = w == 4 ? launch_merge_tasks<uint32_t>(nullptr, nullptr, 0, cap, c.side, mg)
+                 : launch_merge_tasks<u64>(nullptr, nullptr, 0, cap, c.side, mg);
     if (e == cudaSuccess)
-      e = w == 4 ? launch_query_batch<uint32_t>(nullptr, nullptr, 0, c.k, nullptr, nullptr, c.side)
-                 : launch_query_batch<u64>(nullptr, nullptr, 0, c.k, nullptr, nullptr, c.side);
+      e = w == 4 ? launch_query_batch<uint32_t>(nullptr, nullptr, 0, cap, nullptr, nullptr, c.side)
+                 : launch_query_batch<u64>(nullptr, nullptr, 0, cap, nullptr, nullptr, c.side);
   }
   if (e != cudaSuccess) {
     destroy(b);
@@ -425,6 +450,17 @@ extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_ba
   }
   *out = b;
   return PSS_OK;
+}
+
+}  // namespace
+
+extern "C" int pss_batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out) {
+  return batch_create(desc, stream, out, PSS_KIND_SPACE_SAVING);
+}
+
+extern "C" int pss_frequent_batch_create(const pss_batch_desc* desc, void* stream,
+                                         pss_batch** out) {
+  return batch_create(desc, stream, out, PSS_KIND_FREQUENT);
 }
 
 extern "C" int pss_batch_plan(const pss_batch* b, uint32_t* p) {
@@ -495,7 +531,7 @@ extern "C" int pss_batch_export(pss_batch* b, uint32_t index, pss_entry* host_ou
   cudaStream_t s = (cudaStream_t)stream;
   const StreamPlan& sp = b->s[index];
   void* root = b->arena + sp.level_off.back();
-  const uint32_t k = sp.k;
+  const uint32_t k = sp.cap;
   void* dmem = nullptr;
   cudaError_t e = cudaMallocAsync(&dmem, sizeof(pss_entry) * k + 16, s);
   if (e != cudaSuccess) return from_cuda(e);
@@ -521,6 +557,11 @@ extern "C" int pss_batch_export(pss_batch* b, uint32_t index, pss_entry* host_ou
   }
   cudaFreeAsync(dmem, s);
   if (rc == PSS_OK) {
+    if (b->kind == PSS_KIND_FREQUENT) {  // m receives delta, as pss_export
+      uint64_t total = 0;
+      for (uint32_t i = 0; i < hn[0]; ++i) total += host_out[i].count;
+      hm = (hc - total) / sp.k;
+    }
     *size = hn[0];
     if (m) *m = hm;
     if (n_covered) *n_covered = hc;

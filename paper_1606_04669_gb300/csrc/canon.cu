@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(BS) query_batch_kernel(const QueryDesc* __rest
   const uint32_t id = ids[blockIdx.x];
   const QueryDesc d = descs[id];
   const SetView<ItemT> root = set_view_dev<ItemT>(d.root, 1, d.k);
-  canon_node<ItemT, BS>(root, 0, d.n, d.k, 1, out + d.out_off, out_n + 2 * id, smem);
+  canon_node<ItemT, BS>(root, 0, d.n, d.kq, d.filter, out + d.out_off, out_n + 2 * id, smem);
 }
 
 }  // namespace

@@ -24,6 +24,7 @@
 // n / k decrement steps in a block of n items, so this work adds O(1) per
 // item.  The output node is sorted by item (a bitonic sort over
 // the warp's slice), the layout the combine kernel reads; err and m are 0.
+#include <algorithm>
 #include <atomic>
 
 #include "pss_internal.cuh"
@@ -324,6 +325,42 @@ __global__ void __launch_bounds__(256) frequent_block_kernel(const ItemT* __rest
                         out, node);
 }
 
+// Persistent form for many streams: each warp takes (stream, block) tasks
+// from a shared counter until the list is exhausted (the tasks of one launch
+// share kc, so every warp's slice has one layout).
+template <typename ItemT>
+__global__ void __launch_bounds__(256) frequent_batch_kernel(const BatchStream* __restrict__ streams,
+                                                             const BatchTask* __restrict__ tasks,
+                                                             uint32_t ntasks, uint32_t* counter,
+                                                             uint32_t wbytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* slice = smem + (size_t)warp * wbytes;
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1u);
+    t = __shfl_sync(FULL_MASK, t, 0);
+    if (t >= ntasks) break;
+    const BatchTask task = tasks[t];
+    const BatchStream st = streams[task.stream];
+    const SetView<ItemT> out = set_view_dev<ItemT>(st.level0, st.p, st.k);
+    const u64 left = block_bound(task.index, st.n, st.p);
+    const u64 right = block_bound((u64)task.index + 1, st.n, st.p);
+    if (right - left >= (1ull << 32)) {
+      if (lane == 0) {
+        out.size[task.index] = 0;
+        out.m[task.index] = 0;
+        out.ncov[task.index] = right - left;
+        atomicOr(out.status, (uint32_t)ST_CHUNK);
+      }
+      continue;
+    }
+    frequent_block<ItemT>((const ItemT*)st.items + left, (uint32_t)(right - left), st.k, slice,
+                          out, task.index);
+    __syncwarp();
+  }
+}
+
 // Warps per CTA with the most warps resident per SM (ties: fewer), per k.
 template <typename ItemT>
 int frequent_warps_per_cta(uint32_t kc) {
@@ -373,6 +410,44 @@ cudaError_t launch_frequent_blocks(const ItemT* items, u64 n, uint32_t p, uint32
   return cudaGetLastError();
 }
 
+template <typename ItemT>
+uint32_t frequent_batch_grid(uint32_t kc, uint32_t ntasks, int sms) {
+  if (kc == 0 || kc > PSS_MAX_K_RESIDENT) return 0;
+  const int wpc = frequent_warps_per_cta<ItemT>(kc);
+  if (wpc <= 0) return 0;
+  const void* kern = (const void*)frequent_batch_kernel<ItemT>;
+  if (ensure_kernel_attrs(kern) != cudaSuccess) return 0;
+  const size_t wb = f_layout(kc, (int)sizeof(ItemT)).bytes;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * wpc, (size_t)wpc * wb) !=
+          cudaSuccess ||
+      blocks <= 0)
+    return 0;
+  const uint64_t need = (ntasks + (uint32_t)wpc - 1) / (uint32_t)wpc;
+  return (uint32_t)std::min<uint64_t>((uint64_t)sms * (uint64_t)blocks, need ? need : 1);
+}
+
+template <typename ItemT>
+cudaError_t launch_frequent_batch(const BatchStream* streams, const BatchTask* tasks,
+                                  uint32_t ntasks, uint32_t* counter, uint32_t kc, uint32_t grid,
+                                  cudaStream_t stream) {
+  const int wpc = frequent_warps_per_cta<ItemT>(kc);
+  if (wpc <= 0) return cudaErrorInvalidConfiguration;
+  cudaError_t e = ensure_kernel_attrs((const void*)frequent_batch_kernel<ItemT>);
+  if (e != cudaSuccess) return e;
+  if (ntasks == 0 || grid == 0) return cudaSuccess;
+  const size_t wb = f_layout(kc, (int)sizeof(ItemT)).bytes;
+  frequent_batch_kernel<ItemT><<<grid, 32 * wpc, (size_t)wpc * wb, stream>>>(streams, tasks, ntasks,
+                                                                            counter, (uint32_t)wb);
+  return cudaGetLastError();
+}
+
+template uint32_t frequent_batch_grid<uint32_t>(uint32_t, uint32_t, int);
+template uint32_t frequent_batch_grid<u64>(uint32_t, uint32_t, int);
+template cudaError_t launch_frequent_batch<uint32_t>(const BatchStream*, const BatchTask*, uint32_t,
+                                                     uint32_t*, uint32_t, uint32_t, cudaStream_t);
+template cudaError_t launch_frequent_batch<u64>(const BatchStream*, const BatchTask*, uint32_t,
+                                                uint32_t*, uint32_t, uint32_t, cudaStream_t);
 template cudaError_t launch_frequent_blocks<uint32_t>(const uint32_t*, u64, uint32_t, uint32_t,
                                                       uint32_t, SetView<uint32_t>, uint32_t,
                                                       cudaStream_t);

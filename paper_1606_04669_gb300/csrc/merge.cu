@@ -282,8 +282,9 @@ __global__ void __launch_bounds__(BS) merge_pair_kernel(SetView<ItemT> a, uint32
   merge_nodes<ItemT, BS, BIG, MG>(a, ia, b, ib, out, 0, smem, gscratch);
 }
 
-// Batch form: task (d, j) builds node j of the next level of descriptor d.
-template <typename ItemT, int BS>
+// Batch form: task (d, j) builds node j of the next level of descriptor d
+// (MG: the Frequent merge).
+template <typename ItemT, int BS, bool MG>
 __global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __restrict__ descs,
                                                          const BatchTask* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __rest
     copy_node<ItemT, BS>(in, 2 * j, out, j);
     return;
   }
-  merge_nodes<ItemT, BS, false>(in, 2 * j, in, 2 * j + 1, out, j, smem, nullptr);
+  merge_nodes<ItemT, BS, false, MG>(in, 2 * j, in, 2 * j + 1, out, j, smem, nullptr);
 }
 
 template <typename ItemT, int BS>
@@ -395,10 +396,10 @@ cudaError_t launch_copy_node(SetView<ItemT> in, uint32_t node, SetView<ItemT> ou
 
 template <typename ItemT>
 cudaError_t launch_merge_tasks(const MergeDesc* descs, const BatchTask* tasks, uint32_t ntasks,
-                               uint32_t k, cudaStream_t stream) {
+                               uint32_t k, cudaStream_t stream, bool mg) {
   if (k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;  // the batch keeps k in shared memory
   const size_t smem = merge_smem_bytes<ItemT>(k);
-  auto kern = merge_tasks_kernel<ItemT, MERGE_BS>;
+  auto kern = mg ? merge_tasks_kernel<ItemT, MERGE_BS, true> : merge_tasks_kernel<ItemT, MERGE_BS, false>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   if (ntasks == 0) return cudaSuccess;
@@ -407,9 +408,9 @@ cudaError_t launch_merge_tasks(const MergeDesc* descs, const BatchTask* tasks, u
 }
 
 template cudaError_t launch_merge_tasks<uint32_t>(const MergeDesc*, const BatchTask*, uint32_t,
-                                                  uint32_t, cudaStream_t);
+                                                  uint32_t, cudaStream_t, bool);
 template cudaError_t launch_merge_tasks<u64>(const MergeDesc*, const BatchTask*, uint32_t, uint32_t,
-                                             cudaStream_t);
+                                             cudaStream_t, bool);
 template size_t merge_smem_bytes<uint32_t>(uint32_t);
 template size_t merge_smem_bytes<u64>(uint32_t);
 template cudaError_t launch_merge_level<uint32_t>(SetView<uint32_t>, SetView<uint32_t>, cudaStream_t,

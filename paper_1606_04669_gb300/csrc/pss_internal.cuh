@@ -115,11 +115,15 @@ struct MergeDesc {
   uint32_t in_nodes, k;
 };
 
-// One stream's query in a batch: Pruned(root, n, kq) written at out_off.
+// One stream's query in a batch: Pruned(root, n, kq) written at out_off;
+// k is the root's capacity, filter the query of launch_canon (1: Space
+// Saving candidates, 3: Frequent candidates).
 struct QueryDesc {
   void* root;
   u64 n;
   uint32_t k, out_off;
+  uint32_t kq;
+  int32_t filter;
 };
 
 // floor(r * n / p) without overflow (r <= p, p < 2^32): 128-bit product,

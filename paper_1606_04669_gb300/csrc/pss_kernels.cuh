@@ -150,10 +150,22 @@ int summarize_warp_ctas_per_sm(uint32_t k);
 template <typename ItemT>
 int summarize_ctas_per_sm(uint32_t k);
 
-// One CTA per task: node task.index of the next level of descriptor task.stream.
+// One CTA per task: node task.index of the next level of descriptor task.stream
+// (mg: the Frequent merge).
 template <typename ItemT>
 cudaError_t launch_merge_tasks(const MergeDesc* descs, const BatchTask* tasks, uint32_t ntasks,
-                               uint32_t k, cudaStream_t stream);
+                               uint32_t k, cudaStream_t stream, bool mg = false);
+
+// Persistent Frequent block summaries over a task list (frequent.cu): each
+// warp takes (stream, block) tasks from *counter; streams[i].k is the
+// capacity k - 1.  frequent_batch_grid gives the CTAs for ntasks tasks (0 if
+// it cannot run).
+template <typename ItemT>
+cudaError_t launch_frequent_batch(const BatchStream* streams, const BatchTask* tasks,
+                                  uint32_t ntasks, uint32_t* counter, uint32_t kc, uint32_t grid,
+                                  cudaStream_t stream);
+template <typename ItemT>
+uint32_t frequent_batch_grid(uint32_t kc, uint32_t ntasks, int sms);
 
 // One CTA per id: the query of descs[ids[i]].
 template <typename ItemT>

@@ -125,6 +125,8 @@ SIGNATURES = {
     "pss_free": (None, [vp]),
     "pss_plan_blocks": (ctypes.c_uint32, [u64, u32, ctypes.c_int, ctypes.c_double]),
     "pss_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp, ctypes.POINTER(vp)]),
+    "pss_frequent_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp,
+                                                 ctypes.POINTER(vp)]),
     "pss_batch_plan": (ctypes.c_int, [vp, u32p]),
     "pss_batch_info": (ctypes.c_int, [vp, u32p, u64p, u64p, u32p]),
     "pss_batch_run": (ctypes.c_int, [vp, ctypes.c_int, vp]),
@@ -509,9 +511,10 @@ class Batch:
     """Many independent streams summarized in one launch graph (pss_batch_*).
 
     items: CUDA tensors of one item width (borrowed for the batch's life);
-    ks: counters per stream; ps: blocks per stream (None / 0 = planned)."""
+    ks: counters per stream; ps: blocks per stream (None / 0 = planned);
+    frequent: Frequent (Misra–Gries) summaries instead of Space Saving."""
 
-    def __init__(self, items, ks, ps=None, skews=None, stream=None):
+    def __init__(self, items, ks, ps=None, skews=None, stream=None, frequent: bool = False):
         if not items:
             raise ValueError("a batch needs at least one stream")
         widths = {_check_items(t) for t in items}
@@ -527,9 +530,11 @@ class Batch:
         self._skew = (ctypes.c_double * ns)(*[float(x or 0.0) for x in (skews or [0.0] * ns)])
         d = BatchDesc(ns, self.item_bytes, self._ptrs, self._n, self._k, self._p, self._skew)
         h = vp()
-        _check(load().pss_batch_create(ctypes.byref(d), vp(_stream_handle(stream)), ctypes.byref(h)),
-               "pss_batch_create")
+        create = "pss_frequent_batch_create" if frequent else "pss_batch_create"
+        _check(getattr(load(), create)(ctypes.byref(d), vp(_stream_handle(stream)), ctypes.byref(h)),
+               create)
         self._h = h
+        self.kind = KIND_FREQUENT if frequent else KIND_SPACE_SAVING
         self.nstreams = ns
         self.ks = [int(k) for k in ks]
 

@@ -164,3 +164,34 @@ def test_full_size_sampled_blocks_and_bounds():
     frequent_items = set(np.nonzero(f[:-1] * k > n)[0].tolist())
     assert frequent_items <= set(root.query(n, k).item.tolist())
     tree.close()
+
+
+@pytest.mark.parametrize("width", [8, 4])
+def test_frequent_batch_equals_plain_and_oracle(width):
+    # pss_frequent_batch_create: every stream's query and root equal the plain
+    # Frequent path with the batch's block count, and the oracle's
+    rng = np.random.default_rng(40 + width)
+    lens = [0, 7, 999, 50_000, 123_457, 300_000, 700_001]
+    ks = [2, 64, 256, 1024, 4096, 300, 3]
+    specs = [dict(n=lens[i % len(lens)], k=ks[(3 * i) % len(ks)], s=float(0.8 + 1.2 * rng.random()),
+                  stream=i) for i in range(18)]
+    items = [P.gen_zipf(sp["n"], seed=7, s=sp["s"], log2u=32, item_bytes=width,
+                        stream_id=sp["stream"]) for sp in specs]
+    batch = P.Batch(items, [sp["k"] for sp in specs], frequent=True)
+    assert batch.kind == P.KIND_FREQUENT
+    plan = batch.plan()
+    for use_graph in (False, True, True):
+        batch.run(use_graph=use_graph)
+        res = batch.results()
+        for i, sp in enumerate(specs):
+            n, k = sp["n"], sp["k"]
+            plain = P.frequent(items[i], k, plan[i])
+            assert ents(res[i]) == ents(plain.query(n, k)), i
+            e, pe = batch.export(i), plain.export()
+            assert ents(e) == ents(pe) and (e.m, e.n_covered) == (pe.m, pe.n_covered), i
+            if use_graph is False and n <= 300_000:
+                x = oracle.gen_zipf(n, seed=7, s=sp["s"], log2u=32, width=width, stream=sp["stream"])
+                root, cand = oracle.parallel_frequent(x, k, plan[i])
+                assert ents(e) == ents(root) and e.m == oracle.frequent_delta(root, k), i
+                assert ents(res[i]) == ents(cand), i
+    batch.close()
