@@ -346,7 +346,8 @@ def run_sweep(args):
 def run_batched(args):
     """1024 independent u64 streams (log-uniform lengths in [1e4, 1e8], Zipf s
     in [0.8, 2] over [0, 2^32), k in {64, 256, 1024, 4096}, seed 3) in one
-    graph launch, against the plain path looped over the same streams."""
+    graph launch, against the plain path looped over the same streams
+    (--kind frequent: the Frequent summary, batched and plain)."""
     import torch
 
     import paper_1606_04669_gb300 as P
@@ -362,7 +363,9 @@ def run_batched(args):
     ks = [sp.k for sp in specs]
     ps = [autotune.plan_blocks(sp.n, sp.k, sp.s) for sp in specs]
     total = sum(sp.n for sp in specs)
-    batch = P.Batch(items, ks, ps=ps, skews=[sp.s for sp in specs])
+    frequent = args.kind == "frequent"
+    batch = P.Batch(items, ks, ps=ps, skews=[sp.s for sp in specs], frequent=frequent)
+    summarize = P.frequent if frequent else P.summarize
     for _ in range(max(args.warmup, 1)):
         batch.run(use_graph=True)
     torch.cuda.synchronize()
@@ -381,7 +384,7 @@ def run_batched(args):
     def plain():
         out = []
         for i, sp in enumerate(specs):
-            sm = P.summarize(items[i], ks[i], ps[i], stream=stream)
+            sm = summarize(items[i], ks[i], ps[i], stream=stream)
             out.append(sm.query(sp.n, ks[i], stream=stream))
             sm.close()
         return out
@@ -397,7 +400,8 @@ def run_batched(args):
                and a.err.tolist() == b.err.tolist() for a, b in zip(res, pres))
     hbm, _ = peaks()
     line = {
-        "metric": METRIC, "workload": "batched", "value": total / (ms_batched / 1e3),
+        "metric": METRIC, "workload": "batched", "summary": args.kind,
+        "value": total / (ms_batched / 1e3),
         "unit": "items/s", "ms_per_step": ms_batched, "steps": args.steps, "warmup": args.warmup,
         "input_gbs": total * 8 / (ms_batched / 1e3) / 1e9,
         "hbm_frac": total * 8 / (ms_batched / 1e3) / 1e9 / hbm,
@@ -644,6 +648,8 @@ def main():
     ap.add_argument("--nstreams", type=int, default=1024)
     ap.add_argument("--points", default="",
                     help="sweep points to run, e.g. 0.5:500,1.1:2000; frequent: k values, e.g. 2000,64")
+    ap.add_argument("--kind", choices=("space_saving", "frequent"), default="space_saving",
+                    help="batched: the summary the streams use")
     ap.add_argument("--base", choices=sorted(WORKLOADS), default="plain",
                     help="frequent: the workload whose data, n and p it runs on")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
