@@ -203,8 +203,8 @@ void pss_tree_free(pss_tree* tree);
  * pss_export, pss_free, and pss_tree_levels / _level_nodes / _read_level /
  * _root / _free for trees.  Not available for Frequent summaries:
  * pss_accuracy_of (PSS_EINVAL), pss_import (always Space Saving), the
- * server and allocation-free forms, host input.  The batched form is
- * pss_frequent_batch_create.
+ * allocation-free form, host input.  The batched form is
+ * pss_frequent_batch_create, the served form pss_frequent_server_create.
  *
  * pss_frequent_summarize — p Misra–Gries block summaries (Algorithm 1
  * bounds) merged in the binary tree over adjacent pairs (an odd last summary
@@ -445,6 +445,14 @@ typedef struct {
 } pss_completion;
 
 int pss_server_create(const pss_server_config* config, pss_server** out);
+
+/* The served form with Frequent (Misra–Gries) summaries: segments are
+ * summarized by the Frequent batch, merged into their tenant with the
+ * Frequent merge and both are queried with the Frequent query (err = delta).
+ * Tenant summaries hold k - 1 entries; pss_server_tenant_export reports delta
+ * in m and pss_server_tenant_import ignores m.  Everything else as
+ * pss_server_create. */
+int pss_frequent_server_create(const pss_server_config* config, pss_server** out);
 
 /* Queue requests (any order; each is released at its arrival time).  May be
  * called before or after pss_server_start.  Request ids must be unique among

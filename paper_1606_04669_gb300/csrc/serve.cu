@@ -68,6 +68,8 @@ struct Result {
 
 struct pss_server {
   pss_server_config cfg{};
+  int kind = PSS_KIND_SPACE_SAVING;  // of every summary the server keeps
+  uint32_t cap = 0;                  // entries per summary: k, or k - 1 (Frequent)
   int dev = 0;
   std::mutex mu;
   std::condition_variable cv;
@@ -107,11 +109,11 @@ struct pss_server {
 
 namespace {
 
-uint64_t request_bytes(const pss_request& r, uint32_t k, uint32_t p) {
+uint64_t request_bytes(const pss_request& r, uint32_t cap, uint32_t p) {
   const uint64_t items = r.d_items ? 0 : r.n * 4;
   // block summaries and one tree level, plus the root (set_layout sizes)
-  return items + set_layout(p, k, 4).total + set_layout((p + 1) / 2, k, 4).total +
-         set_layout(1, k, 4).total;
+  return items + set_layout(p, cap, 4).total + set_layout((p + 1) / 2, cap, 4).total +
+         set_layout(1, cap, 4).total;
 }
 
 // Enqueue one tick (called by the scheduler thread without the lock held):
@@ -119,7 +121,8 @@ uint64_t request_bytes(const pss_request& r, uint32_t k, uint32_t p) {
 // launch over every block of the tick), then, in arrival order on the tenant
 // stream, merge each into its tenant and query the tenant.
 void launch_tick(pss_server* sv, Tick& t) {
-  const uint32_t k = sv->cfg.k;
+  const uint32_t k = sv->cfg.k, cap = sv->cap;
+  const bool mg = sv->kind == PSS_KIND_FREQUENT;
   cudaStream_t seg = sv->seg_stream[sv->ticks & 1];
   ++sv->ticks;
   const uint32_t nr = (uint32_t)t.reqs.size();
@@ -153,7 +156,8 @@ void launch_tick(pss_server* sv, Tick& t) {
   int rc = PSS_OK;
   if (nb) {
     pss_batch_desc desc{nb, 4, items.data(), ns.data(), ks.data(), ps.data(), nullptr};
-    rc = pss_batch_create(&desc, sv->plan_stream, &t.batch);
+    rc = mg ? pss_frequent_batch_create(&desc, sv->plan_stream, &t.batch)
+            : pss_batch_create(&desc, sv->plan_stream, &t.batch);
     if (rc == PSS_OK) rc = pss_batch_run(t.batch, 0, seg);
   }
   if (rc != PSS_OK) {
@@ -174,9 +178,9 @@ void launch_tick(pss_server* sv, Tick& t) {
     void* in = sv->tenant_mem[cur][T];
     void* out = sv->tenant_mem[cur ^ 1][T];
     void* root = batch_root(t.batch, bidx[i]);
-    cudaError_t e = launch_merge_pair<uint32_t>(set_view<uint32_t>(in, 1, k), 0,
-                                                set_view<uint32_t>(root, 1, k), 0,
-                                                set_view<uint32_t>(out, 1, k), ts);
+    cudaError_t e = launch_merge_pair<uint32_t>(set_view<uint32_t>(in, 1, cap), 0,
+                                                set_view<uint32_t>(root, 1, cap), 0,
+                                                set_view<uint32_t>(out, 1, cap), ts, mg);
     count_launches(1);
     sv->tenant_cur[T] = cur ^ 1;
     sv->tenant_items[T] += a.r.n;
@@ -184,8 +188,8 @@ void launch_tick(pss_server* sv, Tick& t) {
     pss_entry* q = sv->d_q + (size_t)a.slot * 2 * k;
     uint32_t* qn = sv->d_qn + (size_t)a.slot * 4;
     if (e == cudaSuccess)
-      e = launch_canon<uint32_t>(set_view<uint32_t>(out, 1, k), 0, a.tenant_items, k, 1, q + k,
-                                 qn + 2, ts);
+      e = launch_canon<uint32_t>(set_view<uint32_t>(out, 1, cap), 0, a.tenant_items, k,
+                                 mg ? 3 : 1, q + k, qn + 2, ts);
     count_launches(1);
     pss_entry* sq;
     uint32_t* sqn;
@@ -271,7 +275,7 @@ void scheduler(pss_server* sv) {
       while (!sv->ready.empty() && tick.reqs.size() < sv->cfg.max_batch && !sv->free_slots.empty()) {
         const pss_request& r = sv->ready.front();
         const uint32_t p = r.p ? r.p : pss_plan_blocks(r.n, k, 4, r.s);
-        const uint64_t bytes = request_bytes(r, k, p);
+        const uint64_t bytes = request_bytes(r, sv->cap, p);
         // admit while the budget allows; a request larger than the whole
         // budget runs alone
         if (sv->inflight_bytes + bytes > sv->cfg.budget_bytes &&
@@ -345,7 +349,9 @@ void destroy(pss_server* sv) {
 
 }  // namespace
 
-extern "C" int pss_server_create(const pss_server_config* cfg, pss_server** out) {
+namespace {
+
+int server_create(const pss_server_config* cfg, pss_server** out, int kind) {
   if (!cfg || !out) return PSS_EINVAL;
   *out = nullptr;
   if (cfg->tenants == 0 || cfg->k < 2 || cfg->k > PSS_MAX_K_RESIDENT || cfg->max_batch == 0 ||
@@ -354,9 +360,11 @@ extern "C" int pss_server_create(const pss_server_config* cfg, pss_server** out)
   pss_server* sv = new (std::nothrow) pss_server;
   if (!sv) return PSS_ENOMEM;
   sv->cfg = *cfg;
+  sv->kind = kind;
+  sv->cap = kind == PSS_KIND_FREQUENT ? cfg->k - 1 : cfg->k;
   cudaError_t e = cudaGetDevice(&sv->dev);
   const uint32_t k = cfg->k, T = cfg->tenants;
-  const SetLayout L = set_layout(1, k, 4);
+  const SetLayout L = set_layout(1, sv->cap, 4);
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
     sv->tenant_mem[b].assign(T, nullptr);
     for (uint32_t t = 0; t < T && e == cudaSuccess; ++t) {
@@ -382,6 +390,16 @@ extern "C" int pss_server_create(const pss_server_config* cfg, pss_server** out)
   }
   *out = sv;
   return PSS_OK;
+}
+
+}  // namespace
+
+extern "C" int pss_server_create(const pss_server_config* cfg, pss_server** out) {
+  return server_create(cfg, out, PSS_KIND_SPACE_SAVING);
+}
+
+extern "C" int pss_frequent_server_create(const pss_server_config* cfg, pss_server** out) {
+  return server_create(cfg, out, PSS_KIND_FREQUENT);
 }
 
 extern "C" int pss_server_submit(pss_server* sv, const pss_request* reqs, uint32_t count) {
@@ -464,7 +482,9 @@ extern "C" int pss_server_tenant_import(pss_server* sv, uint32_t tenant, const p
                                         uint32_t size, uint64_t m, uint64_t n_covered) {
   if (!sv || tenant >= sv->cfg.tenants) return PSS_EINVAL;
   std::vector<char> image;
-  int rc = summary_image(entries, size, m, n_covered, sv->cfg.k, 4, image);
+  // a Frequent summary stores minimum 0 (export reports delta in m instead)
+  const bool mg = sv->kind == PSS_KIND_FREQUENT;
+  int rc = summary_image(entries, size, mg ? 0 : m, n_covered, sv->cap, 4, image);
   if (rc) return rc;
   std::lock_guard<std::mutex> lock(sv->mu);
   if (sv->started) return PSS_EINVAL;
@@ -484,7 +504,7 @@ extern "C" int pss_server_tenant_export(pss_server* sv, uint32_t tenant, pss_ent
     std::lock_guard<std::mutex> lock(sv->mu);
     mem = sv->tenant_mem[sv->tenant_cur[tenant]][tenant];
   }
-  const uint32_t k = sv->cfg.k;
+  const uint32_t k = sv->cap;
   pss_entry* d_out = nullptr;
   cudaError_t e = cudaMalloc(&d_out, sizeof(pss_entry) * k + 16);
   if (e != cudaSuccess) return from_cuda(e);
@@ -501,9 +521,16 @@ extern "C" int pss_server_tenant_export(pss_server* sv, uint32_t tenant, pss_ent
   int rc = from_cuda(e);
   if (rc == PSS_OK && hn[1]) rc = PSS_EDEVICE;
   if (rc == PSS_OK && hn[0] > cap) rc = PSS_ERANGE;
-  if (rc == PSS_OK && hn[0] && host_out)
-    rc = from_cuda(cudaMemcpy(host_out, d_out, sizeof(pss_entry) * hn[0], cudaMemcpyDeviceToHost));
+  std::vector<pss_entry> ents(hn[0]);
+  if (rc == PSS_OK && hn[0])
+    rc = from_cuda(cudaMemcpy(ents.data(), d_out, sizeof(pss_entry) * hn[0], cudaMemcpyDeviceToHost));
+  if (rc == PSS_OK && hn[0] && host_out) memcpy(host_out, ents.data(), sizeof(pss_entry) * hn[0]);
   cudaFree(d_out);
+  if (rc == PSS_OK && sv->kind == PSS_KIND_FREQUENT) {  // m receives delta, as pss_export
+    uint64_t total = 0;
+    for (const pss_entry& en : ents) total += en.count;
+    hm = (hc - total) / sv->cfg.k;
+  }
   if (rc == PSS_OK) {
     *size = hn[0];
     if (m) *m = hm;

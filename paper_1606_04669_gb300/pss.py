@@ -134,6 +134,8 @@ SIGNATURES = {
     "pss_batch_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p, u64p, vp]),
     "pss_batch_free": (None, [vp]),
     "pss_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+    "pss_frequent_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig),
+                                                  ctypes.POINTER(vp)]),
     "pss_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(Request), u32]),
     "pss_server_start": (ctypes.c_int, [vp]),
     "pss_server_wait": (ctypes.c_int, [vp, ctypes.c_double]),
@@ -589,14 +591,17 @@ class Batch:
 
 class Server:
     """Request loop with continuous batching over resident tenant summaries
-    (pss_server_*).  Requests carry scheduled arrival times (open loop)."""
+    (pss_server_*).  Requests carry scheduled arrival times (open loop).
+    frequent: Frequent (Misra–Gries) summaries instead of Space Saving."""
 
     def __init__(self, tenants: int, k: int, budget_bytes: int = 16 << 30, max_batch: int = 256,
-                 max_inflight: int = 2048):
+                 max_inflight: int = 2048, frequent: bool = False):
         cfg = ServerConfig(int(tenants), int(k), int(budget_bytes), int(max_batch), int(max_inflight))
         h = vp()
-        _check(load().pss_server_create(ctypes.byref(cfg), ctypes.byref(h)), "pss_server_create")
+        create = "pss_frequent_server_create" if frequent else "pss_server_create"
+        _check(getattr(load(), create)(ctypes.byref(cfg), ctypes.byref(h)), create)
         self._h = h
+        self.kind = KIND_FREQUENT if frequent else KIND_SPACE_SAVING
         self.k = int(k)
         self.tenants = int(tenants)
         self._keep = []  # device buffers of caller-provided segments

@@ -146,3 +146,37 @@ def test_served_injected_allocation_failures():
         assert ents(res[r["id"]][1]) == ents(res2[r["id"]][1]), r["id"]
     for t in range(tenants):
         assert ents(final[t]) == ents(final2[t])
+
+
+def test_frequent_server_matches_oracle():
+    # pss_frequent_server_create: segments summarized by the Frequent batch,
+    # merged into their tenant with the Frequent merge in arrival order
+    tenants, k = 5, 48
+    reqs = make_requests(120, tenants, seed=12)
+    srv = P.Server(tenants, k, budget_bytes=64 << 20, max_batch=10, frequent=True)
+    assert srv.kind == P.KIND_FREQUENT
+    srv.submit(reqs)
+    srv.start()
+    srv.wait(300)
+    comps = {c["id"]: c for c in srv.poll()}
+    res = {r["id"]: srv.result(r["id"]) for r in reqs}
+    final = {t: srv.tenant_export(t) for t in range(tenants)}
+    srv.close()
+    empty = np.zeros(0, np.uint64)
+    tenant = {t: oracle.Summary(empty, empty, empty, 0, 0) for t in range(tenants)}
+    for r in sorted(reqs, key=lambda r: r["arrival"]):
+        x = oracle.gen_zipf(r["n"], seed=r["seed"], s=r["s"], log2u=r["log2u"], stream=r["stream_id"])
+        p = P.plan_blocks(r["n"], k, 4, r["s"])
+        seg, segq = oracle.parallel_frequent(x, k, p)
+        tenant[r["tenant"]] = oracle.frequent_combine(tenant[r["tenant"]], seg, k)
+        tn = tenant[r["tenant"]]
+        tq = oracle.frequent_query(tn, tn.n_covered, k)
+        c = comps[r["id"]]
+        assert c["status"] == 0 and c["tenant_items"] == tn.n_covered
+        got_seg, got_ten = res[r["id"]]
+        assert ents(got_seg) == ents(segq), r["id"]
+        assert ents(got_ten) == ents(tq), r["id"]
+    for t in range(tenants):
+        assert ents(final[t]) == ents(tenant[t])
+        assert (final[t].m, final[t].n_covered) == (oracle.frequent_delta(tenant[t], k),
+                                                    tenant[t].n_covered)
