@@ -423,7 +423,8 @@ def run_served(args):
     (seed 4): segments of log-uniform length in [1e4, 1e7] uint32 items, Zipf
     s in [1, 2] over [0, 2^24), generated on the device at admission, for 256
     tenants whose k = 1024 summaries stay resident; 16 GB admission budget.
-    Latency = completion - scheduled arrival (no coordinated omission)."""
+    Latency = completion - scheduled arrival (no coordinated omission).
+    --kind frequent: Frequent (Misra-Gries) tenant summaries."""
     import numpy as np
     import torch
 
@@ -444,9 +445,11 @@ def run_served(args):
     torch.cuda.synchronize()
     gen_rate = (1 << 28) / (g0.elapsed_time(g1) / 1e3)
     del g
-    srv = P.Server(tenants, k, budget_bytes=16 << 30, max_batch=256, max_inflight=4096)
+    frequent = args.kind == "frequent"
+    srv = P.Server(tenants, k, budget_bytes=16 << 30, max_batch=256, max_inflight=4096,
+                   frequent=frequent)
     # warm the kernels and the allocator pool outside the measured run
-    warm = P.Server(tenants, k, budget_bytes=16 << 30)
+    warm = P.Server(tenants, k, budget_bytes=16 << 30, frequent=frequent)
     warm.submit([dict(id=i, arrival=0.0, tenant=i, n=100_000, s=1.5, log2u=24, seed=99,
                       stream_id=i) for i in range(8)])
     warm.start()
@@ -469,7 +472,8 @@ def run_served(args):
     t_end = max(c["completed"] for c in comps)
     bad = sum(1 for c in comps if c["status"] != 0)
     line = {
-        "metric": METRIC, "workload": "served", "value": total / t_end, "unit": "items/s",
+        "metric": METRIC, "workload": "served", "summary": args.kind,
+        "value": total / t_end, "unit": "items/s",
         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
                        "p99": float(np.percentile(lat, 99) * 1e3),
                        "max": float(lat.max() * 1e3),
@@ -649,7 +653,7 @@ def main():
     ap.add_argument("--points", default="",
                     help="sweep points to run, e.g. 0.5:500,1.1:2000; frequent: k values, e.g. 2000,64")
     ap.add_argument("--kind", choices=("space_saving", "frequent"), default="space_saving",
-                    help="batched: the summary the streams use")
+                    help="batched / served: the summary the streams or tenants use")
     ap.add_argument("--base", choices=sorted(WORKLOADS), default="plain",
                     help="frequent: the workload whose data, n and p it runs on")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
