@@ -361,9 +361,9 @@ def run_batched(args):
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t
     ks = [sp.k for sp in specs]
-    ps = [autotune.plan_blocks(sp.n, sp.k, sp.s) for sp in specs]
-    total = sum(sp.n for sp in specs)
     frequent = args.kind == "frequent"
+    ps = [autotune.plan_blocks(sp.n, sp.k, sp.s, frequent=frequent) for sp in specs]
+    total = sum(sp.n for sp in specs)
     batch = P.Batch(items, ks, ps=ps, skews=[sp.s for sp in specs], frequent=frequent)
     summarize = P.frequent if frequent else P.summarize
     for _ in range(max(args.warmup, 1)):

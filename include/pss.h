@@ -253,6 +253,11 @@ typedef struct {
  * skew_hint <= 0 means unknown and takes 1.4). */
 uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint);
 
+/* The planner of the Frequent batch and server (same classes; its own
+ * measured block lengths: 2^15 for k <= 256, 2^14 at k <= 1024 (2^15 at skew
+ * class 2.0), 2^16 above). */
+uint32_t pss_frequent_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint);
+
 /* Plan and allocate a batch (device memory for every stream's tree, task
  * lists, results).  The streams' item buffers are borrowed for the batch's
  * lifetime.  Synchronizes stream. */

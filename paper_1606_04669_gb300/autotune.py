@@ -30,6 +30,7 @@ import time
 K_CLASSES = (64, 256, 1024, 4096)
 SKEW_CLASSES = (0.8, 1.4, 2.0)
 LENGTHS = (1 << 15, 1 << 16, 1 << 17, 1 << 18, 1 << 19)
+FREQUENT_LENGTHS = (1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)
 
 # Measured by sweep() on a GB300 (one stream of 2^27 u64 items per point,
 # through the batch path): the block length with the highest items/s for each
@@ -44,29 +45,40 @@ TABLE = {
 }
 
 
+# The same measurement for the Frequent batch (sweep(frequent=True), lengths
+# 2^12 .. 2^16): one warp per block favours shorter blocks.
+FREQUENT_TABLE = {
+    64: {0.8: 1 << 15, 1.4: 1 << 15, 2.0: 1 << 15},
+    256: {0.8: 1 << 15, 1.4: 1 << 15, 2.0: 1 << 15},
+    1024: {0.8: 1 << 14, 1.4: 1 << 14, 2.0: 1 << 15},
+    4096: {0.8: 1 << 16, 1.4: 1 << 16, 2.0: 1 << 16},
+}
+
+
 def _nearest(v, options):
     return min(options, key=lambda o: (abs(o - v), o))
 
 
-def block_length(k: int, skew: float) -> int:
+def block_length(k: int, skew: float, frequent: bool = False) -> int:
     kc = min((c for c in K_CLASSES if c >= k), default=K_CLASSES[-1])
-    return TABLE[kc][_nearest(skew, SKEW_CLASSES)]
+    return (FREQUENT_TABLE if frequent else TABLE)[kc][_nearest(skew, SKEW_CLASSES)]
 
 
-def plan_blocks(n: int, k: int, skew: float = 1.0) -> int:
-    """Blocks for a stream of n items with k counters and Zipf skew `skew`."""
-    length = block_length(k, skew)
+def plan_blocks(n: int, k: int, skew: float = 1.0, frequent: bool = False) -> int:
+    """Blocks for a stream of n items with k counters and Zipf skew `skew`
+    (frequent: the Frequent summary's table)."""
+    length = block_length(k, skew, frequent)
     p = max(1, (n + length - 1) // length)
     while (n + p - 1) // p >= 1 << 32:
         p += 1
     return p
 
 
-def _time_batch(P, torch, x, k, p, skew, steps):
+def _time_batch(P, torch, x, k, p, skew, steps, frequent=False):
     """ms per run of one stream through the batch path (the kernel the batch
-    picks for k and the skew hint)."""
+    picks for k and the skew hint; frequent: the Frequent summary)."""
     stream = torch.cuda.current_stream()
-    b = P.Batch([x], [k], ps=[p], skews=[skew])
+    b = P.Batch([x], [k], ps=[p], skews=[skew], frequent=frequent)
     b.run(use_graph=False)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -80,23 +92,26 @@ def _time_batch(P, torch, x, k, p, skew, steps):
     return e0.elapsed_time(e1) / steps
 
 
-def sweep(n: int = 1 << 27, item_bytes: int = 8, steps: int = 3, seed: int = 77):
+def sweep(n: int = 1 << 27, item_bytes: int = 8, steps: int = 3, seed: int = 77,
+          frequent: bool = False, lengths=None):
     """Items/s of the batch path for one stream of n items (about the largest
     stream of the batched workload) for every (k, skew, block length), so
     that the length trades per-block fixed work against the number of blocks
-    in flight; returns (results, table).  Runs on the current CUDA device."""
+    in flight; returns (results, table).  frequent: the Frequent summary
+    (lengths FREQUENT_LENGTHS).  Runs on the current CUDA device."""
     import torch
 
     import paper_1606_04669_gb300 as P
+    lengths = lengths or (FREQUENT_LENGTHS if frequent else LENGTHS)
     results, table = [], {}
     for zs in SKEW_CLASSES:
         x = P.gen_zipf(n, seed=seed, s=zs, log2u=32, item_bytes=item_bytes)
         for k in K_CLASSES:
             table.setdefault(k, {})
             best = None
-            for length in LENGTHS:
+            for length in lengths:
                 p = (n + length - 1) // length
-                ms = _time_batch(P, torch, x, k, p, zs, steps)
+                ms = _time_batch(P, torch, x, k, p, zs, steps, frequent)
                 rate = n / (ms / 1e3)
                 results.append({"k": k, "skew": zs, "block_length": length, "p": p, "ms": ms,
                                 "items_per_s": rate})

@@ -107,19 +107,16 @@ struct pss_batch {
   cudaGraphExec_t exec = nullptr;
 };
 
-extern "C" uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint) {
-  (void)item_bytes;
-  // Block length per (k class, skew class), measured on a GB300 by the
-  // project's autotuner (one 2^27-item stream per class through the batch
-  // path; paper_1606_04669_gb300/autotune.py holds the same table): short
-  // blocks for small k (more blocks in flight), 2^17 at k = 4096.  An unknown
-  // skew (hint <= 0) takes the middle class.
+namespace {
+
+// Blocks for n items with block length 2^len_log2[k class][skew class]; an
+// unknown skew (hint <= 0) takes the middle class.
+uint32_t plan_from(const uint32_t (*len_log2)[3], uint64_t n, uint32_t k, double skew_hint) {
   const double sk = skew_hint > 0.0 ? skew_hint : 1.4;
   static const double classes[3] = {0.8, 1.4, 2.0};
   int sc = 0;  // the nearest class, ties to the lower one
   for (int c = 1; c < 3; ++c)
     if (std::fabs(sk - classes[c]) < std::fabs(sk - classes[sc])) sc = c;
-  static const uint32_t len_log2[4][3] = {{15, 15, 15}, {15, 15, 15}, {15, 16, 16}, {17, 17, 17}};
   const int kc = k <= 64 ? 0 : (k <= 256 ? 1 : (k <= 1024 ? 2 : 3));
   const uint64_t len = 1ull << len_log2[kc][sc];
   uint64_t p = (n + len - 1) / len;
@@ -127,6 +124,28 @@ extern "C" uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, doub
   while ((n + p - 1) / p >= (1ull << 32)) ++p;
   if (p > 0x7FFFFFFFull) p = 0x7FFFFFFFull;
   return (uint32_t)p;
+}
+
+}  // namespace
+
+extern "C" uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint) {
+  (void)item_bytes;
+  // Block length per (k class, skew class), measured on a GB300 by the
+  // project's autotuner (one 2^27-item stream per class through the batch
+  // path; paper_1606_04669_gb300/autotune.py holds the same table): short
+  // blocks for small k (more blocks in flight), 2^17 at k = 4096.
+  static const uint32_t len_log2[4][3] = {{15, 15, 15}, {15, 15, 15}, {15, 16, 16}, {17, 17, 17}};
+  return plan_from(len_log2, n, k, skew_hint);
+}
+
+extern "C" uint32_t pss_frequent_plan_blocks(uint64_t n, uint32_t k, int item_bytes,
+                                             double skew_hint) {
+  (void)item_bytes;
+  // The same measurement for the Frequent batch (autotune.FREQUENT_TABLE):
+  // one warp per block favours shorter blocks than the CTA kernel, 2^14 at
+  // k = 1024 and 2^16 at k = 4096.
+  static const uint32_t len_log2[4][3] = {{15, 15, 15}, {15, 15, 15}, {14, 14, 15}, {16, 16, 16}};
+  return plan_from(len_log2, n, k, skew_hint);
 }
 
 namespace {
@@ -262,7 +281,9 @@ int batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out, int 
     sp.n = desc->n[i];
     sp.k = desc->k[i];
     const double skew = desc->skew_hint ? desc->skew_hint[i] : 0.0;
-    sp.p = (desc->p && desc->p[i]) ? desc->p[i] : pss_plan_blocks(sp.n, sp.k, w, skew);
+    sp.p = (desc->p && desc->p[i]) ? desc->p[i]
+                                   : (mg ? pss_frequent_plan_blocks(sp.n, sp.k, w, skew)
+                                         : pss_plan_blocks(sp.n, sp.k, w, skew));
     sp.warp = !mg && use_warp_kernel(sp.k, skew);
     if (sp.k < 2 || sp.k > PSS_MAX_K_RESIDENT || sp.p == 0 || (sp.n > 0 && !sp.items) ||
         (sp.n + sp.p - 1) / sp.p >= (1ull << 32)) {

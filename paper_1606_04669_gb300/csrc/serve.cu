@@ -274,7 +274,9 @@ void scheduler(pss_server* sv) {
       reap(sv);
       while (!sv->ready.empty() && tick.reqs.size() < sv->cfg.max_batch && !sv->free_slots.empty()) {
         const pss_request& r = sv->ready.front();
-        const uint32_t p = r.p ? r.p : pss_plan_blocks(r.n, k, 4, r.s);
+        const uint32_t p = r.p ? r.p
+                               : (sv->kind == PSS_KIND_FREQUENT ? pss_frequent_plan_blocks(r.n, k, 4, r.s)
+                                                                : pss_plan_blocks(r.n, k, 4, r.s));
         const uint64_t bytes = request_bytes(r, sv->cap, p);
         // admit while the budget allows; a request larger than the whole
         // budget runs alone

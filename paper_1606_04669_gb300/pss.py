@@ -124,6 +124,7 @@ SIGNATURES = {
     "pss_summary_info": (ctypes.c_int, [vp, u32p, ctypes.POINTER(ctypes.c_int)]),
     "pss_free": (None, [vp]),
     "pss_plan_blocks": (ctypes.c_uint32, [u64, u32, ctypes.c_int, ctypes.c_double]),
+    "pss_frequent_plan_blocks": (ctypes.c_uint32, [u64, u32, ctypes.c_int, ctypes.c_double]),
     "pss_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp, ctypes.POINTER(vp)]),
     "pss_frequent_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchDesc), vp,
                                                  ctypes.POINTER(vp)]),
@@ -504,9 +505,12 @@ def profile_read(reset: bool = False) -> dict:
     return {name: getattr(p, name) for name, _ in Profile._fields_}
 
 
-def plan_blocks(n: int, k: int, item_bytes: int = 4, skew_hint: float = 0.0) -> int:
-    """The library's default block count for a stream (pss_plan_blocks)."""
-    return int(load().pss_plan_blocks(int(n), int(k), int(item_bytes), float(skew_hint)))
+def plan_blocks(n: int, k: int, item_bytes: int = 4, skew_hint: float = 0.0,
+                frequent: bool = False) -> int:
+    """The library's default block count for a stream (pss_plan_blocks, or
+    pss_frequent_plan_blocks for the Frequent summary)."""
+    fn = load().pss_frequent_plan_blocks if frequent else load().pss_plan_blocks
+    return int(fn(int(n), int(k), int(item_bytes), float(skew_hint)))
 
 
 class Batch:

@@ -60,3 +60,4 @@ def test_planner_matches_the_autotuned_table():
         k = rng.choice([2, 64, 65, 256, 257, 1024, 1025, 4096, 8000])
         s = rng.choice([0.5, 0.8, 1.1, 1.4, 1.7, 2.0, 2.7, rng.uniform(0.3, 3.0)])
         assert P.plan_blocks(n, k, 4, s) == A.plan_blocks(n, k, s), (n, k, s)
+        assert P.plan_blocks(n, k, 4, s, frequent=True) == A.plan_blocks(n, k, s, frequent=True)

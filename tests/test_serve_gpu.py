@@ -166,7 +166,7 @@ def test_frequent_server_matches_oracle():
     tenant = {t: oracle.Summary(empty, empty, empty, 0, 0) for t in range(tenants)}
     for r in sorted(reqs, key=lambda r: r["arrival"]):
         x = oracle.gen_zipf(r["n"], seed=r["seed"], s=r["s"], log2u=r["log2u"], stream=r["stream_id"])
-        p = P.plan_blocks(r["n"], k, 4, r["s"])
+        p = P.plan_blocks(r["n"], k, 4, r["s"], frequent=True)
         seg, segq = oracle.parallel_frequent(x, k, p)
         tenant[r["tenant"]] = oracle.frequent_combine(tenant[r["tenant"]], seg, k)
         tn = tenant[r["tenant"]]
