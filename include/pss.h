@@ -202,8 +202,8 @@ void pss_tree_free(pss_tree* tree);
  * arguments of one kind, else PSS_EMISMATCH), pss_query / pss_query_mode,
  * pss_export, pss_free, and pss_tree_levels / _level_nodes / _read_level /
  * _root / _free for trees.  Not available for Frequent summaries:
- * pss_accuracy_of (PSS_EINVAL), pss_import (always Space Saving), the
- * allocation-free form, host input.  The batched form is
+ * pss_accuracy_of (PSS_EINVAL), the allocation-free form, host input
+ * (pss_import makes a Space Saving summary; pss_frequent_import a Frequent one).  The batched form is
  * pss_frequent_batch_create, the served form pss_frequent_server_create.
  *
  * pss_frequent_summarize — p Misra–Gries block summaries (Algorithm 1
@@ -397,6 +397,12 @@ int pss_summary_info(const pss_summary* summary, uint32_t* k, int* item_bytes);
  */
 int pss_import(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered, uint32_t k,
                int item_bytes, void* stream, pss_summary** out);
+
+/* pss_import for a Frequent summary: entries[0 .. size) (the counts of
+ * pss_export's output; err is ignored), size <= k - 1, 2 <= k <=
+ * PSS_MAX_K_RESIDENT.  Its delta follows from n_covered and the counts. */
+int pss_frequent_import(const pss_entry* entries, uint32_t size, uint64_t n_covered, uint32_t k,
+                        int item_bytes, void* stream, pss_summary** out);
 
 /* Release a summary (stream-ordered on the stream that created it). */
 void pss_free(pss_summary* summary);

@@ -641,14 +641,21 @@ int pss_query(const pss_summary* summary, uint64_t n, uint32_t k, pss_entry* hos
                    cap, n_out, (cudaStream_t)stream);
 }
 
-int pss_import(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered, uint32_t k,
-               int item_bytes, void* stream, pss_summary** out) {
+namespace {
+
+int import_kind(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered,
+                uint32_t k, int item_bytes, void* stream, pss_summary** out, int kind) {
   if (!out) return PSS_EINVAL;
   *out = nullptr;
   int rc = check_k_width(k, item_bytes);
   if (rc) return rc;
+  const bool mg = kind == PSS_KIND_FREQUENT;
+  if (mg && k > PSS_MAX_K_RESIDENT) return PSS_EINVAL;
   std::vector<char> image;
-  if ((rc = pss::summary_image(entries, size, m, n_covered, k, item_bytes, image))) return rc;
+  // a Frequent summary stores minimum 0 (its export reports delta in m)
+  if ((rc = pss::summary_image(entries, size, mg ? 0 : m, n_covered, mg ? k - 1 : k, item_bytes,
+                               image)))
+    return rc;
   cudaError_t e = prepare_device();
   if (e != cudaSuccess) return from_cuda(e);
   cudaStream_t s = (cudaStream_t)stream;
@@ -662,13 +669,26 @@ int pss_import(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_c
     cudaFreeAsync(mem, s);
     return from_cuda(e);
   }
-  pss_summary* sm = new_summary(k, PSS_KIND_SPACE_SAVING, item_bytes, mem, s);
+  pss_summary* sm = new_summary(k, kind, item_bytes, mem, s);
   if (!sm) {
     cudaFreeAsync(mem, s);
     return PSS_ENOMEM;
   }
   *out = sm;
   return PSS_OK;
+}
+
+}  // namespace
+
+int pss_import(const pss_entry* entries, uint32_t size, uint64_t m, uint64_t n_covered, uint32_t k,
+               int item_bytes, void* stream, pss_summary** out) {
+  return import_kind(entries, size, m, n_covered, k, item_bytes, stream, out,
+                     PSS_KIND_SPACE_SAVING);
+}
+
+int pss_frequent_import(const pss_entry* entries, uint32_t size, uint64_t n_covered, uint32_t k,
+                        int item_bytes, void* stream, pss_summary** out) {
+  return import_kind(entries, size, 0, n_covered, k, item_bytes, stream, out, PSS_KIND_FREQUENT);
 }
 
 int pss_query_mode(const pss_summary* summary, uint64_t n, uint32_t k, int mode, pss_entry* host_out,

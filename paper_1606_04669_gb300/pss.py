@@ -145,6 +145,8 @@ SIGNATURES = {
                                          u32p]),
     "pss_import": (ctypes.c_int, [ctypes.POINTER(Entry), u32, u64, u64, u32, ctypes.c_int, vp,
                                   ctypes.POINTER(vp)]),
+    "pss_frequent_import": (ctypes.c_int, [ctypes.POINTER(Entry), u32, u64, u32, ctypes.c_int, vp,
+                                           ctypes.POINTER(vp)]),
     "pss_server_tenant_import": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u64, u64]),
     "pss_server_inject_alloc_failures": (ctypes.c_int, [vp, u32]),
     "pss_server_tenant_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p,
@@ -433,10 +435,17 @@ def _entries_from(ex: "Exported"):
     return buf, n
 
 
-def import_summary(ex: "Exported", k: int, item_bytes: int = 4, stream=None) -> Summary:
-    """pss_import: a device summary from an exported one (a checkpoint)."""
+def import_summary(ex: "Exported", k: int, item_bytes: int = 4, stream=None,
+                   frequent: bool = False) -> Summary:
+    """pss_import: a device summary from an exported one (a checkpoint);
+    frequent: pss_frequent_import (a Frequent summary's export)."""
     buf, n = _entries_from(ex)
     h = vp()
+    if frequent:
+        _check(load().pss_frequent_import(buf, n, int(ex.n_covered), int(k), int(item_bytes),
+                                          vp(_stream_handle(stream)), ctypes.byref(h)),
+               "pss_frequent_import")
+        return Summary(h.value)
     _check(load().pss_import(buf, n, int(ex.m), int(ex.n_covered), int(k), int(item_bytes),
                              vp(_stream_handle(stream)), ctypes.byref(h)), "pss_import")
     return Summary(h.value)

@@ -45,6 +45,25 @@ def test_export_import_round_trip_and_merge(k, w):
     assert ents(q) == summary_entries(rq)
 
 
+@pytest.mark.parametrize("k,w", [(64, 4), (1000, 8), (4096, 4)])
+def test_frequent_export_import_round_trip_and_merge(k, w):
+    xa = oracle.gen_zipf(200_000, seed=84, s=1.0, log2u=20, width=w)
+    xb = oracle.gen_zipf(150_000, seed=85, s=1.3, log2u=20, width=w)
+    a = P.frequent(to_dev(xa), k, 4)
+    b = P.frequent(to_dev(xb), k, 3)
+    ea = a.export()
+    ia = P.import_summary(ea, k, w, frequent=True)
+    assert ia.kind == P.KIND_FREQUENT
+    ei = ia.export()
+    assert ents(ei) == ents(ea) and (ei.m, ei.n_covered) == (ea.m, ea.n_covered)
+    assert ents(P.merge(ia, b).export()) == ents(P.merge(a, b).export())
+    ra, rq = oracle.parallel_frequent(xa, k, 4)
+    assert ents(ia.query(ea.n_covered, k)) == ents(rq)
+    with pytest.raises(P.PssError) as er:
+        P.import_summary(ea, ea.size, w, frequent=True)  # k - 1 < entries
+    assert er.value.code == P.PSS_EINVAL
+
+
 def test_import_rejects_bad_checkpoints():
     x = oracle.gen_zipf(50_000, seed=83, s=1.1, log2u=16)
     e = P.summarize(to_dev(x), 32, 2).export()
@@ -61,8 +80,8 @@ def test_import_rejects_bad_checkpoints():
     assert ents(P.import_summary(wide, 32, 8).export()) == [(1 << 40, 5, 0)]
 
 
-def run(reqs, tenants, k, start_from=None):
-    srv = P.Server(tenants, k, budget_bytes=64 << 20, max_batch=8)
+def run(reqs, tenants, k, start_from=None, frequent=False):
+    srv = P.Server(tenants, k, budget_bytes=64 << 20, max_batch=8, frequent=frequent)
     if start_from:
         for t, ex in start_from.items():
             srv.tenant_import(t, ex)
@@ -79,15 +98,16 @@ def run(reqs, tenants, k, start_from=None):
     return res, comps, final
 
 
-def test_server_resume_equals_uninterrupted_run():
+@pytest.mark.parametrize("frequent", [False, True])
+def test_server_resume_equals_uninterrupted_run(frequent):
     tenants, k = 5, 64
     reqs = sorted(make_requests(120, tenants, seed=12), key=lambda r: r["arrival"])
     first, second = reqs[:50], reqs[50:]
-    res_all, comps_all, final_all = run(reqs, tenants, k)
-    _, _, ckpt = run(first, tenants, k)
+    res_all, comps_all, final_all = run(reqs, tenants, k, frequent=frequent)
+    _, _, ckpt = run(first, tenants, k, frequent=frequent)
     shift = second[0]["arrival"]
     resumed = [dict(r, arrival=r["arrival"] - shift) for r in second]
-    res2, comps2, final2 = run(resumed, tenants, k, start_from=ckpt)
+    res2, comps2, final2 = run(resumed, tenants, k, start_from=ckpt, frequent=frequent)
     for r in second:
         assert ents(res2[r["id"]][0]) == ents(res_all[r["id"]][0]), r["id"]
         assert ents(res2[r["id"]][1]) == ents(res_all[r["id"]][1]), r["id"]
