@@ -202,8 +202,9 @@ void pss_tree_free(pss_tree* tree);
  * arguments of one kind, else PSS_EMISMATCH), pss_query / pss_query_mode,
  * pss_export, pss_free, and pss_tree_levels / _level_nodes / _read_level /
  * _root / _free for trees.  Not available for Frequent summaries:
- * pss_accuracy_of (PSS_EINVAL), the allocation-free form, host input
- * (pss_import makes a Space Saving summary; pss_frequent_import a Frequent one).  The batched form is
+ * pss_accuracy_of (PSS_EINVAL) and the allocation-free form (pss_import
+ * makes a Space Saving summary, pss_frequent_import a Frequent one;
+ * pss_frequent_summarize_host takes host input).  The batched form is
  * pss_frequent_batch_create, the served form pss_frequent_server_create.
  *
  * pss_frequent_summarize — p Misra–Gries block summaries (Algorithm 1
@@ -215,6 +216,12 @@ void pss_tree_free(pss_tree* tree);
 #define PSS_KIND_FREQUENT 1
 int pss_frequent_summarize(const void* d_items, uint64_t n, int item_bytes, uint32_t k,
                            uint32_t p, void* stream, pss_summary** out);
+
+/* pss_frequent_summarize for items in HOST memory, read in place when
+ * mapped pinned, else copied in slabs overlapped with the block summaries
+ * (as pss_summarize_host).  Asynchronous on stream. */
+int pss_frequent_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t k,
+                                uint32_t p, void* stream, pss_summary** out);
 
 /* pss_frequent_summarize keeping every level of the tree (nodes hold k - 1
  * entries: pss_tree_read_level's stride is k - 1).  Asynchronous. */

@@ -190,10 +190,11 @@ cudaError_t copy_stream(cudaStream_t* out) {
 
 // Host input: the blocks are copied in `groups` slabs on the copy stream;
 // the summarize kernel of slab g starts as soon as slab g has landed, so the
-// copy of slab g+1 overlaps it.
+// copy of slab g+1 overlaps it.  k is the node capacity; mg: Frequent
+// summaries (block kernel and merge).
 template <typename ItemT>
 int run_tree_host(const void* h_items, uint64_t n, uint32_t k, uint32_t p, cudaStream_t s,
-                  std::vector<void*>& mems, std::vector<uint32_t>& nodes) {
+                  std::vector<void*>& mems, std::vector<uint32_t>& nodes, bool mg = false) {
   const size_t w = sizeof(ItemT);
   cudaStream_t cs;
   cudaError_t e = copy_stream(&cs);
@@ -233,11 +234,12 @@ int run_tree_host(const void* h_items, uint64_t n, uint32_t k, uint32_t p, cudaS
         }
         if (r == cudaSuccess && r1 > r0) {
           count_launches(1);
-          r = launch_summarize_blocks<ItemT>((const ItemT*)dbuf, n, p, r0, r1 - r0, v0, r0, s);
+          r = mg ? launch_frequent_blocks<ItemT>((const ItemT*)dbuf, n, p, r0, r1 - r0, v0, r0, s)
+                 : launch_summarize_blocks<ItemT>((const ItemT*)dbuf, n, p, r0, r1 - r0, v0, r0, s);
         }
       }
       return r;
-    });
+    }, mg);
   }
   if (dbuf) cudaFreeAsync(dbuf, s);
   for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
@@ -267,19 +269,38 @@ int tree_common(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p, 
                 : run_tree_device<u64>(d_items, n, k, p, s, keep, mems, nodes);
 }
 
-int frequent_tree_common(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p,
-                         cudaStream_t s, bool keep, std::vector<void*>& mems,
-                         std::vector<uint32_t>& nodes) {
+int validate_frequent(const void* items, uint64_t n, int w, uint32_t k, uint32_t p) {
   if ((w != 4 && w != 8) || k < 2 || k > PSS_MAX_K_RESIDENT || p == 0) return PSS_EINVAL;
-  if (n > 0 && d_items == nullptr) return PSS_EINVAL;
+  if (n > 0 && items == nullptr) return PSS_EINVAL;
   if ((n + p - 1) / p >= (1ull << 32)) return PSS_EINVAL;
-  cudaError_t e = prepare_device();
-  if (e != cudaSuccess) return from_cuda(e);
   const size_t have = max_optin_smem();
   const size_t need_m = w == 4 ? merge_smem_bytes<uint32_t>(k - 1) : merge_smem_bytes<u64>(k - 1);
   if (frequent_warp_bytes(k - 1, w) > have || need_m > have) return PSS_EINVAL;
+  return PSS_OK;
+}
+
+int frequent_tree_common(const void* d_items, uint64_t n, int w, uint32_t k, uint32_t p,
+                         cudaStream_t s, bool keep, std::vector<void*>& mems,
+                         std::vector<uint32_t>& nodes) {
+  cudaError_t e = prepare_device();
+  if (e != cudaSuccess) return from_cuda(e);
+  int rc = validate_frequent(d_items, n, w, k, p);
+  if (rc) return rc;
   return w == 4 ? run_frequent_tree_device<uint32_t>(d_items, n, k, p, s, keep, mems, nodes)
                 : run_frequent_tree_device<u64>(d_items, n, k, p, s, keep, mems, nodes);
+}
+
+// Pinned host memory mapped into the device's address space (a coherent
+// CPU-GPU link): its device address, else nullptr (then the items are
+// staged).
+const void* mapped_host(const void* h_items, uint64_t n) {
+  if (!n || !g_host_direct.load()) return nullptr;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, h_items) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+      attr.devicePointer)
+    return attr.devicePointer;
+  cudaGetLastError();  // an unregistered pointer is not an error here
+  return nullptr;
 }
 
 // A summary object for one-node set `mem` (nullptr when out of host memory;
@@ -444,18 +465,9 @@ int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t
   if (rc) return rc;
   std::vector<void*> mems;
   std::vector<uint32_t> nodes;
-  // Pinned host memory mapped into the device's address space (a coherent
-  // CPU-GPU link): the kernels read the items in place, each block's windows
-  // copied into shared memory one window ahead as for device input.
-  const void* mapped = nullptr;
-  if (n && g_host_direct.load()) {
-    cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, h_items) == cudaSuccess &&
-        attr.type == cudaMemoryTypeHost && attr.devicePointer)
-      mapped = attr.devicePointer;
-    else
-      cudaGetLastError();  // an unregistered pointer is not an error here
-  }
+  // mapped pinned memory: the kernels read the items in place, each block's
+  // windows copied into shared memory one window ahead as for device input
+  const void* mapped = mapped_host(h_items, n);
   if (mapped)
     rc = item_bytes == 4 ? run_tree_device<uint32_t>(mapped, n, k, p, s, false, mems, nodes)
                          : run_tree_device<u64>(mapped, n, k, p, s, false, mems, nodes);
@@ -464,6 +476,34 @@ int pss_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t
                          : run_tree_host<u64>(h_items, n, k, p, s, mems, nodes);
   if (rc) return rc;
   pss_summary* sm = new_summary(k, PSS_KIND_SPACE_SAVING, item_bytes, mems.back(), s);
+  if (!sm) {
+    cudaFreeAsync(mems.back(), s);
+    return PSS_ENOMEM;
+  }
+  *out = sm;
+  return PSS_OK;
+}
+
+int pss_frequent_summarize_host(const void* h_items, uint64_t n, int item_bytes, uint32_t k,
+                                uint32_t p, void* stream, pss_summary** out) {
+  if (!out) return PSS_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prepare_device();
+  if (e != cudaSuccess) return from_cuda(e);
+  int rc = validate_frequent(h_items, n, item_bytes, k, p);
+  if (rc) return rc;
+  std::vector<void*> mems;
+  std::vector<uint32_t> nodes;
+  const void* mapped = mapped_host(h_items, n);
+  if (mapped)
+    rc = item_bytes == 4 ? run_frequent_tree_device<uint32_t>(mapped, n, k, p, s, false, mems, nodes)
+                         : run_frequent_tree_device<u64>(mapped, n, k, p, s, false, mems, nodes);
+  else
+    rc = item_bytes == 4 ? run_tree_host<uint32_t>(h_items, n, k - 1, p, s, mems, nodes, true)
+                         : run_tree_host<u64>(h_items, n, k - 1, p, s, mems, nodes, true);
+  if (rc) return rc;
+  pss_summary* sm = new_summary(k, PSS_KIND_FREQUENT, item_bytes, mems.back(), s);
   if (!sm) {
     cudaFreeAsync(mems.back(), s);
     return PSS_ENOMEM;

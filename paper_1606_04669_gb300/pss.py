@@ -108,6 +108,8 @@ SIGNATURES = {
                                               ctypes.POINTER(vp)]),
     "pss_frequent_summarize_tree": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp,
                                                    ctypes.POINTER(vp)]),
+    "pss_frequent_summarize_host": (ctypes.c_int, [vp, u64, ctypes.c_int, u32, u32, vp,
+                                                   ctypes.POINTER(vp)]),
     "pss_summary_kind": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
     "pss_tree_kind": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
     "pss_tree_levels": (ctypes.c_int, [vp, u32p]),
@@ -412,6 +414,21 @@ def frequent(items, k: int, p: int, stream=None) -> Summary:
     _check(load().pss_frequent_summarize(vp(items.data_ptr()), items.numel(), w, int(k), int(p),
                                          vp(_stream_handle(stream)), ctypes.byref(h)),
            "pss_frequent_summarize")
+    return Summary(h.value)
+
+
+def frequent_host(items, k: int, p: int, stream=None) -> Summary:
+    """pss_frequent_summarize_host: frequent() on a CPU tensor (pinned: read
+    in place or copies overlapped)."""
+    if items.is_cuda:
+        raise ValueError("frequent_host takes a CPU tensor")
+    if not items.is_contiguous():
+        raise ValueError("items must be contiguous")
+    w = _item_bytes(items)
+    h = vp()
+    _check(load().pss_frequent_summarize_host(vp(items.data_ptr()), items.numel(), w, int(k),
+                                              int(p), vp(_stream_handle(stream)), ctypes.byref(h)),
+           "pss_frequent_summarize_host")
     return Summary(h.value)
 
 

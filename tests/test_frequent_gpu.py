@@ -195,3 +195,24 @@ def test_frequent_batch_equals_plain_and_oracle(width):
                 assert ents(e) == ents(root) and e.m == oracle.frequent_delta(root, k), i
                 assert ents(res[i]) == ents(cand), i
     batch.close()
+
+
+@pytest.mark.parametrize("direct,pinned", [(True, True), (False, True), (True, False)])
+def test_frequent_host_input(direct, pinned):
+    # mapped pinned memory read in place, pinned memory staged, pageable memory staged
+    x = oracle.gen_zipf(700_001, seed=61, s=1.1, log2u=20, width=8)
+    h = torch.from_numpy(x.view(np.int64))
+    if pinned:
+        h = h.pin_memory()
+    prev = P.set_host_direct(direct)
+    try:
+        s = P.frequent_host(h, 300, 19)
+        e = s.export()
+        torch.cuda.synchronize()
+    finally:
+        P.set_host_direct(prev)
+    root, q = oracle.parallel_frequent(x, 300, 19)
+    assert s.kind == P.KIND_FREQUENT
+    assert ents(e) == ents(root)
+    assert (e.m, e.n_covered) == (oracle.frequent_delta(root, 300), root.n_covered)
+    assert ents(s.query(len(x), 300)) == ents(q)
