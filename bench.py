@@ -71,9 +71,9 @@ TRAFFIC = {"summarize_sha1": "f34a6510834efe750b50d521d53c776477dc093f",
 
 # DRAM traffic of the Frequent block kernel from one ncu capture (profiles/
 # frequent_block_kernel_wave_k2000.md: 1368 blocks of 262144 u32 items,
-# k = 2000 -> 1434.75 MB read + 3.48 MB written), valid for that source only.
-FREQ_TRAFFIC = {"frequent_sha1": "936320a285ffb8ea4737aa15e0872cdb515a8279",
-                "bytes_per_block": (1434.75e6 + 3.48e6) / 1368, "block_items": 262144, "k": 2000,
+# k = 2000 -> 1434.60 MB read + 3.76 MB written), valid for that source only.
+FREQ_TRAFFIC = {"frequent_sha1": "b2f35211bbd44917466a2c57c50e8e0958cfcd08",
+                "bytes_per_block": (1434.60e6 + 3.76e6) / 1368, "block_items": 262144, "k": 2000,
                 "w": 4}
 
 
@@ -507,8 +507,7 @@ def run_frequent(args):
     n, p, w = wl["n"], wl["p"], wl["w"]
     stream = torch.cuda.current_stream()
     x = P.gen_zipf(n, seed=wl["seed"], s=wl["s"], log2u=wl["log2u"], item_bytes=w)
-    counts = P.exact_counts(x, wl["log2u"], stream=stream).cpu().numpy().view(np.uint32)
-    counts = counts.astype(np.int64)
+    dcounts = P.exact_counts(x, wl["log2u"], stream=stream)
     torch.cuda.synchronize()
     points = [int(v) for v in args.points.split(",")] if args.points else FREQUENT_K
     for k in points:
@@ -543,17 +542,11 @@ def run_frequent(args):
         alg = n * w + p * (k - 1) * (w + 16) + p * 24
 
         # accuracy of the candidates against exact counts (outside the timed region)
-        f = counts[q.item.astype(np.int64)]
-        true_frequent = int((counts[:-1] * k > n).sum())
-        tp = int((f * k > n).sum())
-        rep = int(q.size)
-        accuracy = {"reported": rep, "true_frequent": true_frequent, "true_positive": tp,
-                    "guaranteed": int((q.count.astype(np.int64) * k > n).sum()),
-                    "are": float(np.mean(np.abs(f - q.count.astype(np.int64)) / f)) if rep else 0.0,
-                    "precision": tp / rep if rep else 1.0,
-                    "recall": tp / true_frequent if true_frequent else 1.0,
-                    "delta": int(q.err[0]) if rep else None,
-                    "reported_as": "query (count + delta) * k > n; ARE over the reported items"}
+        sm = P.frequent(x, k, p, stream=stream)
+        accuracy = sm.accuracy(dcounts, wl["log2u"], n, k, stream=stream)
+        sm.close()
+        accuracy["delta"] = int(q.err[0]) if q.size else None
+        accuracy["reported_as"] = "query (count + delta) * k > n; ARE over the reported items"
 
         e2e = None
         if not args.no_e2e:

@@ -202,9 +202,9 @@ void pss_tree_free(pss_tree* tree);
  * arguments of one kind, else PSS_EMISMATCH), pss_query / pss_query_mode,
  * pss_export, pss_free, and pss_tree_levels / _level_nodes / _read_level /
  * _root / _free for trees.  Not available for Frequent summaries:
- * pss_accuracy_of (PSS_EINVAL) and the allocation-free form (pss_import
- * makes a Space Saving summary, pss_frequent_import a Frequent one;
- * pss_frequent_summarize_host takes host input).  The batched form is
+ * the allocation-free form (pss_import makes a Space Saving summary,
+ * pss_frequent_import a Frequent one; pss_frequent_summarize_host takes host
+ * input; pss_accuracy_of uses the Frequent bounds).  The batched form is
  * pss_frequent_batch_create, the served form pss_frequent_server_create.
  *
  * pss_frequent_summarize — p Misra–Gries block summaries (Algorithm 1
@@ -362,7 +362,9 @@ int pss_exact_counts(const void* d_items, uint64_t n, int item_bytes, int log2u,
  * reported items, recall = reported true k-majority items / true k-majority
  * items.  "Reported" means pss_query's answer (count * k > n), "true
  * k-majority" f * k > n.  Empty denominators give ARE 0, precision 1,
- * recall 1.  Synchronizes stream.
+ * recall 1.  For a Frequent summary "reported" is its query's answer,
+ * (count + delta) * k > n, and "guaranteed" count * k > n.  Synchronizes
+ * stream.
  */
 typedef struct {
   uint64_t reported;      /* entries with count * k > n */

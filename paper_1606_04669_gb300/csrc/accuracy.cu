@@ -44,27 +44,38 @@ __device__ __forceinline__ T block_sum(T v, T* scratch) {
   return r;  // valid in thread 0
 }
 
-// One CTA over the summary's entries.
+// One CTA over the summary's entries.  mg: a Frequent summary, whose counts
+// are lower bounds: reported when count + delta exceeds the threshold,
+// guaranteed when count does.
 template <typename ItemT>
 __global__ void __launch_bounds__(ACC_BS) accuracy_entries_kernel(SetView<ItemT> in,
                                                                   const uint32_t* __restrict__ counts,
                                                                   int log2u, u64 n, uint32_t kq,
-                                                                  AccOut* out) {
+                                                                  bool mg, AccOut* out) {
   __shared__ unsigned long long su[ACC_BS / 32];
   __shared__ double sd[ACC_BS / 32];
+  __shared__ u64 sdelta;
   const u64 u = 1ull << log2u;
   const u64 thr = n / kq;  // count k > n  <=>  count > floor(n / k)
   const uint32_t size = in.size[0];
+  if (mg) {  // delta = floor((n_covered - sum of counts) / k)
+    unsigned long long sum = 0;
+    for (uint32_t i = threadIdx.x; i < size; i += ACC_BS) sum += in.count[i];
+    sum = block_sum(sum, su);
+    if (threadIdx.x == 0) sdelta = (in.ncov[0] - sum) / kq;
+    __syncthreads();
+  }
+  const u64 delta = mg ? sdelta : 0;
   unsigned long long rep = 0, tp = 0, gu = 0;
   double are = 0.0;
   for (uint32_t i = threadIdx.x; i < size; i += ACC_BS) {
     const u64 c = in.count[i], e = in.err[i];
-    if (c <= thr) continue;
+    if (c + delta <= thr) continue;
     const u64 x = (u64)in.item[i];
     const u64 f = x < u ? counts[x] : 0;
     ++rep;
     tp += f > thr ? 1 : 0;
-    gu += c - e > thr ? 1 : 0;
+    gu += (mg ? c : c - e) > thr ? 1 : 0;
     if (f) are += (double)(c > f ? c - f : f - c) / (double)f;
   }
   rep = block_sum(rep, su);
@@ -117,11 +128,11 @@ cudaError_t launch_exact_counts(const void* items, u64 n, int item_bytes, int lo
 
 template <typename ItemT>
 cudaError_t launch_accuracy(SetView<ItemT> in, const uint32_t* counts, int log2u, u64 n,
-                            uint32_t kq, AccOut* out, cudaStream_t stream) {
+                            uint32_t kq, AccOut* out, cudaStream_t stream, bool mg) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(AccOut), stream);
   if (e != cudaSuccess) return e;
   count_launches(2);
-  accuracy_entries_kernel<ItemT><<<1, ACC_BS, 0, stream>>>(in, counts, log2u, n, kq, out);
+  accuracy_entries_kernel<ItemT><<<1, ACC_BS, 0, stream>>>(in, counts, log2u, n, kq, mg, out);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const u64 u = 1ull << log2u;
   true_frequent_kernel<<<grid_for(u), 256, 0, stream>>>(counts, u, n / kq, out);
@@ -129,8 +140,8 @@ cudaError_t launch_accuracy(SetView<ItemT> in, const uint32_t* counts, int log2u
 }
 
 template cudaError_t launch_accuracy<uint32_t>(SetView<uint32_t>, const uint32_t*, int, u64, uint32_t,
-                                               AccOut*, cudaStream_t);
+                                               AccOut*, cudaStream_t, bool);
 template cudaError_t launch_accuracy<u64>(SetView<u64>, const uint32_t*, int, u64, uint32_t, AccOut*,
-                                          cudaStream_t);
+                                          cudaStream_t, bool);
 
 }  // namespace pss

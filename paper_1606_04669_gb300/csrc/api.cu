@@ -755,7 +755,7 @@ int pss_exact_counts(const void* d_items, uint64_t n, int item_bytes, int log2u,
 int pss_accuracy_of(const pss_summary* summary, const uint32_t* d_counts, int log2u, uint64_t n,
                     uint32_t k, pss_accuracy* out, void* stream) {
   if (!summary || !d_counts || !out || k < 2 || log2u < 1 || log2u > 32) return PSS_EINVAL;
-  if (summary->kind != PSS_KIND_SPACE_SAVING) return PSS_EINVAL;
+  const bool mg = summary->kind == PSS_KIND_FREQUENT;
   cudaStream_t s = (cudaStream_t)stream;
   void* dmem = nullptr;
   cudaError_t e = cudaMallocAsync(&dmem, sizeof(pss::AccOut), s);
@@ -763,9 +763,9 @@ int pss_accuracy_of(const pss_summary* summary, const uint32_t* d_counts, int lo
   pss::AccOut* d = (pss::AccOut*)dmem;
   e = summary->item_bytes == 4
           ? pss::launch_accuracy<uint32_t>(set_view<uint32_t>(summary->mem, 1, summary->cap), d_counts,
-                                           log2u, n, k, d, s)
+                                           log2u, n, k, d, s, mg)
           : pss::launch_accuracy<u64>(set_view<u64>(summary->mem, 1, summary->cap), d_counts, log2u, n,
-                                      k, d, s);
+                                      k, d, s, mg);
   pss::AccOut h{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -123,7 +123,7 @@ cudaError_t launch_exact_counts(const void* items, u64 n, int item_bytes, int lo
 
 template <typename ItemT>
 cudaError_t launch_accuracy(SetView<ItemT> in, const uint32_t* counts, int log2u, u64 n,
-                            uint32_t kq, AccOut* out, cudaStream_t stream);
+                            uint32_t kq, AccOut* out, cudaStream_t stream, bool mg = false);
 
 // Warp-per-block summaries for k <= WARP_SS_MAX_K (summarize_warp.cu).  The
 // plain path (launch_summarize_blocks) uses them for k <= warp_kmax()

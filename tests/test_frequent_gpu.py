@@ -123,10 +123,20 @@ def test_merge_api_and_kind_checks():
     with pytest.raises(P.PssError) as ei:
         P.merge(a, ss)
     assert ei.value.code == P.PSS_EMISMATCH
+    # accuracy with the Frequent bounds, against the oracle's query and exact counts
     counts = P.exact_counts(to_dev(xa), 20)
-    with pytest.raises(P.PssError) as ei:
-        a.accuracy(counts, 20, len(xa), k)
-    assert ei.value.code == P.PSS_EINVAL
+    acc = a.accuracy(counts, 20, len(xa), k)
+    n = len(xa)
+    f = np.bincount(xa.astype(np.int64), minlength=1 << 20)
+    q = oracle.frequent_query(ra, n, k)
+    fq = f[q.item.astype(np.int64)]
+    cq = q.count.astype(np.int64)
+    assert acc["reported"] == q.size
+    assert acc["true_frequent"] == int((f * k > n).sum())
+    assert acc["true_positive"] == int((fq * k > n).sum())
+    assert acc["guaranteed"] == int((cq * k > n).sum())
+    assert abs(acc["are"] - float(np.mean(np.abs(fq - cq) / fq))) < 1e-12
+    assert acc["recall"] == 1.0
     with pytest.raises(P.PssError) as ei:
         P.frequent(to_dev(xa), 4097, 4)
     assert ei.value.code == P.PSS_EINVAL
