@@ -530,6 +530,16 @@ void pss_server_destroy(pss_server* server);
 uint32_t pss_set_warp_kmax(uint32_t kmax);
 
 /*
+ * Largest k whose block summaries the plain path computes with the round
+ * kernel: one warp per block, counters and table in shared memory, 32 items
+ * per round, the evictions in (count, touch) order from a queue of the
+ * minimum count.  Blocks with k above the warp kernel's limit and at most
+ * kmax (clamped to PSS_MAX_K_RESIDENT) use it; the result is the same as with
+ * the other kernels.  Process-wide; returns the previous value.
+ */
+uint32_t pss_set_round_kmax(uint32_t kmax);
+
+/*
  * Profiling.  The paper reports run time and the "fractional overhead" of
  * the reduction relative to the computation (Section 4.1); the library can
  * time its own kernel groups with CUDA events on the launching stream.

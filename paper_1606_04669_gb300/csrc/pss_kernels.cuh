@@ -91,6 +91,22 @@ cudaError_t launch_frequent_blocks(const ItemT* items, u64 n, uint32_t p, uint32
 // Shared memory of one Frequent warp with kc counters.
 size_t frequent_warp_bytes(uint32_t kc, int item_bytes);
 
+// Space Saving block summaries by one warp per block in rounds of 32 items
+// (summarize_round.cu); k <= PSS_MAX_K_RESIDENT.  round_kmax(): the largest k
+// the plain path sends there (0: none).
+template <typename ItemT>
+cudaError_t launch_summarize_round_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
+                                          uint32_t count, SetView<ItemT> out, uint32_t node0,
+                                          cudaStream_t stream);
+template <typename ItemT>
+cudaError_t launch_summarize_round_batch(const BatchStream* streams, const BatchTask* tasks,
+                                         uint32_t ntasks, uint32_t* counter, uint32_t k,
+                                         uint32_t grid, cudaStream_t stream);
+template <typename ItemT>
+uint32_t round_batch_grid(uint32_t k, uint32_t ntasks, int sms);
+size_t round_warp_bytes(uint32_t k, int item_bytes);
+uint32_t round_kmax();
+
 // Canonical export of node `node`: every entry (filter 0), entries with
 // count * kq > n (filter 1) or (count - err) * kq > n (filter 2), sorted by
 // (count desc, item asc), written to out[0..*out_n).  Frequent summaries:

@@ -1178,9 +1178,11 @@ __global__ void __launch_bounds__(BS, 1024 / BS)
 
 namespace {
 std::atomic<uint32_t> g_warp_kmax{WARP_SS_DEFAULT_K};
+std::atomic<uint32_t> g_round_kmax{0};
 }  // namespace
 
 uint32_t warp_kmax() { return g_warp_kmax.load(); }
+uint32_t round_kmax() { return g_round_kmax.load(); }
 
 template <typename ItemT>
 size_t ss_smem_bytes(uint32_t k) {
@@ -1247,6 +1249,8 @@ cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint3
                                     cudaStream_t stream) {
   if (out.k <= warp_kmax())
     return launch_summarize_warp_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
+  if (out.k <= round_kmax())
+    return launch_summarize_round_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
   if (out.k <= SS_SMEM_MAX_K) {
     const int bs = ss_shape_bs<ItemT>(out.k, false);
     const void* kern = block_kernel_of<ItemT>(bs);
@@ -1322,6 +1326,10 @@ template cudaError_t launch_summarize_blocks<u64>(const u64*, u64, uint32_t, uin
                                                   SetView<u64>, uint32_t, cudaStream_t);
 
 }  // namespace pss
+
+extern "C" uint32_t pss_set_round_kmax(uint32_t kmax) {
+  return pss::g_round_kmax.exchange(kmax < PSS_MAX_K_RESIDENT ? kmax : PSS_MAX_K_RESIDENT);
+}
 
 extern "C" uint32_t pss_set_warp_kmax(uint32_t kmax) {
   return pss::g_warp_kmax.exchange(kmax < pss::WARP_SS_MAX_K ? kmax : pss::WARP_SS_MAX_K);

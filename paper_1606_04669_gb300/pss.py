@@ -155,6 +155,7 @@ SIGNATURES = {
                                                 u64p]),
     "pss_server_destroy": (None, [vp]),
     "pss_set_warp_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
+    "pss_set_round_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
     "pss_set_host_direct": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
@@ -511,6 +512,12 @@ def set_host_direct(on: bool) -> int:
     """pss_summarize_host reads mapped pinned host memory in place (True) or
     stages copies (False).  Returns the previous setting."""
     return int(load().pss_set_host_direct(1 if on else 0))
+
+
+def set_round_kmax(kmax: int) -> int:
+    """pss_set_round_kmax: the largest k the plain path runs on the round
+    kernel (0: none); returns the previous value."""
+    return int(load().pss_set_round_kmax(int(kmax)))
 
 
 def set_warp_kmax(kmax: int) -> int:
