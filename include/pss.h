@@ -534,8 +534,10 @@ uint32_t pss_set_warp_kmax(uint32_t kmax);
  * kernel: one warp per block, counters and table in shared memory, 32 items
  * per round, the evictions in (count, touch) order from a queue of the
  * minimum count.  Blocks with k above the warp kernel's limit and at most
- * kmax (clamped to PSS_MAX_K_RESIDENT) use it; the result is the same as with
- * the other kernels.  Process-wide; returns the previous value.
+ * kmax (clamped to PSS_MAX_K_RESIDENT) use it when the launch has enough
+ * blocks to fill half the warps it keeps resident; the result is the same as
+ * with the other kernels.  The default is 256.  Process-wide; returns the
+ * previous value.
  */
 uint32_t pss_set_round_kmax(uint32_t kmax);
 

@@ -28,8 +28,10 @@ struct StreamPlan {
   std::vector<size_t> level_off;     // arena offset of each level's set
   std::vector<uint32_t> level_nodes;
   uint32_t out_off;                  // first result entry of this stream
-  bool warp;                         // block summaries on the warp kernel
+  int kernel;                        // block summaries: KERN_CTA, KERN_WARP or KERN_ROUND
 };
+
+enum { KERN_CTA = 0, KERN_WARP = 1, KERN_ROUND = 2 };
 
 // Kernel for a stream's block summaries.  Both kernels compute the same
 // summaries; the warp kernel (counters in registers, one item at a time)
@@ -57,6 +59,26 @@ bool use_warp_kernel(uint32_t k, double skew) {
   return false;
 }
 
+// The round kernel (one warp per block in rounds of 32 items) against the
+// best of the other two, measured on a GB300 with the batch's block length
+// (2^28 u32 items in blocks of 2^15; round / best other items/s): k = 32:
+// 0.61..0.91 at s <= 1.2, 1.40..2.97 at s >= 1.5; k = 48..64: 1.10..1.22 at
+// s <= 0.8, 0.80..0.89 at 1.0..1.2, 1.42..2.42 at s >= 1.5; k = 96..256:
+// 1.37..3.77 at every skew; k = 320..448: 1.08..1.88 at s <= 1.0, 0.84..1.11
+// at 1.2..1.5, 1.05..1.15 at s >= 2.0.  It is off when pss_set_round_kmax(0).
+bool use_round_kernel(uint32_t k, double skew) {
+  if (round_kmax() == 0 || k > 448) return false;
+  if (skew <= 0.0) return k > 64 && k <= 256;
+  if (k <= 64) return skew >= 1.4 || (k >= 48 && skew < 0.9);
+  if (k <= 256) return true;
+  return skew < 1.1 || skew >= 1.9;
+}
+
+int choose_kernel(uint32_t k, double skew) {
+  if (use_round_kernel(k, skew)) return KERN_ROUND;
+  return use_warp_kernel(k, skew) ? KERN_WARP : KERN_CTA;
+}
+
 struct LevelLaunch {
   size_t descs_off, tasks_off;
   uint32_t ntasks;
@@ -69,6 +91,8 @@ struct KClass {
   uint32_t ntasks = 0, grid = 0;
   size_t wtasks_off = 0, wcounter_off = 0;  // the class's streams on the warp kernel
   uint32_t wntasks = 0, wgrid = 0;
+  size_t rtasks_off = 0, rcounter_off = 0;  // ... and on the round kernel
+  uint32_t rntasks = 0, rgrid = 0;
   std::vector<LevelLaunch> levels;
   cudaStream_t side = nullptr;
   cudaEvent_t join = nullptr;
@@ -170,9 +194,19 @@ int enqueue(pss_batch* b, cudaStream_t s) {
     if (e != cudaSuccess) return from_cuda(e);
     e = cudaMemsetAsync(b->arena + c.counter_off, 0, 4, c.side);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->arena + c.wcounter_off, 0, 4, c.side);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->arena + c.rcounter_off, 0, 4, c.side);
     if (e != cudaSuccess) return from_cuda(e);
     {
-      ProfScope prof(PROF_SUMMARIZE, c.side, (c.ntasks ? 1 : 0) + (c.wntasks ? 1 : 0));
+      ProfScope prof(PROF_SUMMARIZE, c.side,
+                     (c.ntasks ? 1 : 0) + (c.wntasks ? 1 : 0) + (c.rntasks ? 1 : 0));
+      if (c.rntasks) {
+        count_launches(1);
+        e = launch_summarize_round_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
+                                                (const BatchTask*)(b->arena + c.rtasks_off),
+                                                c.rntasks, (uint32_t*)(b->arena + c.rcounter_off),
+                                                c.k, c.rgrid, c.side);
+        if (e != cudaSuccess) return from_cuda(e);
+      }
       if (c.wntasks) {
         count_launches(1);
         e = launch_summarize_warp_batch<ItemT>((const BatchStream*)(b->arena + b->streams_off),
@@ -284,7 +318,7 @@ int batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out, int 
     sp.p = (desc->p && desc->p[i]) ? desc->p[i]
                                    : (mg ? pss_frequent_plan_blocks(sp.n, sp.k, w, skew)
                                          : pss_plan_blocks(sp.n, sp.k, w, skew));
-    sp.warp = !mg && use_warp_kernel(sp.k, skew);
+    sp.kernel = mg ? KERN_CTA : choose_kernel(sp.k, skew);
     if (sp.k < 2 || sp.k > PSS_MAX_K_RESIDENT || sp.p == 0 || (sp.n > 0 && !sp.items) ||
         (sp.n + sp.p - 1) / sp.p >= (1ull << 32)) {
       destroy(b);
@@ -334,10 +368,10 @@ int batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out, int 
     for (uint32_t i = 0; i < ns; ++i)
       if (b->s[i].k == c.k) c.sids.push_back(i);
     // tasks of each kernel, longest blocks first so that the last wave is short
-    auto plan_tasks = [&](bool warp, size_t* off, size_t* counter, uint32_t* count) {
+    auto plan_tasks = [&](int kernel, size_t* off, size_t* counter, uint32_t* count) {
       std::vector<BatchTask> tasks;
       for (uint32_t i : c.sids)
-        if (b->s[i].warp == warp)
+        if (b->s[i].kernel == kernel)
           for (uint32_t r = 0; r < b->s[i].p; ++r) tasks.push_back(BatchTask{i, r});
       std::vector<uint64_t> key(tasks.size());
       for (size_t t = 0; t < tasks.size(); ++t) {
@@ -356,8 +390,17 @@ int batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out, int 
       upload(*off, sorted.data(), sizeof(BatchTask) * sorted.size());
       *counter = take(4);
     };
-    plan_tasks(false, &c.tasks_off, &c.counter_off, &c.ntasks);
-    plan_tasks(true, &c.wtasks_off, &c.wcounter_off, &c.wntasks);
+    plan_tasks(KERN_CTA, &c.tasks_off, &c.counter_off, &c.ntasks);
+    plan_tasks(KERN_WARP, &c.wtasks_off, &c.wcounter_off, &c.wntasks);
+    plan_tasks(KERN_ROUND, &c.rtasks_off, &c.rcounter_off, &c.rntasks);
+    if (c.rntasks) {
+      c.rgrid = w == 4 ? round_batch_grid<uint32_t>(c.k, c.rntasks, sms)
+                       : round_batch_grid<u64>(c.k, c.rntasks, sms);
+      if (c.rgrid == 0) {
+        destroy(b);
+        return PSS_EINVAL;
+      }
+    }
     if (c.ntasks && mg) {
       c.grid = w == 4 ? frequent_batch_grid<uint32_t>(c.k - 1, c.ntasks, sms)
                       : frequent_batch_grid<u64>(c.k - 1, c.ntasks, sms);

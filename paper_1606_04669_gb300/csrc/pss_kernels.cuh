@@ -106,6 +106,9 @@ template <typename ItemT>
 uint32_t round_batch_grid(uint32_t k, uint32_t ntasks, int sms);
 size_t round_warp_bytes(uint32_t k, int item_bytes);
 uint32_t round_kmax();
+// Warps of the round kernel resident per SM at k (0 if it cannot run).
+template <typename ItemT>
+uint32_t round_resident_warps(uint32_t k);
 
 // Canonical export of node `node`: every entry (filter 0), entries with
 // count * kq > n (filter 1) or (count - err) * kq > n (filter 2), sorted by
@@ -146,6 +149,7 @@ cudaError_t launch_accuracy(SetView<ItemT> in, const uint32_t* counts, int log2u
 // (default WARP_SS_DEFAULT_K); the batch picks per stream (batch.cu).
 constexpr uint32_t WARP_SS_MAX_K = 256;
 constexpr uint32_t WARP_SS_DEFAULT_K = 64;
+constexpr uint32_t ROUND_SS_DEFAULT_K = 256;  // plain path: the round kernel up to this k
 uint32_t warp_kmax();
 
 template <typename ItemT>

@@ -1178,7 +1178,27 @@ __global__ void __launch_bounds__(BS, 1024 / BS)
 
 namespace {
 std::atomic<uint32_t> g_warp_kmax{WARP_SS_DEFAULT_K};
-std::atomic<uint32_t> g_round_kmax{0};
+std::atomic<uint32_t> g_round_kmax{ROUND_SS_DEFAULT_K};
+std::atomic<int> g_sms{0};
+
+// Whether a launch of `count` blocks with k counters runs on the round
+// kernel: k up to round_kmax(), and enough blocks to fill half the warps
+// the round kernel keeps resident (with fewer, the CTA kernel's 256 or 512
+// threads per block win; measured at 2^28 and 2^30 items).
+template <typename ItemT>
+bool use_round_kernel(uint32_t k, uint32_t count) {
+  if (k > round_kmax()) return false;
+  int sms = g_sms.load(std::memory_order_relaxed);
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return false;
+    g_sms.store(sms, std::memory_order_relaxed);
+  }
+  const uint32_t per_sm = round_resident_warps<ItemT>(k);
+  return per_sm > 0 && 2ull * count >= (uint64_t)sms * per_sm;
+}
 }  // namespace
 
 uint32_t warp_kmax() { return g_warp_kmax.load(); }
@@ -1249,7 +1269,7 @@ cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint3
                                     cudaStream_t stream) {
   if (out.k <= warp_kmax())
     return launch_summarize_warp_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
-  if (out.k <= round_kmax())
+  if (use_round_kernel<ItemT>(out.k, count))
     return launch_summarize_round_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
   if (out.k <= SS_SMEM_MAX_K) {
     const int bs = ss_shape_bs<ItemT>(out.k, false);

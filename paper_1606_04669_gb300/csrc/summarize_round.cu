@@ -555,6 +555,28 @@ int round_warps_per_cta(uint32_t k, bool batch) {
 size_t round_warp_bytes(uint32_t k, int item_bytes) { return r_layout(k, item_bytes).bytes; }
 
 template <typename ItemT>
+uint32_t round_resident_warps(uint32_t k) {
+  static std::atomic<uint32_t> memo[PSS_MAX_K_RESIDENT + 1];
+  if (k < 2 || k > PSS_MAX_K_RESIDENT) return 0;
+  uint32_t v = memo[k].load(std::memory_order_relaxed);
+  if (v) return v;
+  const int wpc = round_warps_per_cta<ItemT>(k, false);
+  if (wpc <= 0) return 0;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, (const void*)ssr_block_kernel<ItemT>,
+                                                    32 * wpc,
+                                                    (size_t)wpc * r_layout(k, (int)sizeof(ItemT)).bytes) !=
+      cudaSuccess)
+    return 0;
+  v = (uint32_t)(blocks * wpc);
+  memo[k].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+template uint32_t round_resident_warps<uint32_t>(uint32_t);
+template uint32_t round_resident_warps<u64>(uint32_t);
+
+template <typename ItemT>
 cudaError_t launch_summarize_round_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
                                           uint32_t count, SetView<ItemT> out, uint32_t node0,
                                           cudaStream_t stream) {
