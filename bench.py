@@ -53,6 +53,10 @@ WORKLOADS = {
         desc="one wave of Frequent warps at k=2000: n=1368*262144 uint32 Zipf(s=1.1) over "
              "[0,2^24), seed 2; p=1368 blocks of 262144 items (9 warps on each of 152 SMs)",
         n=1368 * 262144, w=4, s=1.1, log2u=24, seed=2, k=2000, p=1368),
+    "round_k256": dict(
+        desc="round-kernel shape: n=2^28 uint32 Zipf(s=1.0) over [0,2^32), seed 13; k=256; "
+             "p=8192 blocks of 32768 items (one warp per block); binary merge tree; query n/k",
+        n=1 << 28, w=4, s=1.0, log2u=32, seed=13, k=256, p=8192),
     "small": dict(
         desc="plain single stream: n=2^20 uint32 Zipf(s=1.1) over [0,2^20), seed 1; k=100; p=8; "
              "binary merge tree; query n/k",
@@ -785,7 +789,7 @@ def main():
             "input_gbs": input_gbs,
             "hbm_frac": input_gbs / hbm,
             "hbm_frac_nominal_8tbs": input_gbs / 8000.0,
-            "roofline": {"bound": "hbm", "kernel": "ss_block_kernel (block summaries)",
+            "roofline": {"bound": "hbm", "kernel": P.plan_kernel(k, p, w) + " (block summaries)",
                          "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": traffic_per_launch(wl),

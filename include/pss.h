@@ -541,6 +541,17 @@ uint32_t pss_set_warp_kmax(uint32_t kmax);
  */
 uint32_t pss_set_round_kmax(uint32_t kmax);
 
+/* The block-summary kernel the plain path uses for `count` blocks with k
+ * counters (item_bytes 4 or 8): PSS_KERNEL_CTA (window-parallel, one CTA per
+ * block; k above 4096 keeps part of its state in HBM), PSS_KERNEL_WARP
+ * (counters in a warp's registers) or PSS_KERNEL_ROUND (one warp per block in
+ * rounds); -1 for invalid arguments.  Queries the device's occupancy once per
+ * k. */
+#define PSS_KERNEL_CTA 0
+#define PSS_KERNEL_WARP 1
+#define PSS_KERNEL_ROUND 2
+int pss_plan_kernel(uint32_t k, uint32_t count, int item_bytes);
+
 /*
  * Profiling.  The paper reports run time and the "fractional overhead" of
  * the reduction relative to the computation (Section 4.1); the library can

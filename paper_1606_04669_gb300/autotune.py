@@ -122,15 +122,16 @@ def sweep(n: int = 1 << 27, item_bytes: int = 8, steps: int = 3, seed: int = 77,
     return results, table
 
 
-KERNEL_KS = (32, 64, 96, 128, 160, 192, 224, 256)
+KERNEL_KS = (32, 48, 64, 96, 128, 160, 192, 224, 256, 320, 384, 448)
 KERNEL_SKEWS = (0.5, 0.7, 0.9, 1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6, 1.7, 1.8, 1.9)
 
 
 def sweep_kernels(n: int = 1 << 28, item_bytes: int = 8, length: int = 1 << 15, steps: int = 4,
                   seed: int = 11):
-    """Items/s of the two summarize kernels for k <= 256 at full occupancy
-    (n / length blocks), per (skew, k): the data behind the skew bands in
-    which the batch runs a stream on the warp kernel."""
+    """Items/s of the summarize kernels at full occupancy (n / length
+    blocks), per (skew, k): the warp kernel (k <= 256), the round kernel and
+    the CTA kernel -- the data behind the skew bands by which the batch picks
+    a stream's kernel."""
     import torch
 
     import paper_1606_04669_gb300 as P
@@ -149,22 +150,30 @@ def sweep_kernels(n: int = 1 << 28, item_bytes: int = 8, length: int = 1 << 15, 
         return e0.elapsed_time(e1) / steps
 
     out = []
-    prev = P.set_warp_kmax(256)
+    prev_w = P.set_warp_kmax(0)
+    prev_r = P.set_round_kmax(0)
     try:
         for zs in KERNEL_SKEWS:
             x = P.gen_zipf(n, seed=seed, s=zs, log2u=32, item_bytes=item_bytes)
             for k in KERNEL_KS:
                 p = n // length
                 row = {"skew": zs, "k": k, "block_length": length, "p": p}
-                for name, kmax in (("warp", 256), ("cta", 0)):
-                    P.set_warp_kmax(kmax)
+                kernels = [("round", 0, P.PSS_MAX_K_RESIDENT), ("cta", 0, 0)]
+                if k <= 256:
+                    kernels.append(("warp", 256, 0))
+                for name, wk, rk in kernels:
+                    P.set_warp_kmax(wk)
+                    P.set_round_kmax(rk)
                     row[name + "_items_per_s"] = n / (timeit(x, k, p) / 1e3)
-                P.set_warp_kmax(256)
-                row["warp_over_cta"] = row["warp_items_per_s"] / row["cta_items_per_s"]
+                others = [row[nm + "_items_per_s"] for nm in ("cta", "warp") if nm + "_items_per_s" in row]
+                row["round_over_best_other"] = row["round_items_per_s"] / max(others)
+                if k <= 256:
+                    row["warp_over_cta"] = row["warp_items_per_s"] / row["cta_items_per_s"]
                 out.append(row)
             del x
     finally:
-        P.set_warp_kmax(prev)
+        P.set_warp_kmax(prev_w)
+        P.set_round_kmax(prev_r)
     return out
 
 

@@ -61,17 +61,20 @@ bool use_warp_kernel(uint32_t k, double skew) {
 
 // The round kernel (one warp per block in rounds of 32 items) against the
 // best of the other two, measured on a GB300 with the batch's block length
-// (2^28 u32 items in blocks of 2^15; round / best other items/s): k = 32:
-// 0.61..0.91 at s <= 1.2, 1.40..2.97 at s >= 1.5; k = 48..64: 1.10..1.22 at
-// s <= 0.8, 0.80..0.89 at 1.0..1.2, 1.42..2.42 at s >= 1.5; k = 96..256:
-// 1.37..3.77 at every skew; k = 320..448: 1.08..1.88 at s <= 1.0, 0.84..1.11
-// at 1.2..1.5, 1.05..1.15 at s >= 2.0.  It is off when pss_set_round_kmax(0).
+// (autotune.sweep_kernels: 2^28 u64 items in blocks of 2^15; round / best
+// other items/s): k = 32: 0.61..0.88 at s <= 1.3, 1.03..2.34 at s >= 1.4;
+// k = 48..64: 1.11..1.17 at s <= 0.7, 0.77..0.98 at 0.9..1.2, 1.17..1.94 at
+// s >= 1.4; k = 96..256: 1.08..4.05 at every skew; k = 320..384: 1.02..1.79
+// at s <= 1.3, 0.81..0.92 above; k = 448: 1.06..1.14 at s <= 1.1, 0.77..0.97
+// above.  It is off when pss_set_round_kmax(0).
 bool use_round_kernel(uint32_t k, double skew) {
   if (round_kmax() == 0 || k > 448) return false;
   if (skew <= 0.0) return k > 64 && k <= 256;
-  if (k <= 64) return skew >= 1.4 || (k >= 48 && skew < 0.9);
+  if (k <= 32) return skew >= 1.4;
+  if (k <= 64) return skew >= 1.4 || skew < 0.8;
   if (k <= 256) return true;
-  return skew < 1.1 || skew >= 1.9;
+  if (k <= 384) return skew < 1.3;
+  return skew < 1.1;
 }
 
 int choose_kernel(uint32_t k, double skew) {

@@ -1347,6 +1347,14 @@ template cudaError_t launch_summarize_blocks<u64>(const u64*, u64, uint32_t, uin
 
 }  // namespace pss
 
+extern "C" int pss_plan_kernel(uint32_t k, uint32_t count, int item_bytes) {
+  if (k < 2 || (item_bytes != 4 && item_bytes != 8)) return -1;
+  if (k <= pss::warp_kmax()) return PSS_KERNEL_WARP;
+  const bool round = item_bytes == 4 ? pss::use_round_kernel<uint32_t>(k, count)
+                                     : pss::use_round_kernel<pss::u64>(k, count);
+  return round ? PSS_KERNEL_ROUND : PSS_KERNEL_CTA;
+}
+
 extern "C" uint32_t pss_set_round_kmax(uint32_t kmax) {
   return pss::g_round_kmax.exchange(kmax < PSS_MAX_K_RESIDENT ? kmax : PSS_MAX_K_RESIDENT);
 }

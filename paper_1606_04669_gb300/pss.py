@@ -156,6 +156,7 @@ SIGNATURES = {
     "pss_server_destroy": (None, [vp]),
     "pss_set_warp_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
     "pss_set_round_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
+    "pss_plan_kernel": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int]),
     "pss_set_host_direct": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
@@ -512,6 +513,18 @@ def set_host_direct(on: bool) -> int:
     """pss_summarize_host reads mapped pinned host memory in place (True) or
     stages copies (False).  Returns the previous setting."""
     return int(load().pss_set_host_direct(1 if on else 0))
+
+
+KERNEL_NAMES = {0: "ss_block_kernel", 1: "ssw_block_kernel", 2: "ssr_block_kernel"}
+
+
+def plan_kernel(k: int, count: int, item_bytes: int = 4) -> str:
+    """pss_plan_kernel: the name of the block-summary kernel the plain path
+    runs for `count` blocks with k counters."""
+    code = int(load().pss_plan_kernel(int(k), int(count), int(item_bytes)))
+    if code < 0:
+        raise ValueError("invalid k or item width")
+    return KERNEL_NAMES[code]
 
 
 def set_round_kmax(kmax: int) -> int:
