@@ -33,7 +33,7 @@ struct StreamPlan {
 
 enum { KERN_CTA = 0, KERN_WARP = 1, KERN_ROUND = 2 };
 
-// Kernel for a stream's block summaries.  Both kernels compute the same
+// Kernel for a stream's block summaries.  The three kernels compute the same
 // summaries; the warp kernel (counters in registers, one item at a time)
 // wins where misses dominate, the window-parallel CTA kernel where hits do,
 // and its cost rises with k.  The skew band [lo, hi) in which the warp
