@@ -13,9 +13,10 @@
 //
 // A round probes every lane's item and applies at once the longest prefix of
 // the lanes whose effects commute:
-//   * occurrences of one item form a group (__match_any_sync) led by its
-//     lowest lane, which applies them all (count + occurrences, touch = the
-//     last one);
+//   * hits add to their counters with shared-memory atomics (count + 1,
+//     touch = max of the positions); the occurrences of one missing item form
+//     a group (__match_any_sync) led by its lowest lane, which applies them
+//     all;
 //   * while counters are free, each missing item's leader takes one;
 //   * on a full table each missing item's leader is an event: events take
 //     victims from the queue in order, skipping entries no longer at m and
@@ -304,33 +305,34 @@ __device__ void round_block(const ItemT* __restrict__ xs, uint32_t len, uint32_t
       uint32_t fpos = R_NONE;
       if (act) s = W.find(x, h, &fpos);
       const bool miss = act && s < 0;
-      const unsigned am = __ballot_sync(RFULL, act);
+      const bool hit = act && !miss;
+      // hits add with shared-memory atomics; the occurrences of one missing
+      // item form a group led by its lowest lane
+      const unsigned mm = __ballot_sync(RFULL, miss);
       unsigned grp = 0;
-      if (act) grp = __match_any_sync(am, x);
-      const bool leader = act && (grp & below) == 0;
+      if (miss) grp = __match_any_sync(mm, x);
+      const bool leader = miss && (grp & below) == 0;
       uint32_t end;
       if (!W.full) {
         // free counters: each missing item's leader takes one; the round
         // ends at the first leader that finds none
-        const unsigned lead = __ballot_sync(RFULL, leader && miss);
+        const unsigned lead = __ballot_sync(RFULL, leader);
         const uint32_t free_n = k - W.used;
         end = (uint32_t)__popc(lead) <= free_n ? here : (uint32_t)__fns(lead, 0, (int)free_n + 1);
         const unsigned before = end >= 32 ? RFULL : (1u << end) - 1u;
         bool fresh = false;
         if (leader && lane < end) {
           const unsigned g = grp & before;
-          const uint32_t c = (uint32_t)__popc(g), last = 31u - (uint32_t)__clz(g);
-          if (miss) {
-            const uint32_t slot = W.used + (uint32_t)__popc(lead & below);
-            W.item[slot] = x;
-            W.cnt[slot] = c;
-            W.touch[slot] = t0 + last;
-            W.err[slot] = 0;
-            fresh = W.insert(slot, fpos);
-          } else {
-            W.cnt[s] += c;
-            W.touch[s] = t0 + last;
-          }
+          const uint32_t slot = W.used + (uint32_t)__popc(lead & below);
+          W.item[slot] = x;
+          W.cnt[slot] = (uint32_t)__popc(g);
+          W.touch[slot] = t0 + 31u - (uint32_t)__clz(g);
+          W.err[slot] = 0;
+          fresh = W.insert(slot, fpos);
+        }
+        if (hit && lane < end) {
+          atomicAdd(&W.cnt[s], 1u);
+          atomicMax(&W.touch[s], t0 + lane);
         }
         W.taken += (uint32_t)__popc(__ballot_sync(RFULL, fresh));
         W.used += (uint32_t)__popc(lead & before);
@@ -341,11 +343,10 @@ __device__ void round_block(const ItemT* __restrict__ xs, uint32_t len, uint32_t
         }
       } else {
         // full table: events take victims from the queue
-        const bool hit = act && !miss;
         const uint32_t ch = hit ? W.cnt[s] : 0u;
         const bool minhit = hit && ch == W.m;
-        const unsigned mh = __ballot_sync(RFULL, minhit && leader);
-        const unsigned em = __ballot_sync(RFULL, leader && miss);
+        const unsigned mh = __ballot_sync(RFULL, minhit);
+        const unsigned em = __ballot_sync(RFULL, leader);
         const uint32_t ne = (uint32_t)__popc(em);
         end = here;
         uint32_t v = R_NOSLOT;  // this event's victim
@@ -363,7 +364,7 @@ __device__ void round_block(const ItemT* __restrict__ xs, uint32_t len, uint32_t
               const unsigned vm = __ballot_sync(RFULL, valid);
               const uint32_t nv = (uint32_t)__popc(vm);
               const uint32_t tk = min(nv, ne - assigned);
-              const bool mine = leader && miss && rank >= assigned && rank < assigned + tk;
+              const bool mine = leader && rank >= assigned && rank < assigned + tk;
               const int src = mine ? (int)__fns(vm, 0, (int)(rank - assigned) + 1) : (int)lane;
               const uint16_t got = __shfl_sync(RFULL, q, src);
               if (mine) v = got;
@@ -376,10 +377,12 @@ __device__ void round_block(const ItemT* __restrict__ xs, uint32_t len, uint32_t
               exhausted = true;
             }
           } else {
-            // some minimum counters are hit: a warp-uniform walk of the
-            // events in order; the earliest hit of each such counter is
-            // recorded in hitl
-            if (minhit && leader) W.hitl[s] = (uint8_t)lane;
+            // some minimum counters are hit: the earliest hit of each goes to
+            // hitl, then a warp-uniform walk of the events in order
+            unsigned mg = 0;
+            if (minhit) mg = __match_any_sync(mh, s);
+            const bool mlead = minhit && (mg & below) == 0;
+            if (mlead) W.hitl[s] = (uint8_t)lane;
             __syncwarp();
             uint32_t e = 0, qp = W.qh;
             for (uint32_t iter = 0; e < ne && iter <= W.qlen + 32; ++iter) {
@@ -401,34 +404,39 @@ __device__ void round_block(const ItemT* __restrict__ xs, uint32_t len, uint32_t
             }
             W.qh = min(qp, W.qlen);
             __syncwarp();
-            if (minhit && leader) W.hitl[s] = 0xFF;
+            if (mlead) W.hitl[s] = 0xFF;
           }
         }
         const unsigned before = end >= 32 ? RFULL : (1u << end) - 1u;
-        const bool ev = leader && miss && lane < end;
+        const bool ev = leader && lane < end;
         // victims' cells are freed before the new items claim cells
         if (ev) W.cell[W.cellof[v]] = (unsigned short)R_FREED;
         __syncwarp();
         bool fresh = false;
         bool logged = false;
         uint16_t logslot = R_NOSLOT;
-        if (leader && lane < end) {
+        if (ev) {
           const unsigned g = grp & before;
-          const uint32_t c = (uint32_t)__popc(g), last = 31u - (uint32_t)__clz(g);
-          if (ev) {
-            W.item[v] = x;
-            W.err[v] = W.m;
-            W.cnt[v] = W.m + c;
-            W.touch[v] = t0 + last;
-            fresh = W.insert(v, fpos);
-            logged = c == 1;
-            logslot = (uint16_t)v;
-          } else {
-            W.cnt[s] += c;
-            W.touch[s] = t0 + last;
-            logged = minhit && c == 1;
-            logslot = (uint16_t)s;
-          }
+          const uint32_t c = (uint32_t)__popc(g);
+          W.item[v] = x;
+          W.err[v] = W.m;
+          W.cnt[v] = W.m + c;
+          W.touch[v] = t0 + 31u - (uint32_t)__clz(g);
+          fresh = W.insert(v, fpos);
+          logged = c == 1;
+          logslot = (uint16_t)v;
+        }
+        uint32_t old = 0;
+        const bool apply_hit = hit && lane < end;
+        if (apply_hit) {
+          old = atomicAdd(&W.cnt[s], 1u);
+          atomicMax(&W.touch[s], t0 + lane);
+        }
+        __syncwarp();
+        // a minimum counter hit exactly once in the prefix reached m + 1 there
+        if (apply_hit && old == W.m && W.cnt[s] == W.m + 1) {
+          logged = true;
+          logslot = (uint16_t)s;
         }
         // counters that reached m + 1 in the round, in time order
         const unsigned lm = __ballot_sync(RFULL, logged);
