@@ -64,49 +64,47 @@ WORKLOADS = {
 }
 
 
-# DRAM traffic of the summarize kernel from one ncu capture (profiles/
-# ss_block_kernel_wave_k2000.md: 304 blocks of 262144 u32 items, k = 2000 ->
-# 318.87 MB read + 3.37 MB written).  Traffic grows with the number of blocks,
-# so a launch of p such blocks moves p times the per-block bytes.  The figure
-# is only valid for the kernel source it was measured on.
-TRAFFIC = {"summarize_sha1": "f34a6510834efe750b50d521d53c776477dc093f",
-           "bytes_per_block": (318.87e6 + 3.37e6) / 304, "block_items": 262144, "k": 2000, "w": 4}
+# DRAM traffic of each block-summary kernel from one ncu capture of it, valid
+# only for the kernel source it was measured on (the sha1 of that file) and the
+# block shape it was measured at.  Traffic grows with the number of blocks, so
+# a launch of p such blocks moves p times the per-block bytes.
+#   ss_block_kernel: profiles/ss_block_kernel_wave_k2000.md, 304 blocks of
+#     262144 u32 items, k = 2000 -> 318.87 MB read + 3.97 MB written.
+#   ssr_block_kernel: profiles/ssr_block_kernel_k256.md, 8192 blocks of 32768
+#     u32 items, k = 256 -> 1077.7 MB read + 32.5 MB written.
+#   frequent_block_kernel: profiles/frequent_block_kernel_wave_k2000.md, 1368
+#     blocks of 262144 u32 items, k = 2000 -> 1434.60 MB read + 3.76 MB written.
+TRAFFIC = {
+    "ss_block_kernel": {"src": "summarize.cu",
+                        "sha1": "6e7eb939e5cac32d736ed5dbb9bfbc8115e6ad70",
+                        "bytes_per_block": (318.87e6 + 3.97e6) / 304, "block_items": 262144,
+                        "k": 2000, "w": 4},
+    "ssr_block_kernel": {"src": "summarize_round.cu",
+                         "sha1": "0e210092b09dbb8f0a1656928b774624097af347",
+                         "bytes_per_block": (1077.7e6 + 32.5e6) / 8192, "block_items": 32768,
+                         "k": 256, "w": 4},
+    "frequent_block_kernel": {"src": "frequent.cu",
+                              "sha1": "b2f35211bbd44917466a2c57c50e8e0958cfcd08",
+                              "bytes_per_block": (1434.60e6 + 3.76e6) / 1368,
+                              "block_items": 262144, "k": 2000, "w": 4},
+}
 
 
-# DRAM traffic of the Frequent block kernel from one ncu capture (profiles/
-# frequent_block_kernel_wave_k2000.md: 1368 blocks of 262144 u32 items,
-# k = 2000 -> 1434.60 MB read + 3.76 MB written), valid for that source only.
-FREQ_TRAFFIC = {"frequent_sha1": "b2f35211bbd44917466a2c57c50e8e0958cfcd08",
-                "bytes_per_block": (1434.60e6 + 3.76e6) / 1368, "block_items": 262144, "k": 2000,
-                "w": 4}
-
-
-def frequent_traffic_per_launch(n, k, p, w):
+def traffic_per_launch(kernel, n, k, p, w):
+    """Measured DRAM bytes of one launch of `kernel` over p blocks of n/p
+    items, or None when no capture matches this source and block shape."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1606_04669_gb300", "csrc", "frequent.cu")
+    t = TRAFFIC.get(kernel)
+    if t is None:
+        return None
+    src = os.path.join(ROOT, "paper_1606_04669_gb300", "csrc", t["src"])
     try:
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    t = FREQ_TRAFFIC
-    if sha != t["frequent_sha1"] or k != t["k"] or w != t["w"] or n // p != t["block_items"]:
+    if sha != t["sha1"] or k != t["k"] or w != t["w"] or n // p != t["block_items"]:
         return None
     return t["bytes_per_block"] * p
-
-
-def traffic_per_launch(wl):
-    import hashlib
-    src = os.path.join(ROOT, "paper_1606_04669_gb300", "csrc", "summarize.cu")
-    try:
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None
-    t = TRAFFIC
-    if sha != t["summarize_sha1"] or wl["k"] != t["k"] or wl["w"] != t["w"]:
-        return None
-    if wl["n"] // wl["p"] != t["block_items"]:
-        return None
-    return t["bytes_per_block"] * wl["p"]
 
 
 def peaks():
@@ -598,7 +596,7 @@ def run_frequent(args):
                          "achieved": alg / (sum_ms / 1e3) / 1e9, "peak": hbm,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": alg / (sum_ms / 1e3) / 1e9 / hbm,
-                         "traffic": frequent_traffic_per_launch(n, k, p, w),
+                         "traffic": traffic_per_launch("frequent_block_kernel", n, k, p, w),
                          "avg_launch_ms": sum_ms, "algorithmic_bytes": alg},
             "breakdown": {"summarize_ms": sum_ms, "merge_tree_ms": merge_ms},
             "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e,
@@ -776,6 +774,7 @@ def main():
         cpu = cpu_baseline(wl, args.cpu_seconds)
 
     if rank == 0:
+        kernel = P.plan_kernel(k, p, w)
         line = {
             "metric": METRIC, "value": value, "unit": "items/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -789,10 +788,10 @@ def main():
             "input_gbs": input_gbs,
             "hbm_frac": input_gbs / hbm,
             "hbm_frac_nominal_8tbs": input_gbs / 8000.0,
-            "roofline": {"bound": "hbm", "kernel": P.plan_kernel(k, p, w) + " (block summaries)",
+            "roofline": {"bound": "hbm", "kernel": kernel + " (block summaries)",
                          "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": traffic_per_launch(wl),
+                         "traffic": traffic_per_launch(kernel, n, k, p, w),
                          "avg_launch_ms": sum_ms, "algorithmic_bytes": alg_bytes},
             "breakdown": {"summarize_ms": sum_ms, "merge_tree_ms": merge_ms,
                           "query_ms": query_ms,
