@@ -8,7 +8,8 @@
 // Both inputs are stored sorted by item, so the union is formed without any
 // hashing or sorting: the position of an S1 entry in the item-ordered union is
 // its own index plus the number of S2-only items before it, and symmetrically
-// for S2-only entries (binary searches in shared memory plus one prefix sum).
+// for S2-only entries (binary searches in shared memory plus one exchange of
+// per-warp totals).
 // Prune(k) is an exact selection: a most-significant-digit radix select finds
 // the k-th largest count c*, then the entries with count > c* and the first
 // (in item order) of those with count == c* are kept.  The output is again
@@ -58,7 +59,7 @@ __host__ __device__ inline size_t merge_carve(uint32_t k, unsigned char* base, u
   L.ia = (ItemT*)take(sizeof(ItemT) * k);
   L.ib = (ItemT*)take(sizeof(ItemT) * k);
   L.borank = (uint32_t*)take(4ull * (k + 1));
-  L.hist = (uint32_t*)take(4ull * 256);
+  L.hist = (uint32_t*)take(4ull * 512);
   L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
   L.srcA = (uint16_t*)(BIG ? gtake(2ull * 2 * k) : take(2ull * 2 * k));
   L.srcB = (uint16_t*)(BIG ? gtake(2ull * 2 * k) : take(2ull * 2 * k));
@@ -99,72 +100,164 @@ __device__ __forceinline__ u64 block_reduce_u64(u64 v, u64* scratch, bool is_max
 // so the union adds the counts of equal items; when more than k items remain,
 // the (k+1)-th largest count c* is subtracted from every count and only the
 // counts above c* stay (their minimum and errors stay 0).
+//
+// One merge is a short chain of dependent steps in one CTA, so its time is
+// latency: global loads are issued G strided iterations at a time before their
+// values are used, the phases that number entries exchange per-warp totals
+// once (one barrier) instead of scanning the whole block per 512 entries, and
+// the radix histogram adds each warp's equal digits with one atomic.  The
+// kernels are bounded to three CTAs of BS = 512 threads per SM (40 registers),
+// as many as the shared memory of k = 2000 allows.
 template <typename ItemT, int BS, bool BIG, bool MG = false>
 __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<ItemT>& B,
                             uint32_t nb, const SetView<ItemT>& O, uint32_t no,
                             unsigned char* smem, unsigned char* gslice) {
+  constexpr uint32_t NW = BS / 32;
+  constexpr int G = 2;
   __shared__ u64 sh_prefix;
   __shared__ uint32_t sh_need;
   MSmem<ItemT> s;
   const uint32_t k = O.k;
   merge_carve<ItemT, BS, BIG>(k, smem, gslice, &s);
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   const uint32_t sa = A.size[na], sb = B.size[nb];
   const u64 mA = A.m[na], mB = B.m[nb];
   const size_t ba = (size_t)na * k, bb = (size_t)nb * k, bo = (size_t)no * k;
-  for (uint32_t i = tid; i < sa; i += BS) s.ia[i] = A.item[ba + i];
-  for (uint32_t j = tid; j < sb; j += BS) s.ib[j] = B.item[bb + j];
-  __syncthreads();
-
-  uint32_t par = 0;
-  auto scan = [&](uint32_t v, uint32_t* tot) {
-    uint32_t* buf = s.wsum + (par ? (BS / 32 + 1) : 0);
-    par ^= 1;
-    return block_exclusive_scan<BS>(v, buf, tot);
-  };
-
-  // Ranks of the S2-only items.
-  uint32_t run = 0;
-  for (uint32_t base = 0; base < sb; base += BS) {
-    const uint32_t j = base + tid;
-    bool only = false;
-    if (j < sb) {
-      const ItemT x = s.ib[j];
-      const uint32_t ii = lower_bound(s.ia, sa, x);
-      only = !(ii < sa && s.ia[ii] == x);
+  for (uint32_t base = 0; base < sa; base += G * BS) {
+    ItemT v[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t i = base + t * BS + tid;
+      if (i < sa) v[t] = A.item[ba + i];
     }
-    uint32_t tot;
-    const uint32_t ex = scan(only ? 1u : 0u, &tot);
-    if (j < sb) s.borank[j] = run + ex;
-    run += tot;
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t i = base + t * BS + tid;
+      if (i < sa) s.ia[i] = v[t];
+    }
   }
-  if (tid == 0) s.borank[sb] = run;
+  for (uint32_t base = 0; base < sb; base += G * BS) {
+    ItemT v[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t j = base + t * BS + tid;
+      if (j < sb) v[t] = B.item[bb + j];
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t j = base + t * BS + tid;
+      if (j < sb) s.ib[j] = v[t];
+    }
+  }
+  if (tid < 256) s.hist[tid] = 0;  // first radix pass (BS >= 256)
   __syncthreads();
-  const uint32_t U = sa + run;
 
-  // The union in item order.
-  for (uint32_t i = tid; i < sa; i += BS) {
-    const ItemT x = s.ia[i];
-    const uint32_t jj = lower_bound(s.ib, sb, x);
-    const bool both = jj < sb && s.ib[jj] == x;
-    const uint32_t pos = i + s.borank[jj];
-    s.uc[pos] = A.count[ba + i] + (both ? B.count[bb + jj] : mB);
-    s.srcA[pos] = (uint16_t)i;
-    s.srcB[pos] = both ? (uint16_t)jj : NONE;
+  // Ranks of the S2-only items: warp w numbers its own run of S2, then adds
+  // the S2-only items of the runs before it.
+  uint32_t total_only = 0;
+  {
+    const uint32_t seg = (sb + NW - 1) / NW;
+    const uint32_t j0 = min(sb, warp * seg), j1 = min(sb, j0 + seg);
+    uint32_t nonly = 0;
+    for (uint32_t jb = j0; jb < j1; jb += 32 * G) {
+      bool only[G];
+#pragma unroll
+      for (int t = 0; t < G; ++t) {
+        const uint32_t j = jb + 32 * t + lane;
+        only[t] = false;
+        if (j < j1) {
+          const ItemT x = s.ib[j];
+          const uint32_t ii = lower_bound(s.ia, sa, x);
+          only[t] = !(ii < sa && s.ia[ii] == x);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < G; ++t) {
+        const uint32_t j = jb + 32 * t + lane;
+        const unsigned bal = __ballot_sync(0xffffffffu, only[t]);
+        if (j < j1) s.borank[j] = nonly + __popc(bal & lt);
+        nonly += __popc(bal);
+      }
+    }
+    if (lane == 0) s.wsum[warp] = nonly;
+    __syncthreads();
+    uint32_t before = 0;
+    for (uint32_t w = 0; w < NW; ++w) {
+      const uint32_t v = s.wsum[w];
+      before += w < warp ? v : 0u;
+      total_only += v;
+    }
+    for (uint32_t j = j0 + lane; j < j1; j += 32) s.borank[j] += before;
+    if (tid == 0) s.borank[sb] = total_only;
   }
-  for (uint32_t j = tid; j < sb; j += BS) {
-    if (s.borank[j + 1] != s.borank[j]) {
-      const uint32_t ii = lower_bound(s.ia, sa, s.ib[j]);
-      const uint32_t pos = ii + s.borank[j];
-      s.uc[pos] = B.count[bb + j] + mA;
-      s.srcA[pos] = NONE;
-      s.srcB[pos] = (uint16_t)j;
+  __syncthreads();
+  const uint32_t U = sa + total_only;
+
+  // The union in item order: an S1 entry at i + (S2-only items before it),
+  // an S2-only entry at (S1 items before it) + its rank.
+  for (uint32_t base = 0; base < sa; base += G * BS) {
+    u64 c[G];
+    uint32_t jj[G];
+    bool both[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t i = base + t * BS + tid;
+      if (i < sa) c[t] = A.count[ba + i];
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t i = base + t * BS + tid;
+      jj[t] = 0;
+      both[t] = false;
+      if (i < sa) {
+        const ItemT x = s.ia[i];
+        jj[t] = lower_bound(s.ib, sb, x);
+        both[t] = jj[t] < sb && s.ib[jj[t]] == x;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t i = base + t * BS + tid;
+      if (i < sa) c[t] += both[t] ? B.count[bb + jj[t]] : mB;
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t i = base + t * BS + tid;
+      if (i < sa) {
+        const uint32_t pos = i + s.borank[jj[t]];
+        s.uc[pos] = c[t];
+        s.srcA[pos] = (uint16_t)i;
+        s.srcB[pos] = both[t] ? (uint16_t)jj[t] : NONE;
+      }
+    }
+  }
+  for (uint32_t base = 0; base < sb; base += G * BS) {
+    u64 c[G];
+    bool only[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t j = base + t * BS + tid;
+      only[t] = j < sb && s.borank[j + 1] != s.borank[j];
+      if (only[t]) c[t] = B.count[bb + j];
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const uint32_t j = base + t * BS + tid;
+      if (only[t]) {
+        const uint32_t pos = lower_bound(s.ia, sa, s.ib[j]) + s.borank[j];
+        s.uc[pos] = c[t] + mA;
+        s.srcA[pos] = NONE;
+        s.srcB[pos] = (uint16_t)j;
+      }
     }
   }
   __syncthreads();
 
   // Prune(k): the k-th largest count c*, and how many entries equal to c* to
-  // keep (MG: the (k+1)-th largest, none kept).
+  // keep (MG: the (k+1)-th largest, none kept).  Most-significant digit
+  // first, 8 bits a pass; two histogram buffers alternate, so a pass needs
+  // two barriers.
   const bool cut = U > k;
   u64 cstar = 0;
   uint32_t need = 0;
@@ -175,54 +268,126 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     int shift = ((63 - __clzll((long long)mx)) / 8) * 8;
     u64 prefix = 0, pmask = 0;
     need = MG ? k + 1 : k;
-    for (; shift >= 0; shift -= 8) {
-      for (uint32_t i = tid; i < 256; i += BS) s.hist[i] = 0;
-      __syncthreads();
-      for (uint32_t u = tid; u < U; u += BS) {
-        const u64 c = s.uc[u];
-        if ((c & pmask) == prefix) atomicAdd(&s.hist[(c >> shift) & 255u], 1u);
+    for (uint32_t buf = 0; shift >= 0; shift -= 8, buf ^= 1u) {
+      uint32_t* h = s.hist + 256 * buf;
+      for (uint32_t base = 0; base < U; base += BS) {
+        const uint32_t u = base + tid;
+        const u64 c = u < U ? s.uc[u] : 0;
+        const bool in = u < U && (c & pmask) == prefix;
+        const uint32_t d = in ? (uint32_t)(c >> shift) & 255u : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (in && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
       }
+      if (tid < 256) s.hist[256 * (buf ^ 1u) + tid] = 0;  // the next pass's buffer
       __syncthreads();
-      if (tid == 0) {
-        uint32_t acc = 0;
-        int d = 255;
-        for (; d > 0; --d) {
-          if (acc + s.hist[d] >= need) break;
-          acc += s.hist[d];
+      if (warp == 0) {
+        // lane l holds digits 255 - 8l down to 248 - 8l; the first lane whose
+        // running total (from the top digit) reaches `need` holds c*'s digit.
+        // As in a walk down from 255 that stops at 0, digit 0 is taken
+        // without checking its bin.
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          v[t] = h[255 - 8 * lane - t];
+          sum += v[t];
         }
-        sh_need = need - acc;
-        sh_prefix = prefix | ((u64)d << shift);
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= (uint32_t)o) inc += y;
+        }
+        const unsigned reach = __ballot_sync(0xffffffffu, inc >= need);
+        const uint32_t L = reach ? (uint32_t)(__ffs(reach) - 1) : 31u;
+        if (lane == L) {
+          uint32_t acc = inc - sum, d = 0;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const uint32_t dd = 255u - 8u * lane - (uint32_t)t;
+            if (dd == 0 || acc + v[t] >= need) {
+              d = dd;
+              break;
+            }
+            acc += v[t];
+          }
+          sh_need = need - acc;
+          sh_prefix = prefix | ((u64)d << shift);
+        }
       }
       __syncthreads();
       need = sh_need;
       prefix = sh_prefix;
       pmask |= 255ull << shift;
-      __syncthreads();
     }
     cstar = prefix;
   }
 
-  // Keep and write in item order.
-  uint32_t run_eq = 0, run_keep = 0;
-  for (uint32_t base = 0; base < U; base += BS) {
-    const uint32_t u = base + tid;
-    const bool in = u < U;
-    const u64 c = in ? s.uc[u] : 0;
-    const bool eq = in && cut && c == cstar;
-    uint32_t te;
-    const uint32_t ee = scan(eq ? 1u : 0u, &te);
-    const bool keep = in && (!cut || c > cstar || (!MG && eq && run_eq + ee < need));
-    uint32_t tk;
-    const uint32_t ek = scan(keep ? 1u : 0u, &tk);
-    if (keep) {
-      const uint32_t o = run_keep + ek;
-      const uint16_t a = s.srcA[u], b = s.srcB[u];
-      O.item[bo + o] = (a != NONE) ? s.ia[a] : s.ib[b];
-      O.count[bo + o] = (MG && cut) ? c - cstar : c;
-      O.err[bo + o] = ((a != NONE) ? A.err[ba + a] : mA) + ((b != NONE) ? B.err[bb + b] : mB);
+  // Keep and write in item order: warp w takes its own run of the union,
+  // counts what it keeps, and learns from the other warps' totals where its
+  // output starts.  Entries above c* (all, without a cut) are kept; of those
+  // equal to c*, the first `need` in item order (none for MG).
+  uint32_t nkeep = 0;
+  {
+    const uint32_t seg = (U + NW - 1) / NW;
+    const uint32_t u0 = min(U, warp * seg), u1 = min(U, u0 + seg);
+    uint32_t ngt = 0, neq = 0;
+    for (uint32_t ub = u0; ub < u1; ub += 32) {
+      const uint32_t u = ub + lane;
+      const u64 c = u < u1 ? s.uc[u] : 0;
+      ngt += __popc(__ballot_sync(0xffffffffu, u < u1 && (!cut || c > cstar)));
+      neq += __popc(__ballot_sync(0xffffffffu, u < u1 && cut && !MG && c == cstar));
     }
-    run_eq += te;
-    run_keep += tk;
+    if (lane == 0) {
+      s.wsum[warp] = ngt;
+      s.wsum[NW + 1 + warp] = neq;
+    }
+    __syncthreads();
+    uint32_t gbefore = 0, ebefore = 0, gtot = 0, etot = 0;
+    for (uint32_t w = 0; w < NW; ++w) {
+      const uint32_t g = s.wsum[w], e = s.wsum[NW + 1 + w];
+      gbefore += w < warp ? g : 0u;
+      ebefore += w < warp ? e : 0u;
+      gtot += g;
+      etot += e;
+    }
+    nkeep = gtot + min(etot, need);
+    for (uint32_t ub = u0; ub < u1; ub += 32 * G) {
+      u64 c[G], ea[G], eb[G];
+      uint16_t a[G], b[G];
+      uint32_t pos[G];
+      bool keep[G];
+#pragma unroll
+      for (int t = 0; t < G; ++t) {
+        const uint32_t u = ub + 32 * t + lane;
+        const bool in = u < u1;
+        c[t] = in ? s.uc[u] : 0;
+        const bool gt = in && (!cut || c[t] > cstar);
+        const bool eq = in && cut && !MG && c[t] == cstar;
+        const unsigned bg = __ballot_sync(0xffffffffu, gt), be = __ballot_sync(0xffffffffu, eq);
+        const uint32_t r = ebefore + __popc(be & lt);
+        keep[t] = gt || (eq && r < need);
+        pos[t] = gbefore + __popc(bg & lt) + min(r, need);
+        gbefore += __popc(bg);
+        ebefore += __popc(be);
+        a[t] = keep[t] ? s.srcA[u] : NONE;
+        b[t] = keep[t] ? s.srcB[u] : NONE;
+      }
+#pragma unroll
+      for (int t = 0; t < G; ++t) {
+        if (keep[t]) {
+          ea[t] = a[t] != NONE ? A.err[ba + a[t]] : mA;
+          eb[t] = b[t] != NONE ? B.err[bb + b[t]] : mB;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < G; ++t) {
+        if (keep[t]) {
+          O.item[bo + pos[t]] = a[t] != NONE ? s.ia[a[t]] : s.ib[b[t]];
+          O.count[bo + pos[t]] = (MG && cut) ? c[t] - cstar : c[t];
+          O.err[bo + pos[t]] = ea[t] + eb[t];
+        }
+      }
+    }
   }
   u64 mout = 0;
   if (MG) {
@@ -235,7 +400,7 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     mout = block_reduce_u64<BS>(mn, s.red, false);
   }
   if (tid == 0) {
-    O.size[no] = run_keep;
+    O.size[no] = nkeep;
     O.m[no] = mout;
     O.ncov[no] = A.ncov[na] + B.ncov[nb];
     const uint32_t st = *A.status | *B.status;
@@ -262,7 +427,7 @@ __device__ void copy_node(const SetView<ItemT>& in, uint32_t ni, const SetView<I
 }
 
 template <typename ItemT, int BS, bool BIG, bool MG>
-__global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out,
+__global__ void __launch_bounds__(BS, 3) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out,
                                                          unsigned char* gscratch, size_t gslice) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t j = blockIdx.x;
@@ -275,7 +440,7 @@ __global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetV
 }
 
 template <typename ItemT, int BS, bool BIG, bool MG>
-__global__ void __launch_bounds__(BS) merge_pair_kernel(SetView<ItemT> a, uint32_t ia,
+__global__ void __launch_bounds__(BS, 3) merge_pair_kernel(SetView<ItemT> a, uint32_t ia,
                                                         SetView<ItemT> b, uint32_t ib,
                                                         SetView<ItemT> out, unsigned char* gscratch) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -285,7 +450,7 @@ __global__ void __launch_bounds__(BS) merge_pair_kernel(SetView<ItemT> a, uint32
 // Batch form: task (d, j) builds node j of the next level of descriptor d
 // (MG: the Frequent merge).
 template <typename ItemT, int BS, bool MG>
-__global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __restrict__ descs,
+__global__ void __launch_bounds__(BS, 3) merge_tasks_kernel(const MergeDesc* __restrict__ descs,
                                                          const BatchTask* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char smem[];
   const BatchTask t = tasks[blockIdx.x];

@@ -180,3 +180,31 @@ def test_frequent_server_matches_oracle():
         assert ents(final[t]) == ents(tenant[t])
         assert (final[t].m, final[t].n_covered) == (oracle.frequent_delta(tenant[t], k),
                                                     tenant[t].n_covered)
+
+
+def test_wait_expires_before_start_then_completes():
+    """The bounded wait: before the scheduler starts nothing completes, so a
+    short wait returns PSS_ETIMEOUT; the server is still usable afterwards."""
+    tenants, k = 2, 64
+    reqs = make_requests(6, tenants, seed=9)
+    srv = P.Server(tenants, k, budget_bytes=64 << 20, max_batch=4)
+    try:
+        srv.submit(reqs)
+        with pytest.raises(P.PssError) as e:
+            srv.wait(0.2)
+        assert e.value.code == P.pss.PSS_ETIMEOUT
+        assert srv.poll() == []
+        srv.start()
+        srv.wait(300)
+        comps = {c["id"]: c for c in srv.poll()}
+        res = {r["id"]: srv.result(r["id"]) for r in reqs}
+    finally:
+        srv.close()
+    assert sorted(comps) == sorted(r["id"] for r in reqs)
+    expect, _ = oracle_expectations(reqs, tenants, k)
+    for r in reqs:
+        assert comps[r["id"]]["status"] == 0
+        segq, tq, _ = expect[r["id"]]
+        got_seg, got_ten = res[r["id"]]
+        assert ents(got_seg) == summary_entries(segq)
+        assert ents(got_ten) == summary_entries(tq)
