@@ -6,10 +6,10 @@
 // Prune(k) keeps the k largest by (count descending, item ascending).
 //
 // Both inputs are stored sorted by item, so the union is formed without any
-// hashing or sorting: the position of an S1 entry in the item-ordered union is
-// its own index plus the number of S2-only items before it, and symmetrically
-// for S2-only entries (binary searches in shared memory plus one exchange of
-// per-warp totals).
+// hashing or sorting: it is laid out in the order of the merged sequence of
+// S1 and S2 (S1 first on equal items), each thread walking its own run of
+// merged positions from one merge-path search; the S2 copy of an item in both
+// leaves its position empty.
 // Prune(k) is an exact selection: a most-significant-digit radix select finds
 // the k-th largest count c*, then the entries with count > c* and the first
 // (in item order) of those with count == c* are kept.  The output is again
@@ -22,12 +22,12 @@ namespace pss {
 namespace {
 
 constexpr uint16_t NONE = 0xFFFF;
+constexpr u64 EMPTY = ~0ull;  // a merged position without a union entry
 
 template <typename ItemT>
 struct MSmem {
   ItemT* ia;
   ItemT* ib;
-  uint32_t* borank;
   u64* uc;
   uint16_t* srcA;
   uint16_t* srcB;
@@ -58,7 +58,6 @@ __host__ __device__ inline size_t merge_carve(uint32_t k, unsigned char* base, u
   L.red = (u64*)take(8ull * (BS / 32 + 1));
   L.ia = (ItemT*)take(sizeof(ItemT) * k);
   L.ib = (ItemT*)take(sizeof(ItemT) * k);
-  L.borank = (uint32_t*)take(4ull * (k + 1));
   L.hist = (uint32_t*)take(4ull * 512);
   L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
   L.srcA = (uint16_t*)(BIG ? gtake(2ull * 2 * k) : take(2ull * 2 * k));
@@ -68,12 +67,15 @@ __host__ __device__ inline size_t merge_carve(uint32_t k, unsigned char* base, u
   return off;
 }
 
+// How many of the first d elements of the merged sequence of a and b (equal
+// items: a first) come from a.
 template <typename ItemT>
-__device__ __forceinline__ uint32_t lower_bound(const ItemT* a, uint32_t n, ItemT x) {
-  uint32_t lo = 0, hi = n;
+__device__ __forceinline__ uint32_t merge_path(const ItemT* a, uint32_t sa, const ItemT* b,
+                                               uint32_t sb, uint32_t d) {
+  uint32_t lo = d > sb ? d - sb : 0u, hi = d < sa ? d : sa;
   while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= b[d - mid - 1]) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
@@ -102,12 +104,12 @@ __device__ __forceinline__ u64 block_reduce_u64(u64 v, u64* scratch, bool is_max
 // counts above c* stay (their minimum and errors stay 0).
 //
 // One merge is a short chain of dependent steps in one CTA, so its time is
-// latency: global loads are issued G strided iterations at a time before their
-// values are used, the phases that number entries exchange per-warp totals
-// once (one barrier) instead of scanning the whole block per 512 entries, and
-// the radix histogram adds each warp's equal digits with one atomic.  The
-// kernels are bounded to three CTAs of BS = 512 threads per SM (40 registers),
-// as many as the shared memory of k = 2000 allows.
+// latency and instruction count: global loads are issued several at a time
+// before their values are used, the union costs one merge-path search per
+// thread, the keep phase exchanges per-warp totals once (one barrier), and the
+// radix histogram adds each warp's equal digits with one atomic.  (Bounding
+// the kernels to three CTAs per SM, as many as the shared memory of k = 2000
+// allows, forces spills at 40 registers and was slower.)
 template <typename ItemT, int BS, bool BIG, bool MG = false>
 __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<ItemT>& B,
                             uint32_t nb, const SetView<ItemT>& O, uint32_t no,
@@ -116,6 +118,7 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
   constexpr int G = 2;
   __shared__ u64 sh_prefix;
   __shared__ uint32_t sh_need;
+  __shared__ uint32_t sh_dup[NW];
   MSmem<ItemT> s;
   const uint32_t k = O.k;
   merge_carve<ItemT, BS, BIG>(k, smem, gslice, &s);
@@ -153,106 +156,64 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
   if (tid < 256) s.hist[tid] = 0;  // first radix pass (BS >= 256)
   __syncthreads();
 
-  // Ranks of the S2-only items: warp w numbers its own run of S2, then adds
-  // the S2-only items of the runs before it.
-  uint32_t total_only = 0;
+  // The union in merged order: position d holds the entry of the d-th
+  // element of the merged sequence, or EMPTY for S2's copy of an item also in
+  // S1 (it follows S1's copy).  Each thread walks its own run of positions
+  // (an odd length, so that lanes' 8-byte stores fall in different banks),
+  // WS steps at a time with their global loads issued together.
+  const uint32_t L = sa + sb;
   {
-    const uint32_t seg = (sb + NW - 1) / NW;
-    const uint32_t j0 = min(sb, warp * seg), j1 = min(sb, j0 + seg);
-    uint32_t nonly = 0;
-    for (uint32_t jb = j0; jb < j1; jb += 32 * G) {
-      bool only[G];
+    constexpr int WS = 3;
+    const uint32_t per = ((L + BS - 1) / BS) | 1u;
+    const uint32_t d0 = min(L, tid * per), d1 = min(L, d0 + per);
+    uint32_t i = merge_path(s.ia, sa, s.ib, sb, d0), j = d0 - i, ndup = 0;
+    for (uint32_t d = d0; d < d1; d += WS) {
+      uint16_t pa[WS], pb[WS];
+      u64 c[WS], c2[WS];
 #pragma unroll
-      for (int t = 0; t < G; ++t) {
-        const uint32_t j = jb + 32 * t + lane;
-        only[t] = false;
-        if (j < j1) {
-          const ItemT x = s.ib[j];
-          const uint32_t ii = lower_bound(s.ia, sa, x);
-          only[t] = !(ii < sa && s.ia[ii] == x);
+      for (int t = 0; t < WS; ++t) {
+        pa[t] = NONE;
+        pb[t] = NONE;
+        if (d + t < d1) {
+          if (j >= sb || (i < sa && s.ia[i] <= s.ib[j])) {
+            pa[t] = (uint16_t)i;
+            if (j < sb && s.ib[j] == s.ia[i]) pb[t] = (uint16_t)j;
+            ++i;
+          } else {
+            if (i > 0 && s.ia[i - 1] == s.ib[j]) ++ndup;
+            else pb[t] = (uint16_t)j;
+            ++j;
+          }
         }
       }
 #pragma unroll
-      for (int t = 0; t < G; ++t) {
-        const uint32_t j = jb + 32 * t + lane;
-        const unsigned bal = __ballot_sync(0xffffffffu, only[t]);
-        if (j < j1) s.borank[j] = nonly + __popc(bal & lt);
-        nonly += __popc(bal);
+      for (int t = 0; t < WS; ++t) {
+        c[t] = 0;
+        c2[t] = 0;
+        if (pa[t] != NONE) c[t] = A.count[ba + pa[t]];
+        else if (pb[t] != NONE) c[t] = B.count[bb + pb[t]];
+        if (pa[t] != NONE && pb[t] != NONE) c2[t] = B.count[bb + pb[t]];
+      }
+#pragma unroll
+      for (int t = 0; t < WS; ++t) {
+        if (d + t < d1) {
+          u64 v = EMPTY;
+          if (pa[t] != NONE) v = c[t] + (pb[t] != NONE ? c2[t] : mB);
+          else if (pb[t] != NONE) v = c[t] + mA;
+          s.uc[d + t] = v;
+          s.srcA[d + t] = pa[t];
+          s.srcB[d + t] = pb[t];
+        }
       }
     }
-    if (lane == 0) s.wsum[warp] = nonly;
-    __syncthreads();
-    uint32_t before = 0;
-    for (uint32_t w = 0; w < NW; ++w) {
-      const uint32_t v = s.wsum[w];
-      before += w < warp ? v : 0u;
-      total_only += v;
-    }
-    for (uint32_t j = j0 + lane; j < j1; j += 32) s.borank[j] += before;
-    if (tid == 0) s.borank[sb] = total_only;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ndup += __shfl_xor_sync(0xffffffffu, ndup, o);
+    if (lane == 0) sh_dup[warp] = ndup;
   }
   __syncthreads();
-  const uint32_t U = sa + total_only;
-
-  // The union in item order: an S1 entry at i + (S2-only items before it),
-  // an S2-only entry at (S1 items before it) + its rank.
-  for (uint32_t base = 0; base < sa; base += G * BS) {
-    u64 c[G];
-    uint32_t jj[G];
-    bool both[G];
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const uint32_t i = base + t * BS + tid;
-      if (i < sa) c[t] = A.count[ba + i];
-    }
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const uint32_t i = base + t * BS + tid;
-      jj[t] = 0;
-      both[t] = false;
-      if (i < sa) {
-        const ItemT x = s.ia[i];
-        jj[t] = lower_bound(s.ib, sb, x);
-        both[t] = jj[t] < sb && s.ib[jj[t]] == x;
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const uint32_t i = base + t * BS + tid;
-      if (i < sa) c[t] += both[t] ? B.count[bb + jj[t]] : mB;
-    }
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const uint32_t i = base + t * BS + tid;
-      if (i < sa) {
-        const uint32_t pos = i + s.borank[jj[t]];
-        s.uc[pos] = c[t];
-        s.srcA[pos] = (uint16_t)i;
-        s.srcB[pos] = both[t] ? (uint16_t)jj[t] : NONE;
-      }
-    }
-  }
-  for (uint32_t base = 0; base < sb; base += G * BS) {
-    u64 c[G];
-    bool only[G];
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const uint32_t j = base + t * BS + tid;
-      only[t] = j < sb && s.borank[j + 1] != s.borank[j];
-      if (only[t]) c[t] = B.count[bb + j];
-    }
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const uint32_t j = base + t * BS + tid;
-      if (only[t]) {
-        const uint32_t pos = lower_bound(s.ia, sa, s.ib[j]) + s.borank[j];
-        s.uc[pos] = c[t] + mA;
-        s.srcA[pos] = NONE;
-        s.srcB[pos] = (uint16_t)j;
-      }
-    }
-  }
-  __syncthreads();
+  uint32_t dups = 0;
+  for (uint32_t w = 0; w < NW; ++w) dups += sh_dup[w];
+  const uint32_t U = L - dups;
 
   // Prune(k): the k-th largest count c*, and how many entries equal to c* to
   // keep (MG: the (k+1)-th largest, none kept).  Most-significant digit
@@ -263,20 +224,25 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
   uint32_t need = 0;
   if (cut) {
     u64 mx = 0;
-    for (uint32_t u = tid; u < U; u += BS) mx = s.uc[u] > mx ? s.uc[u] : mx;
+    for (uint32_t u = tid; u < L; u += BS) {
+      const u64 c = s.uc[u];
+      if (c != EMPTY && c > mx) mx = c;
+    }
     mx = block_reduce_u64<BS>(mx, s.red, true);
     int shift = ((63 - __clzll((long long)mx)) / 8) * 8;
     u64 prefix = 0, pmask = 0;
     need = MG ? k + 1 : k;
     for (uint32_t buf = 0; shift >= 0; shift -= 8, buf ^= 1u) {
       uint32_t* h = s.hist + 256 * buf;
-      for (uint32_t base = 0; base < U; base += BS) {
+      for (uint32_t base = 0; base < L; base += BS) {
         const uint32_t u = base + tid;
-        const u64 c = u < U ? s.uc[u] : 0;
-        const bool in = u < U && (c & pmask) == prefix;
-        const uint32_t d = in ? (uint32_t)(c >> shift) & 255u : 256u + lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (in && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        const u64 c = u < L ? s.uc[u] : EMPTY;
+        const bool in = c != EMPTY && (c & pmask) == prefix;
+        if (__any_sync(0xffffffffu, in)) {
+          const uint32_t d = in ? (uint32_t)(c >> shift) & 255u : 256u + lane;
+          const unsigned peers = __match_any_sync(0xffffffffu, d);
+          if (in && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        }
       }
       if (tid < 256) s.hist[256 * (buf ^ 1u) + tid] = 0;  // the next pass's buffer
       __syncthreads();
@@ -322,20 +288,21 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     cstar = prefix;
   }
 
-  // Keep and write in item order: warp w takes its own run of the union,
-  // counts what it keeps, and learns from the other warps' totals where its
-  // output starts.  Entries above c* (all, without a cut) are kept; of those
+  // Keep and write in item order: warp w takes its own run of merged
+  // positions, counts what it keeps, and learns from the other warps' totals
+  // where its output starts.  Entries above c* (all, without a cut) are kept; of those
   // equal to c*, the first `need` in item order (none for MG).
   uint32_t nkeep = 0;
   {
-    const uint32_t seg = (U + NW - 1) / NW;
-    const uint32_t u0 = min(U, warp * seg), u1 = min(U, u0 + seg);
+    const uint32_t seg = (L + NW - 1) / NW;
+    const uint32_t u0 = min(L, warp * seg), u1 = min(L, u0 + seg);
     uint32_t ngt = 0, neq = 0;
     for (uint32_t ub = u0; ub < u1; ub += 32) {
       const uint32_t u = ub + lane;
-      const u64 c = u < u1 ? s.uc[u] : 0;
-      ngt += __popc(__ballot_sync(0xffffffffu, u < u1 && (!cut || c > cstar)));
-      neq += __popc(__ballot_sync(0xffffffffu, u < u1 && cut && !MG && c == cstar));
+      const u64 c = u < u1 ? s.uc[u] : EMPTY;
+      const bool live = c != EMPTY;
+      ngt += __popc(__ballot_sync(0xffffffffu, live && (!cut || c > cstar)));
+      neq += __popc(__ballot_sync(0xffffffffu, live && cut && !MG && c == cstar));
     }
     if (lane == 0) {
       s.wsum[warp] = ngt;
@@ -359,8 +326,8 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
 #pragma unroll
       for (int t = 0; t < G; ++t) {
         const uint32_t u = ub + 32 * t + lane;
-        const bool in = u < u1;
-        c[t] = in ? s.uc[u] : 0;
+        c[t] = u < u1 ? s.uc[u] : EMPTY;
+        const bool in = c[t] != EMPTY;
         const bool gt = in && (!cut || c[t] > cstar);
         const bool eq = in && cut && !MG && c[t] == cstar;
         const unsigned bg = __ballot_sync(0xffffffffu, gt), be = __ballot_sync(0xffffffffu, eq);
@@ -396,7 +363,7 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     mout = cstar;
   } else if (U == k) {
     u64 mn = ~0ull;
-    for (uint32_t u = tid; u < U; u += BS) mn = s.uc[u] < mn ? s.uc[u] : mn;
+    for (uint32_t u = tid; u < L; u += BS) mn = s.uc[u] < mn ? s.uc[u] : mn;  // EMPTY is the largest
     mout = block_reduce_u64<BS>(mn, s.red, false);
   }
   if (tid == 0) {
@@ -427,7 +394,7 @@ __device__ void copy_node(const SetView<ItemT>& in, uint32_t ni, const SetView<I
 }
 
 template <typename ItemT, int BS, bool BIG, bool MG>
-__global__ void __launch_bounds__(BS, 3) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out,
+__global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out,
                                                          unsigned char* gscratch, size_t gslice) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t j = blockIdx.x;
@@ -440,7 +407,7 @@ __global__ void __launch_bounds__(BS, 3) merge_level_kernel(SetView<ItemT> in, S
 }
 
 template <typename ItemT, int BS, bool BIG, bool MG>
-__global__ void __launch_bounds__(BS, 3) merge_pair_kernel(SetView<ItemT> a, uint32_t ia,
+__global__ void __launch_bounds__(BS) merge_pair_kernel(SetView<ItemT> a, uint32_t ia,
                                                         SetView<ItemT> b, uint32_t ib,
                                                         SetView<ItemT> out, unsigned char* gscratch) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -450,7 +417,7 @@ __global__ void __launch_bounds__(BS, 3) merge_pair_kernel(SetView<ItemT> a, uin
 // Batch form: task (d, j) builds node j of the next level of descriptor d
 // (MG: the Frequent merge).
 template <typename ItemT, int BS, bool MG>
-__global__ void __launch_bounds__(BS, 3) merge_tasks_kernel(const MergeDesc* __restrict__ descs,
+__global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __restrict__ descs,
                                                          const BatchTask* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char smem[];
   const BatchTask t = tasks[blockIdx.x];
