@@ -13,6 +13,12 @@ steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+On one GPU the default line also carries a `batched` object (1024 uint64
+streams in one graph launch against the plain path looped over them) and a
+`served` object (60 s of open-loop Poisson arrivals, p50/p99 latency), the
+other two forms the metric compares (--no-batched / --no-served leave them
+out; --workload batched / served print their full lines).
+
 With --gpus N > 1 (launched by torchrun) every rank runs an independent
 replica on its own GPU (the path is replicated, not sharded) and the value is
 the items of all ranks over the slowest rank's time.
@@ -243,6 +249,42 @@ def cpu_baseline(wl, budget_s: float, seed_offset: int = 0):
             "seconds": dt, "host": host_info()}
 
 
+def workload_config(wl, world: int = 1) -> dict:
+    """The `config` object of the plain workloads' lines (both arms)."""
+    n, w = wl["n"], wl["w"]
+    return {"workload": wl["desc"], "n": n, "k": wl["k"], "p": wl["p"], "item_bytes": w,
+            "zipf_s": wl["s"], "universe": f"2^{wl['log2u']}", "seed": wl["seed"],
+            "l2": (f"input ({n * w / 2**30:.2f} GiB) larger than L2; no flush"
+                   if n * w > (256 << 20) else "input smaller than L2"),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def batched_summary(b: dict) -> dict:
+    """The batched form's object on the default line."""
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "input_gbs", "hbm_frac",
+            "batched_over_plain", "results_identical", "gpu_launches_per_step")
+    out = {key: b[key] for key in keep}
+    out["plain_loop_value"] = b["plain_loop"]["value"]
+    out["config"] = {key: b["config"][key] for key in ("streams", "total_items", "item_bytes",
+                                                         "k_classes", "blocks", "seed")}
+    out["workload"] = ("batched: 1024 uint64 streams, lengths log-uniform [1e4, 1e8], Zipf s "
+                       "U[0.8, 2] over [0, 2^32), k in {64, 256, 1024, 4096}, seed 3; one graph "
+                       "launch per step against the plain path looped over the streams")
+    return out
+
+
+def served_summary(v: dict) -> dict:
+    """The served form's object on the default line."""
+    keep = ("value", "unit", "latency_ms", "requests", "errors", "offered_items_per_s",
+            "generator_items_per_s", "makespan_s", "gpu_launches", "clocks")
+    out = {key: v[key] for key in keep}
+    out["config"] = v["config"]
+    out["workload"] = ("served: open-loop Poisson 2000 req/s, segments log-uniform [1e4, 1e7] "
+                       "uint32, Zipf s U[1, 2] over [0, 2^24), 256 tenants at k = 1024, 16 GB "
+                       "budget, seed 4; latency = completion - scheduled arrival")
+    return out
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return 0
@@ -270,7 +312,7 @@ def run_reference(args, wl, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32" if w == 4 else "u64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "n": n, "k": k, "p": p},
+        "config": workload_config(wl, 1),
         "cpu_baseline": {"value": value, "unit": "items/s", "cores": 1, "kind": "oracle",
                          "sample": f"per step: blocks 0..{blocks - 1} of {p} ({hi} items), "
                                    "block summaries + combine tree + query",
@@ -345,11 +387,12 @@ def run_sweep(args):
     return 0
 
 
-def run_batched(args):
+def run_batched(args, emit: bool = True):
     """1024 independent u64 streams (log-uniform lengths in [1e4, 1e8], Zipf s
     in [0.8, 2] over [0, 2^32), k in {64, 256, 1024, 4096}, seed 3) in one
     graph launch, against the plain path looped over the same streams
-    (--kind frequent: the Frequent summary, batched and plain)."""
+    (--kind frequent: the Frequent summary, batched and plain).  Returns the
+    line (printed when emit)."""
     import torch
 
     import paper_1606_04669_gb300 as P
@@ -415,18 +458,20 @@ def run_batched(args):
                    "plan": "autotune.plan_blocks (block length per k and skew class)",
                    "generation_s": gen_s},
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     batch.close()
-    return 0
+    return line
 
 
-def run_served(args):
+def run_served(args, emit: bool = True):
     """Open-loop Poisson arrivals at 2000 requests/s for `duration` seconds
     (seed 4): segments of log-uniform length in [1e4, 1e7] uint32 items, Zipf
     s in [1, 2] over [0, 2^24), generated on the device at admission, for 256
     tenants whose k = 1024 summaries stay resident; 16 GB admission budget.
     Latency = completion - scheduled arrival (no coordinated omission).
-    --kind frequent: Frequent (Misra-Gries) tenant summaries."""
+    --kind frequent: Frequent (Misra-Gries) tenant summaries.  Returns the
+    line (printed when emit)."""
     import numpy as np
     import torch
 
@@ -489,8 +534,9 @@ def run_served(args):
                    "universe": "2^24", "budget_bytes": 16 << 30, "seed": 4,
                    "segments": "generated on the device at admission (included in latency)"},
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 FREQUENT_K = (2000, 500, 64)
@@ -653,12 +699,17 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="plain workload: leave out the batched form's object")
+    ap.add_argument("--no-served", action="store_true",
+                    help="plain workload: leave out the served form's object")
     args = ap.parse_args()
     if args.workload in ("sweep", "batched", "served", "frequent"):
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        return {"sweep": run_sweep, "batched": run_batched, "served": run_served,
-                "frequent": run_frequent}[args.workload](args)
+        rc = {"sweep": run_sweep, "batched": run_batched, "served": run_served,
+              "frequent": run_frequent}[args.workload](args)
+        return rc if isinstance(rc, int) else 0
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -780,11 +831,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32" if w == 4 else "u64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": n, "k": k, "p": p, "item_bytes": w,
-                       "zipf_s": wl["s"], "universe": f"2^{wl['log2u']}", "seed": wl["seed"],
-                       "l2": (f"input ({n * w / 2**30:.2f} GiB) larger than L2; no flush"
-                              if n * w > (256 << 20) else "input smaller than L2"),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(wl, world),
             "input_gbs": input_gbs,
             "hbm_frac": input_gbs / hbm,
             "hbm_frac_nominal_8tbs": input_gbs / 8000.0,
@@ -803,6 +850,20 @@ def main():
             "gpu_launches": int(prof["launches"]),
             "clocks": clk,
         }
+        # The batched and served forms beside the plain one (single-GPU runs:
+        # the metric compares the three forms on one GPU).
+        if world == 1 and args.workload == "plain":
+            del x, q
+            torch.cuda.empty_cache()
+            if not args.no_batched:
+                line["batched"] = batched_summary(run_batched(
+                    argparse.Namespace(nstreams=1024, kind="space_saving",
+                                       steps=min(args.steps, 5),
+                                       warmup=max(1, min(args.warmup, 2))), emit=False))
+                torch.cuda.empty_cache()
+            if not args.no_served:
+                line["served"] = served_summary(run_served(
+                    argparse.Namespace(duration=args.duration, kind="space_saving"), emit=False))
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -229,6 +229,32 @@ def pss_tree(items, k: int, p: int) -> list[list[Summary]]:
     return levels
 
 
+def pss_tree_threads(items, k: int, p: int, threads: int | None = None) -> list[list[Summary]]:
+    """pss_tree with its independent calls spread over host threads.
+
+    Level 0 is the p calls of block_summary (one block each, Algorithm 1
+    bounds); every later level is the combines of adjacent pairs of the level
+    below (Algorithm 2), the odd last node carried up unchanged.  Each call is
+    the same single-threaded C++ as pss_tree's (ctypes releases the GIL, so
+    calls on different threads run on different cores); only their
+    scheduling differs, and a CPU test checks that the levels equal
+    pss_tree's."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    a, _ = _items_array(items)
+    threads = threads or min(32, os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        levels = [list(ex.map(lambda r: block_summary(a, k, p, r), range(p)))]
+        while len(levels[-1]) > 1:
+            cur = levels[-1]
+            nxt = list(ex.map(lambda i: combine(cur[2 * i], cur[2 * i + 1], k),
+                              range(len(cur) // 2)))
+            if len(cur) % 2:
+                nxt.append(cur[-1])
+            levels.append(nxt)
+    return levels
+
+
 def query(s: Summary, n: int, k: int) -> Summary:
     """Pruned(global, n, k): entries with count * k > n, canonical order."""
     lib = _load()

@@ -1,0 +1,188 @@
+"""Full-size replays: the GPU path against the oracle at the sizes the
+benchmark runs, every block, every tree node, the root and the query.
+
+The oracle replays the same blocks (Algorithm 1 bounds) and the same binary
+tree of combines (Algorithm 2) on the host, its single-threaded calls spread
+over the host's cores.  The oracle generates its own input on the host; the
+device path consumes a copy of the same bytes.  Everything is integer work:
+comparisons are exact."""
+from __future__ import annotations
+
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1606_04669_gb300.gen import workloads as W
+from tests._helpers import summary_entries
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1606_04669_gb300 as P  # noqa: E402
+
+THREADS = min(32, os.cpu_count() or 1)
+
+
+def to_dev(x: np.ndarray):
+    return torch.from_numpy(x.view(np.int32 if x.dtype == np.uint32 else np.int64)).cuda()
+
+
+def ents(e):
+    return list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist()))
+
+
+def by_item(s: oracle.Summary):
+    o = np.argsort(s.item, kind="stable")
+    return s.item[o], s.count[o], s.err[o]
+
+
+def assert_levels_equal(tree, ref, k):
+    """Every node of every level: entries (device layout is item-sorted), m, n covered."""
+    assert tree.levels == len(ref)
+    for lv, ref_level in enumerate(ref):
+        got = tree.read_level(lv, k)
+        assert len(got) == len(ref_level), lv
+        for j, ((it, ct, er, m, cov), r) in enumerate(zip(got, ref_level)):
+            ri, rc, re = by_item(r)
+            assert np.array_equal(it, ri), f"level {lv} node {j}: items"
+            assert np.array_equal(ct, rc), f"level {lv} node {j}: counts"
+            assert np.array_equal(er, re), f"level {lv} node {j}: errs"
+            assert (m, cov) == (r.m, r.n_covered), f"level {lv} node {j}"
+
+
+def replay(n, k, p, seed, s, log2u):
+    x = oracle.gen_zipf(n, seed=seed, s=s, log2u=log2u, threads=THREADS)
+    ref = oracle.pss_tree_threads(x, k, p, threads=THREADS)
+    xd = to_dev(x)
+    # every level of the tree
+    tree = P.summarize_tree(xd, k, p)
+    assert_levels_equal(tree, ref, k)
+    tree.close()
+    # the call the benchmark times: pss_summarize + pss_query
+    root = ref[-1][0]
+    sm = P.summarize(xd, k, p)
+    e = sm.export()
+    assert ents(e) == summary_entries(root)
+    assert (e.m, e.n_covered) == (root.m, root.n_covered) and root.n_covered == n
+    q = sm.query(n, k)
+    rq = oracle.query(root, n, k)
+    assert ents(q) == summary_entries(rq)
+    sm.close()
+    return rq
+
+
+def test_headline_2p30_every_block_node_root_and_query():
+    # n = 2^30 u32 Zipf(1.1) over [0, 2^24), seed 2, k = 2000, p = 4096:
+    # 4096 block summaries, 12 levels (4095 combines), the root and the query.
+    rq = replay(1 << 30, 2000, 4096, seed=2, s=1.1, log2u=24)
+    assert rq.size == 140  # the k-majority candidates the benchmark reports
+
+
+SWEEP = [(zs, k, 10 + 4 * i_s + i_k) for i_s, zs in enumerate((0.5, 1.0, 1.5, 2.0, 3.0))
+         for i_k, k in enumerate((500, 1000, 2000, 4000))]
+
+
+@pytest.mark.parametrize("zs,k,seed", SWEEP)
+def test_sweep_point_every_block_node_root_and_query(zs, k, seed):
+    # Every point of the skew x k sweep: n = 2^30 u32 over [0, 2^32), p = 4096,
+    # seed = 10 + 4 i_s + i_k (s-major).
+    replay(1 << 30, k, 4096, seed=seed, s=zs, log2u=32)
+
+
+def test_batched_workload_full_size():
+    # The batched workload at full size: 1024 u64 streams (1.1e10 items, seed 3)
+    # in one graph launch with the autotuner's plan.  Every stream's root and
+    # query equal the plain path's with the same k and p, and streams of every
+    # k class (the shortest and longest among them) are replayed by the oracle.
+    from paper_1606_04669_gb300 import autotune
+    specs = W.batched_streams(seed=3, nstreams=1024)
+    items = [P.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, item_bytes=sp.item_bytes,
+                        stream_id=sp.index) for sp in specs]
+    ks = [sp.k for sp in specs]
+    ps = [autotune.plan_blocks(sp.n, sp.k, sp.s) for sp in specs]
+    batch = P.Batch(items, ks, ps=ps, skews=[sp.s for sp in specs])
+    batch.run(use_graph=True)
+    res = batch.results()
+    for i, sp in enumerate(specs):
+        plain = P.summarize(items[i], ks[i], ps[i])
+        e, pe = batch.export(i), plain.export()
+        assert ents(e) == ents(pe) and (e.m, e.n_covered) == (pe.m, pe.n_covered), i
+        assert ents(res[i]) == ents(plain.query(sp.n, ks[i])), i
+        plain.close()
+    sample = set()
+    for k in W.BATCH_KS:
+        idx = [i for i, sp in enumerate(specs) if sp.k == k]
+        idx.sort(key=lambda i: specs[i].n)
+        sample.update((idx[0], idx[len(idx) // 2], idx[-1]))
+    for i in sorted(sample):
+        sp = specs[i]
+        x = oracle.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, width=8, stream=sp.index,
+                            threads=THREADS)
+        root = oracle.pss_tree_threads(x, sp.k, ps[i], threads=THREADS)[-1][0]
+        e = batch.export(i)
+        assert ents(e) == summary_entries(root) and (e.m, e.n_covered) == (root.m, sp.n), i
+        assert ents(res[i]) == summary_entries(oracle.query(root, sp.n, sp.k)), i
+    batch.close()
+
+
+def test_served_workload_k1024_tenants():
+    # The served workload's shape: Poisson arrivals at 2000 requests/s (seed 4),
+    # segments of log-uniform length in [1e4, 1e7] u32 items, 256 tenants
+    # whose k = 1024 summaries stay resident, 16 GB admission budget; half a
+    # second of arrivals (about 1000 requests, 1.4e9 items).  Every request's
+    # segment and tenant answers and every final tenant summary against the
+    # oracle (tenants combined in arrival order); one tenant's requests alone
+    # on a server of their own give the same answers as in the mix.
+    tenants, k = 256, 1024
+    reqs = [dict(id=r.index, arrival=r.arrival, tenant=r.tenant, n=r.n, s=r.s, log2u=r.log2u,
+                 seed=r.seed, stream_id=r.index)
+            for r in W.served_requests(seed=4, rate=2000.0, duration=0.5)]
+    srv = P.Server(tenants, k, budget_bytes=16 << 30, max_batch=256, max_inflight=4096)
+    srv.submit(reqs)
+    srv.start()
+    srv.wait(600)
+    comps = {c["id"]: c for c in srv.poll()}
+    res = {r["id"]: srv.result(r["id"]) for r in reqs}
+    final = {t: srv.tenant_export(t) for t in range(tenants)}
+    srv.close()
+    assert len(comps) == len(reqs) and all(c["status"] == 0 for c in comps.values())
+
+    def segment(r):
+        x = oracle.gen_zipf(r["n"], seed=r["seed"], s=r["s"], log2u=r["log2u"],
+                            stream=r["stream_id"])
+        p = P.plan_blocks(r["n"], k, 4, r["s"])
+        root = oracle.pss_tree(x, k, p)[-1][0]
+        return root, oracle.query(root, r["n"], k)
+
+    with ThreadPoolExecutor(max_workers=THREADS) as ex:
+        segs = dict(zip([r["id"] for r in reqs], ex.map(segment, reqs)))
+    tenant = {t: oracle.Summary(np.zeros(0, np.uint64), np.zeros(0, np.uint64),
+                                np.zeros(0, np.uint64), 0, 0) for t in range(tenants)}
+    for r in sorted(reqs, key=lambda r: r["arrival"]):
+        seg, segq = segs[r["id"]]
+        tenant[r["tenant"]] = oracle.combine(tenant[r["tenant"]], seg, k)
+        tq = oracle.query(tenant[r["tenant"]], tenant[r["tenant"]].n_covered, k)
+        got_seg, got_ten = res[r["id"]]
+        assert ents(got_seg) == summary_entries(segq), r["id"]
+        assert ents(got_ten) == summary_entries(tq), r["id"]
+        assert comps[r["id"]]["tenant_items"] == tenant[r["tenant"]].n_covered
+    for t in range(tenants):
+        assert ents(final[t]) == summary_entries(tenant[t]), t
+        assert (final[t].m, final[t].n_covered) == (tenant[t].m, tenant[t].n_covered), t
+    # alone vs in the mix: the busiest tenant's requests on their own server
+    busiest = max(range(tenants), key=lambda t: sum(1 for r in reqs if r["tenant"] == t))
+    alone = [r for r in reqs if r["tenant"] == busiest]
+    srv2 = P.Server(tenants, k, budget_bytes=16 << 30, max_batch=1)
+    srv2.submit(alone)
+    srv2.start()
+    srv2.wait(600)
+    for r in alone:
+        a_seg, a_ten = srv2.result(r["id"])
+        assert ents(a_seg) == ents(res[r["id"]][0]) and ents(a_ten) == ents(res[r["id"]][1])
+    srv2.close()

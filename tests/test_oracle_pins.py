@@ -229,6 +229,21 @@ def test_tree_levels(n, k, p):
     assert all(c * k > n for c in q.count.tolist())
 
 
+@pytest.mark.parametrize("n,k,p,threads", [(200_000, 50, 37, 4), (90_000, 300, 16, 3),
+                                           (5, 4, 9, 2), (0, 3, 4, 2), (40_000, 2, 1, 2)])
+def test_threaded_tree_equals_tree(n, k, p, threads):
+    # The threaded driver used for full-size replays only reschedules the
+    # single-threaded calls: every node of every level equals pss_tree's.
+    x = oracle.gen_zipf(n, seed=70 + p, s=1.1, log2u=16)
+    ref = oracle.pss_tree(x, k, p)
+    got = oracle.pss_tree_threads(x, k, p, threads=threads)
+    assert [len(l) for l in got] == [len(l) for l in ref]
+    for lg, lr in zip(got, ref):
+        for g, r in zip(lg, lr):
+            assert summary_entries(g) == summary_entries(r)
+            assert (g.m, g.n_covered) == (r.m, r.n_covered)
+
+
 def test_p1_is_sequential():
     rng = np.random.default_rng(17)
     x = _rand_stream(rng, 3000, 500)

@@ -241,41 +241,6 @@ def test_fuzz_small_universes():
         compare_tree(x, k, p)
 
 
-@pytest.mark.parametrize("zs,k,seed", [(0.5, 4000, 13), (3.0, 500, 26)])
-def test_sweep_corners_sampled_blocks_and_bounds(zs, k, seed):
-    # The skew x k sweep at full size: n = 2^30 u32 over [0, 2^32), p = 4096,
-    # seed = 10 + 4 i_s + i_k.  Sampled blocks against the oracle; the root
-    # against exact frequencies of the whole stream.
-    n, p = 1 << 30, 4096
-    x = P.gen_zipf(n, seed=seed, s=zs, log2u=32)
-    tree = P.summarize_tree(x, k, p)
-    level0 = tree.read_level(0, k)
-    for r in (0, 1234, 4095):
-        lo, hi = oracle.block_bounds(n, p, r)
-        xr = oracle.gen_zipf(hi - lo, seed=seed, s=zs, log2u=32, start=lo, threads=8)
-        ref = oracle.space_saving(xr, k)
-        ent, m, cov = node_entries(level0[r])
-        assert canonical(ent) == summary_entries(ref), r
-        assert (m, cov) == (ref.m, hi - lo)
-    del level0
-    root = tree.root()
-    e = root.export()
-    tree.close()
-    vals, cnts = torch.unique(x.view(torch.int32).to(torch.int64) & 0xFFFFFFFF,
-                              return_counts=True)
-    vals = vals.cpu().numpy().astype(np.uint64)
-    cnts = cnts.cpu().numpy().astype(np.uint64)
-    pos = np.searchsorted(vals, e.item)
-    found = (pos < len(vals)) & (vals[np.minimum(pos, len(vals) - 1)] == e.item)
-    f = np.where(found, cnts[np.minimum(pos, len(vals) - 1)], 0)
-    assert np.all(e.count - e.err <= f) and np.all(f <= e.count)
-    stored = np.zeros(len(vals), bool)
-    stored[pos[found]] = True
-    assert cnts[~stored].max(initial=0) <= e.m
-    q = root.query(n, k)
-    assert set(vals[cnts * np.uint64(k) > np.uint64(n)].tolist()) <= set(q.item.tolist())
-
-
 @pytest.fixture
 def warp_kmax():
     prev = P.set_warp_kmax(256)
