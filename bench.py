@@ -63,6 +63,11 @@ WORKLOADS = {
         desc="round-kernel shape: n=2^28 uint32 Zipf(s=1.0) over [0,2^32), seed 13; k=256; "
              "p=8192 blocks of 32768 items (one warp per block); binary merge tree; query n/k",
         n=1 << 28, w=4, s=1.0, log2u=32, seed=13, k=256, p=8192),
+    "warp_k64": dict(
+        desc="warp-kernel shape: n=2^27 uint32 Zipf(s=1.1) over [0,2^24), seed 2; k=64; "
+             "p=4096 blocks of 32768 items (one warp per block, counters in registers); binary "
+             "merge tree; query n/k",
+        n=1 << 27, w=4, s=1.1, log2u=24, seed=2, k=64, p=4096),
     "small": dict(
         desc="plain single stream: n=2^20 uint32 Zipf(s=1.1) over [0,2^20), seed 1; k=100; p=8; "
              "binary merge tree; query n/k",
