@@ -265,6 +265,27 @@ uint32_t pss_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hin
  * class 2.0), 2^16 above). */
 uint32_t pss_frequent_plan_blocks(uint64_t n, uint32_t k, int item_bytes, double skew_hint);
 
+/* The planner's skew estimate for streams the caller knows nothing about (no
+ * counterpart in the paper: it only steers the kernel choice and block
+ * length, never a result).  For each stream, P = the number of pairs of
+ * equal items among its first S = min(n[i], sample) items, counted exactly
+ * on the device; skew_out[i] = pss_skew_of_pairs(P, S) and, if pairs_out is
+ * not NULL, pairs_out[i] = P.  Both are pure functions of the stream's bytes,
+ * so a plan built from them can be replayed.
+ *   d_items: nstreams device pointers (NULL allowed where n[i] == 0);
+ *   item_bytes 4 or 8; 2 <= sample <= 4096.
+ * Allocates a small stream-ordered buffer; synchronizes stream.  PSS_EINVAL
+ * on bad arguments. */
+int pss_estimate_skew(const void* const* d_items, const uint64_t* n, uint32_t nstreams,
+                      int item_bytes, uint32_t sample, void* stream, double* skew_out,
+                      uint64_t* pairs_out);
+
+/* Host only: the Zipf exponent s whose collision rate over [0, 2^32),
+ * H(2^32, 2s) / H(2^32, s)^2 (H(U, s) = sum of r^-s for r = 1..U), equals
+ * pairs / C(sample, 2), by interpolation in a table for s = 0.30 .. 4.00
+ * (clamped to that range; 0.0 = unknown when sample < 2). */
+double pss_skew_of_pairs(uint64_t pairs, uint64_t sample);
+
 /* Plan and allocate a batch (device memory for every stream's tree, task
  * lists, results).  The streams' item buffers are borrowed for the batch's
  * lifetime.  Synchronizes stream. */

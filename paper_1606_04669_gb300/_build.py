@@ -27,7 +27,7 @@ def _sources() -> list[str]:
 
 
 def _deps() -> list[str]:
-    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh"))
+    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.inc"))
             + [os.path.join(HERE, "gen", "pss_zipf.h"),
                os.path.join(HERE, "..", "include", "pss.h"), __file__])
 

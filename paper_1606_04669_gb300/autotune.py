@@ -7,6 +7,12 @@ and never of load; the plan is recorded so that the oracle can replay it.
 produced by `sweep()` on a GB300 (TABLE below; the library's own
 `pss_plan_blocks` is the default when no table is used).
 
+The skew class need not come from the caller: `pss_estimate_skew`
+(P.estimate_skew) estimates each stream's Zipf exponent on the device from
+the pairs of equal items among its first 4096 items -- an exact count, so the
+plan stays a pure function of the stream's bytes and can be replayed.  The
+batched benchmark plans from those estimates, not from the generator's s.
+
 What is tuned and what is not:
   * block length (hence p): tuned here, per (k class, skew class);
   * summarize kernel (window-parallel CTA kernel, or one warp per block with

@@ -154,6 +154,9 @@ SIGNATURES = {
     "pss_server_tenant_export": (ctypes.c_int, [vp, u32, ctypes.POINTER(Entry), u32, u32p, u64p,
                                                 u64p]),
     "pss_server_destroy": (None, [vp]),
+    "pss_estimate_skew": (ctypes.c_int, [ctypes.POINTER(vp), u64p, u32, ctypes.c_int, u32, vp,
+                                         ctypes.POINTER(ctypes.c_double), u64p]),
+    "pss_skew_of_pairs": (ctypes.c_double, [u64, u64]),
     "pss_set_warp_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
     "pss_set_round_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
     "pss_plan_kernel": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int]),
@@ -557,6 +560,29 @@ def plan_blocks(n: int, k: int, item_bytes: int = 4, skew_hint: float = 0.0,
     pss_frequent_plan_blocks for the Frequent summary)."""
     fn = load().pss_frequent_plan_blocks if frequent else load().pss_plan_blocks
     return int(fn(int(n), int(k), int(item_bytes), float(skew_hint)))
+
+
+def estimate_skew(items, sample: int = 4096, stream=None):
+    """pss_estimate_skew: (skews, pairs) per stream, from the pairs of equal
+    items among each stream's first min(n, sample) items."""
+    if not items:
+        return [], []
+    widths = {_check_items(t) for t in items}
+    if len(widths) != 1:
+        raise ValueError("every stream must have the same item width")
+    ns = len(items)
+    ptrs = (vp * ns)(*[t.data_ptr() for t in items])
+    n = (ctypes.c_uint64 * ns)(*[t.numel() for t in items])
+    sk = (ctypes.c_double * ns)()
+    pr = (ctypes.c_uint64 * ns)()
+    _check(load().pss_estimate_skew(ptrs, n, ns, widths.pop(), int(sample),
+                                    vp(_stream_handle(stream)), sk, pr), "pss_estimate_skew")
+    return list(sk), [int(v) for v in pr]
+
+
+def skew_of_pairs(pairs: int, sample: int) -> float:
+    """pss_skew_of_pairs (host only)."""
+    return float(load().pss_skew_of_pairs(int(pairs), int(sample)))
 
 
 class Batch:

@@ -104,3 +104,52 @@ def test_batch_kernel_choice_by_skew(kmax):
         batch.close()
     finally:
         P.set_warp_kmax(prev)
+
+
+def _pairs_of(x: np.ndarray) -> int:
+    _, c = np.unique(x, return_counts=True)
+    return int((c.astype(np.int64) * (c - 1) // 2).sum())
+
+
+@pytest.mark.parametrize("width", [4, 8])
+def test_estimate_skew_counts_pairs_exactly(width):
+    # The device count of equal pairs in each stream's first min(n, 4096)
+    # items equals a numpy recount of the same prefix; the skew is
+    # pss_skew_of_pairs of that count (so a pure function of the bytes).
+    xs = [oracle.gen_zipf(n, seed=31, s=s, log2u=32, width=width, stream=i)
+          for i, (n, s) in enumerate([(100_000, 0.8), (5000, 1.3), (4096, 2.0), (4095, 1.1),
+                                      (37, 3.0), (1, 1.5), (0, 1.5)])]
+    dt = np.uint32 if width == 4 else np.uint64
+    xs += [np.full(9000, np.iinfo(dt).max, dt), np.arange(9000, dtype=dt)]
+    dev = [torch.from_numpy(x.view(np.int32 if width == 4 else np.int64)).cuda() for x in xs]
+    skews, pairs = P.estimate_skew(dev)
+    for x, sk, pr in zip(xs, skews, pairs):
+        S = min(len(x), 4096)
+        assert pr == _pairs_of(x[:S])
+        assert sk == P.skew_of_pairs(pr, S)
+    assert pairs[-2] == 4096 * 4095 // 2 and pairs[-1] == 0
+    # the same bytes give the same estimate again
+    assert P.estimate_skew(dev) == (skews, pairs)
+
+
+def test_batch_planned_from_estimated_skew():
+    # A batch planned from the estimated skews (block lengths and kernel
+    # choice) gives every stream the result of the plain path with the plan's
+    # p, and the oracle's.
+    from paper_1606_04669_gb300 import autotune
+    specs = W.batched_streams(seed=3, nstreams=24, lo=1e3, hi=4e5)
+    items = [P.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, item_bytes=8,
+                        stream_id=sp.index) for sp in specs]
+    est, _ = P.estimate_skew(items)
+    assert all(abs(e - sp.s) < 0.25 for e, sp in zip(est, specs) if sp.n >= 4096)
+    ps = [autotune.plan_blocks(sp.n, sp.k, e) for sp, e in zip(specs, est)]
+    batch = P.Batch(items, [sp.k for sp in specs], ps=ps, skews=est)
+    batch.run(use_graph=True)
+    res = batch.results()
+    for i, sp in enumerate(specs):
+        x = oracle.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, width=8, stream=sp.index)
+        root, rq = oracle.parallel_space_saving(x, sp.k, ps[i])
+        e = batch.export(i)
+        assert ents(e) == summary_entries(root) and (e.m, e.n_covered) == (root.m, sp.n), i
+        assert ents(res[i]) == summary_entries(rq), i
+    batch.close()

@@ -97,7 +97,8 @@ def test_sweep_point_every_block_node_root_and_query(zs, k, seed):
 
 def test_batched_workload_full_size():
     # The batched workload at full size: 1024 u64 streams (1.1e10 items, seed 3)
-    # in one graph launch with the autotuner's plan.  Every stream's root and
+    # in one graph launch with the autotuner's plan on skews estimated from the
+    # data (pss_estimate_skew).  Every stream's root and
     # query equal the plain path's with the same k and p, and streams of every
     # k class (the shortest and longest among them) are replayed by the oracle.
     from paper_1606_04669_gb300 import autotune
@@ -105,8 +106,9 @@ def test_batched_workload_full_size():
     items = [P.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, item_bytes=sp.item_bytes,
                         stream_id=sp.index) for sp in specs]
     ks = [sp.k for sp in specs]
-    ps = [autotune.plan_blocks(sp.n, sp.k, sp.s) for sp in specs]
-    batch = P.Batch(items, ks, ps=ps, skews=[sp.s for sp in specs])
+    est, _ = P.estimate_skew(items)  # the plan the benchmark uses: skews from the data
+    ps = [autotune.plan_blocks(sp.n, sp.k, e) for sp, e in zip(specs, est)]
+    batch = P.Batch(items, ks, ps=ps, skews=est)
     batch.run(use_graph=True)
     res = batch.results()
     for i, sp in enumerate(specs):

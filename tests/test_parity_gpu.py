@@ -300,3 +300,19 @@ def test_large_k_merge_and_resident_limits():
     with pytest.raises(P.PssError) as ei:
         P.Server(2, P.PSS_MAX_K_RESIDENT + 1)
     assert ei.value.code == P.PSS_EINVAL
+
+
+@pytest.mark.parametrize("w,off", [(4, 1), (4, 2), (4, 3), (8, 1)])
+def test_input_pointer_offsets(w, off):
+    # Windows are copied in 16-byte pieces aligned to global memory, so every
+    # offset of the input pointer within 16 bytes (a view starting `off`
+    # items into an aligned tensor) is compared with the oracle, with blocks,
+    # cut windows and the stream's end at every offset as well.
+    x = oracle.gen_zipf(300_001 + off, seed=60 + off, s=1.0, log2u=20, width=w)
+    dev = to_dev(x)[off:]
+    assert dev.data_ptr() % 16 == off * w
+    for k, p in ((700, 7), (2000, 3), (100, 1)):
+        e = P.summarize(dev, k, p).export()
+        r, _ = oracle.parallel_space_saving(x[off:], k, p)
+        assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == summary_entries(r)
+        assert (e.m, e.n_covered) == (r.m, r.n_covered)
