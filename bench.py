@@ -80,15 +80,15 @@ WORKLOADS = {
 # block shape it was measured at.  Traffic grows with the number of blocks, so
 # a launch of p such blocks moves p times the per-block bytes.
 #   ss_block_kernel: profiles/ss_block_kernel_wave_k2000.md, 304 blocks of
-#     262144 u32 items, k = 2000 -> 318.87 MB read + 3.97 MB written.
+#     262144 u32 items, k = 2000 -> 319.08 MB read + 3.83 MB written.
 #   ssr_block_kernel: profiles/ssr_block_kernel_k256.md, 8192 blocks of 32768
 #     u32 items, k = 256 -> 1077.7 MB read + 32.5 MB written.
 #   frequent_block_kernel: profiles/frequent_block_kernel_wave_k2000.md, 1368
 #     blocks of 262144 u32 items, k = 2000 -> 1434.60 MB read + 3.76 MB written.
 TRAFFIC = {
     "ss_block_kernel": {"src": "summarize.cu",
-                        "sha1": "6e7eb939e5cac32d736ed5dbb9bfbc8115e6ad70",
-                        "bytes_per_block": (318.87e6 + 3.97e6) / 304, "block_items": 262144,
+                        "sha1": "54d7d46506036fbb4a3457b2a5197708fb5cf7bd",
+                        "bytes_per_block": (319.075e6 + 3.828e6) / 304, "block_items": 262144,
                         "k": 2000, "w": 4},
     "ssr_block_kernel": {"src": "summarize_round.cu",
                          "sha1": "0e210092b09dbb8f0a1656928b774624097af347",

@@ -46,6 +46,7 @@
 // Output: the block's summary sorted by item ascending, with size, minimum m
 // (the minimum count if k counters are in use, else 0) and the block length.
 #include <atomic>
+#include <type_traits>
 
 #include "pss_internal.cuh"
 #include "pss_kernels.cuh"
@@ -59,6 +60,7 @@ constexpr uint16_t NONE16 = 0xFFFFu;
 constexpr uint32_t PEND = 0x8000u;  // cell reference of a pending item: PEND | window position
 constexpr int HMAX = 256;     // skipped members tracked per window
 constexpr int CONVMAX = 32;   // conversions tracked per window (one per lane)
+constexpr uint32_t EVR_HEAVY = 512;  // events per 1024 items of a miss-heavy stream
 
 template <typename ItemT>
 struct ItemOps;
@@ -95,6 +97,7 @@ struct SSState {
   uint32_t norig;        // events (not conversions) before the cut
   uint32_t exhausted;
   uint32_t maxdisp;      // largest distance of an item past its second bucket
+  uint32_t evn, evc;     // the last cut window: events before its cut, and the cut (0: none)
   uint32_t status;
 };
 
@@ -493,7 +496,9 @@ struct SSBlock {
     for (uint32_t i = c0; i < c1; ++i) mn = min(mn, s.cnt[i]);
     for (uint32_t w = threadIdx.x; w < 2 * s.NBW; w += BS) s.ovf[w] = 0;
     if (threadIdx.x == 0) S->maxdisp = 0;
-    mn = block_min_u32<BS>(mn, s.wsum);
+    // in the half of the scan buffer the window's last scan did not use: no
+    // barrier separates that scan's reads of its own half from these writes
+    mn = block_min_u32<BS>(mn, s.wsum + (par ? (BS / 32 + 1) : 0));
     // overflow bits and distances of the counters as they are placed now
     for (uint32_t i = c0; i < c1; ++i) {
       const ItemT x = s.item[i];
@@ -660,7 +665,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   B.reset_window_scratch();
   if (tid == 0) {
     S.m = 0; S.head = 0; S.list_len = 0; S.log_len = 0; S.used = 0; S.full = 0;
-    S.epoch_start = 0; S.maxdisp = 0; S.status = 0;
+    S.epoch_start = 0; S.maxdisp = 0; S.status = 0; S.evn = 0; S.evc = 0;
   }
   __syncthreads();
 
@@ -668,10 +673,21 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
   // the next window is copied in as soon as its start is known.
   uint32_t t0 = 0, stall = 0;
   if (len) copy_window<ItemT, BS, IPT>(s.wbuf, xs, 0, len);
-  while (t0 < len) {
-    const uint32_t nact = min(W, len - t0);
-    cp_wait();
-    __syncthreads();
+  // One window; false when the block makes no progress.  It is compiled
+  // twice: HEAVY for windows of miss-heavy streams (EVR_HEAVY or more events
+  // per 1024 items), where windows end soon after they start because the
+  // bucket list runs out, and the plain form for the rest, which then carries
+  // none of the miss-heavy code.  In HEAVY windows the window is sized to the
+  // items the list's remaining entries last at that rate, with an eighth to
+  // spare (any length gives the same result; items looked up past the cut
+  // would be looked up again), and missing items claim cells at once.
+  auto window = [&](auto mode) -> bool {
+    constexpr bool HEAVY = decltype(mode)::value;
+    uint32_t nact = min(W, len - t0);
+    if constexpr (HEAVY) {
+      const uint32_t want = (S.list_len - S.head) * S.evc * 9u / (S.evn * 8u) + 32u;
+      nact = min(nact, max(want, W / 4));
+    }
     ItemT x[IPT];
 #pragma unroll
     for (int j = 0; j < IPT; ++j) x[j] = s.wbuf[tid * IPT + j];
@@ -703,6 +719,39 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       }
 #pragma unroll
       for (int j = 0; j < IPT; ++j) sl[j] = B.match4(hc[j], tg[j], x[j]);
+      // In a HEAVY window a missing item whose first bucket has a free cell,
+      // and none of whose items lives outside it, claims there at once:
+      // the first step of find_or_claim's walk (a cell seen free and since
+      // claimed fails the CAS and is compared, as in the walk).  Elsewhere
+      // the packed walk below runs the few missing lanes on full warps.
+      if constexpr (HEAVY) {
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+          const uint32_t rel = tid * IPT + j;
+          if (sl[j] != -1 || rel >= nact) continue;
+          const uint32_t h = ItemOps<ItemT>::h1(x[j]), b = h >> s.nbshift;
+          if (B.ovf_bit(0, b)) continue;
+          const uint32_t tag = B.tag_of(h), val = (tag << 16) | PEND | rel;
+          const uint4 cv = *(const uint4*)&s.cell[b * 4];
+          const uint32_t c4[4] = {cv.x, cv.y, cv.z, cv.w};
+          for (int i = 0; i < 4; ++i) {
+            uint32_t c = c4[i];
+            if (c == 0u) {
+              c = atomicCAS(&s.cell[b * 4 + i], 0u, val);
+              if (c == 0u) {
+                s.pcell[rel] = (uint16_t)(b * 4 + i);
+                sl[j] = -2 - (int)rel;
+                break;
+              }
+            }
+            const int r = B.cell_match(c, tag, x[j]);
+            if (r != -1) {
+              sl[j] = r;
+              break;
+            }
+          }
+        }
+      }
       // the rest (past the first bucket, or not in the table), packed onto
       // the warp's lanes; results by position in evpid (free until P2):
       // slot, or PEND | pid
@@ -780,7 +829,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
         atomicMax(&s.touch[hot], hot_t);
       }
       t0 += nact;
-      continue;
+      return true;
     }
 
     // ---- P2: first occurrences of the misses (the events), ranked by position
@@ -843,18 +892,104 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     }
     __syncthreads();
 
-    // ---- P4: one warp walks the members hit in this window (skips, conversions)
+    // ---- P4: one warp decides the members hit in this window (skips, conversions).
+    // Member j (in list order, candidate index a, first hit at h) is reached by
+    // the merged event e = a - s, s the skips before it; each earlier member was
+    // skipped or converted, so exactly j - s conversions precede e.  Hence it is
+    // reached iff a - j < M, and its event time lies in [T[a - j], T[a]] (T the
+    // original events' times; the upper end needs a < M).  A member whose h lies
+    // below that range is skipped, above it converted, whatever came before; a
+    // batch of 32 members with none in between is decided at once.  Otherwise the
+    // batch (and the rest) takes the walk one member at a time.
     if (full && M > 0 && warp == 0) {
       const uint32_t nv = S.nvalid, nh = S.nhit;
+      const unsigned below = (1u << lane) - 1u;
       uint32_t nskip = 0, nconv = 0, astop = nv;
-      uint32_t ct = NONE32, clo = 0, cs = 0;  // conversion held by this lane, sorted by time
-      bool done = false;
+      uint32_t ct = NONE32, clo = 0, cs = 0;  // walk: conversion held by this lane, sorted by time
+      bool done = false, walk = false;
       for (uint32_t hb = 0; hb < nh && !done; hb += 32) {
        // this batch's hit members, one per lane
        uint32_t a_l = 0, hq_l = 0;
        if (hb + lane < nh) {
          a_l = s.hitc[hb + lane];
          hq_l = s.hfirst[s.cand[a_l]];
+       }
+       if (!walk && nh - hb >= 2u) {  // a lone member: the walk costs less
+         const uint32_t nb0 = min(32u, nh - hb), j = hb + lane;
+         const unsigned ub = __ballot_sync(0xffffffffu, lane < nb0 && a_l - j >= M);
+         const uint32_t lim = ub ? (uint32_t)__ffs(ub) - 1u : nb0;  // reached members
+         bool amb = false, skp = false;
+         if (lane < lim) {
+           if (a_l >= M) {
+             amb = true;
+           } else {
+             const uint32_t tlo = s.rankpos[a_l - j], thi = s.rankpos[a_l];
+             skp = hq_l < tlo;
+             amb = !skp && hq_l <= thi;
+           }
+         }
+         const unsigned bskip = __ballot_sync(0xffffffffu, lane < lim && skp);
+         const unsigned bconv = __ballot_sync(0xffffffffu, lane < lim && !skp && !amb);
+         const uint32_t ns = __popc(bskip), nc = __popc(bconv);
+         if (!__any_sync(0xffffffffu, amb) && nskip + ns <= (uint32_t)HMAX &&
+             nconv + nc <= (uint32_t)CONVMAX) {
+           if ((bskip >> lane) & 1u) s.skipl[nskip + __popc(bskip & below)] = (uint16_t)a_l;
+           nskip += ns;
+           if (nc) {
+             const bool cv = (bconv >> lane) & 1u;
+             uint32_t lo = 0, rk = 0;
+             if (cv) {  // original events before the conversion's time
+               uint32_t hi = M;
+               while (lo < hi) {
+                 const uint32_t mid = (lo + hi) >> 1;
+                 if (s.rankpos[mid] < hq_l) lo = mid + 1;
+                 else hi = mid;
+               }
+             }
+             for (unsigned mm = bconv; mm; mm &= mm - 1) {  // time order among the new ones
+               const uint32_t t2 = __shfl_sync(0xffffffffu, hq_l, __ffs(mm) - 1);
+               rk += t2 < hq_l ? 1u : 0u;
+             }
+             // merge with the conversions of earlier batches (time order)
+             uint32_t ot = NONE32, olo = 0, osrc = 0, ork = lane;
+             if (lane < nconv) {
+               ot = s.convt[lane];
+               olo = s.convlo[lane];
+               osrc = s.convsrc[lane];
+             }
+             for (uint32_t c = 0; c < nconv; ++c) {
+               const uint32_t t2 = __shfl_sync(0xffffffffu, ot, c);
+               rk += t2 < hq_l ? 1u : 0u;
+             }
+             for (unsigned mm = bconv; mm; mm &= mm - 1) {
+               const uint32_t t2 = __shfl_sync(0xffffffffu, hq_l, __ffs(mm) - 1);
+               ork += t2 < ot ? 1u : 0u;
+             }
+             __syncwarp();
+             if (lane < nconv) {
+               s.convt[ork] = (uint16_t)ot;
+               s.convlo[ork] = (uint16_t)olo;
+               s.convsrc[ork] = (uint16_t)osrc;
+             }
+             if (cv) {
+               s.convt[rk] = (uint16_t)hq_l;
+               s.convlo[rk] = (uint16_t)lo;
+               s.convsrc[rk] = (uint16_t)a_l;
+             }
+             __syncwarp();
+             nconv += nc;
+           }
+           if (ub) done = true;  // later members are not reached either
+           continue;
+         }
+       }
+       if (!walk) {  // the walk from here: this lane's conversion of the list so far
+         walk = true;
+         if (lane < nconv) {
+           ct = s.convt[lane];
+           clo = s.convlo[lane];
+           cs = s.convsrc[lane];
+         }
        }
        const uint32_t nb_ = min(32u, nh - hb);
        for (uint32_t ii = 0; ii < nb_; ++ii) {
@@ -908,7 +1043,7 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
         }
        }
       }
-      if (lane < nconv) {
+      if (walk && lane < nconv) {
         s.convt[lane] = (uint16_t)ct;
         s.convlo[lane] = (uint16_t)clo;
         s.convsrc[lane] = (uint16_t)cs;
@@ -1089,6 +1224,10 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
       }
     }
     stall = cut ? 0u : stall + 1u;
+    if (tid == 0 && cut) {
+      S.evn = norig;
+      S.evc = cut;
+    }
     if (need) {
       const bool clobbered = B.rebuild_list(need == 2, t0 + cut);
       if (S.maxdisp > 2) B.rebuild_table(status);
@@ -1096,9 +1235,16 @@ __device__ void summarize_block(const ItemT* __restrict__ items, u64 n, uint32_t
     }
     if (stall >= 3) {
       status |= ST_NOPROGRESS;
-      break;
+      return false;
     }
     t0 += cut;
+    return true;
+  };
+  while (t0 < len) {
+    cp_wait();
+    __syncthreads();
+    const bool heavy = S.full && S.evc && S.evn * 1024u >= EVR_HEAVY * S.evc;
+    if (!(heavy ? window(std::true_type{}) : window(std::false_type{}))) break;
   }
   cp_wait();  // a copy may be in flight after an error exit
 
