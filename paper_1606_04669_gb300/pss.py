@@ -590,11 +590,18 @@ class Batch:
 
     items: CUDA tensors of one item width (borrowed for the batch's life);
     ks: counters per stream; ps: blocks per stream (None / 0 = planned);
+    skews: per-stream skew hints for the planner, None (unknown), or
+    "estimate" (pss_estimate_skew on each stream's first 4096 items);
     frequent: Frequent (Misra–Gries) summaries instead of Space Saving."""
 
     def __init__(self, items, ks, ps=None, skews=None, stream=None, frequent: bool = False):
         if not items:
             raise ValueError("a batch needs at least one stream")
+        if isinstance(skews, str):
+            if skews != "estimate":
+                raise ValueError('skews must be a sequence, None or "estimate"')
+            skews, _ = estimate_skew(items, stream=stream)
+        self.skews = list(skews) if skews is not None else None
         widths = {_check_items(t) for t in items}
         if len(widths) != 1:
             raise ValueError("every stream of a batch must have the same item width")

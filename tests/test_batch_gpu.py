@@ -153,3 +153,23 @@ def test_batch_planned_from_estimated_skew():
         assert ents(e) == summary_entries(root) and (e.m, e.n_covered) == (root.m, sp.n), i
         assert ents(res[i]) == summary_entries(rq), i
     batch.close()
+
+
+def test_batch_skews_estimate_option():
+    # Batch(skews="estimate") plans from pss_estimate_skew: the same plan as
+    # passing the estimates by hand.
+    specs = W.batched_streams(seed=3, nstreams=6, lo=1e4, hi=2e5)
+    items = [P.gen_zipf(sp.n, seed=sp.seed, s=sp.s, log2u=sp.log2u, item_bytes=8,
+                        stream_id=sp.index) for sp in specs]
+    ks = [sp.k for sp in specs]
+    est, _ = P.estimate_skew(items)
+    a = P.Batch(items, ks, skews="estimate")
+    b = P.Batch(items, ks, skews=est)
+    assert a.plan() == b.plan() and a.skews == est
+    a.run()
+    b.run()
+    assert all(ents(x) == ents(y) for x, y in zip(a.results(), b.results()))
+    a.close()
+    b.close()
+    with pytest.raises(ValueError):
+        P.Batch(items, ks, skews="guess")
