@@ -87,7 +87,7 @@ WORKLOADS = {
 #     blocks of 262144 u32 items, k = 2000 -> 1434.60 MB read + 3.76 MB written.
 TRAFFIC = {
     "ss_block_kernel": {"src": "summarize.cu",
-                        "sha1": "54d7d46506036fbb4a3457b2a5197708fb5cf7bd",
+                        "sha1": "5305902fae5dfee1654cf886c8667b258eddb4d9",
                         "bytes_per_block": (319.075e6 + 3.828e6) / 304, "block_items": 262144,
                         "k": 2000, "w": 4},
     "ssr_block_kernel": {"src": "summarize_round.cu",

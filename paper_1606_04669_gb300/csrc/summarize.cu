@@ -24,11 +24,14 @@
 //   * event e (in time order) evicts the (e + s)-th bucket member, s being the
 //     number of members before it that were "skipped" (hit before their turn).
 //     Only members hit inside the window can be skipped or converted; one warp
-//     walks just those, in list order, deciding each with the time of the
-//     event that reaches it.  Every other assignment is arithmetic.
+//     decides just those, in list order, each with the time of the event that
+//     reaches it (32 at once where bounds on that time settle every one of
+//     them, else one at a time).  Every other assignment is arithmetic.
 //   * the window is cut only where the bucket runs out (or a fill or a
 //     per-window capacity ends): everything before the cut is exact, the rest
-//     is processed again from the new state.
+//     is processed again from the new state.  In miss-heavy streams, where
+//     that happens soon after every start, windows are sized to the bucket's
+//     expected end instead (the window body is compiled for both kinds).
 //
 // Table: item -> counter slot in buckets of four 32-bit cells (16-bit tag,
 // slot + 1) read with one 128-bit shared load.  Each item has two buckets
