@@ -14,6 +14,9 @@
 //     all counters — each lane keeps the minimum of its own CPL counters, two
 //     warp min-reductions (count, then touch among the minimum counts) find
 //     the lane; touches of distinct counters differ, so the victim is unique.
+//     In a block of fewer than 2^16 items every count and touch fits in 16
+//     bits, so (count << 16 | touch) orders the counters the same way and one
+//     reduction of that key finds the victim (PACK).
 // Output: the block's summary sorted by item ascending (rank of each entry =
 // number of smaller items), minimum m (if k counters are in use, else 0) and
 // the block length.
@@ -27,7 +30,7 @@ namespace {
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr int WS_WPB = 4;  // warps (blocks in flight) per CTA
 
-template <typename ItemT, int CPL>
+template <typename ItemT, int CPL, bool PACK>
 __device__ void warp_summarize(const ItemT* __restrict__ items, u64 n, uint32_t p, uint32_t r,
                                const SetView<ItemT>& out, uint32_t node) {
   const uint32_t lane = threadIdx.x & 31;
@@ -64,7 +67,13 @@ __device__ void warp_summarize(const ItemT* __restrict__ items, u64 n, uint32_t 
     lt = NONE;
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
-      if (cn[c] && (cn[c] < lc || (cn[c] == lc && tc[c] < lt))) {
+      if constexpr (PACK) {  // lc holds the packed key
+        const uint32_t key = cn[c] ? (cn[c] << 16) | tc[c] : NONE;
+        if (key < lc) {
+          lc = key;
+          li = c;
+        }
+      } else if (cn[c] && (cn[c] < lc || (cn[c] == lc && tc[c] < lt))) {
         lc = cn[c];
         lt = tc[c];
         li = c;
@@ -111,9 +120,15 @@ __device__ void warp_summarize(const ItemT* __restrict__ items, u64 n, uint32_t 
         ++used;
         if (used == k) local_min();
       } else {
-        const uint32_t mc = __reduce_min_sync(0xffffffffu, lc);
-        const uint32_t mt = __reduce_min_sync(0xffffffffu, lc == mc ? lt : NONE);
-        if (lc == mc && lt == mt) {
+        bool victim;
+        if constexpr (PACK) {
+          victim = lc == __reduce_min_sync(0xffffffffu, lc);
+        } else {
+          const uint32_t mc = __reduce_min_sync(0xffffffffu, lc);
+          const uint32_t mt = __reduce_min_sync(0xffffffffu, lc == mc ? lt : NONE);
+          victim = lc == mc && lt == mt;
+        }
+        if (victim) {
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
             if (c == li) {
@@ -160,6 +175,16 @@ __device__ void warp_summarize(const ItemT* __restrict__ items, u64 n, uint32_t 
   }
 }
 
+// Block r with the packed keys when it holds fewer than 2^16 items.
+template <typename ItemT, int CPL>
+__device__ __forceinline__ void summarize_one(const ItemT* __restrict__ items, u64 n, uint32_t p,
+                                              uint32_t r, const SetView<ItemT>& out, uint32_t node) {
+  if (block_bound((u64)r + 1, n, p) - block_bound(r, n, p) < (1ull << 16))
+    warp_summarize<ItemT, CPL, true>(items, n, p, r, out, node);
+  else
+    warp_summarize<ItemT, CPL, false>(items, n, p, r, out, node);
+}
+
 template <typename ItemT, int CPL>
 __global__ void __launch_bounds__(32 * WS_WPB) ssw_block_kernel(const ItemT* __restrict__ items,
                                                                  u64 n, uint32_t p, uint32_t r0,
@@ -168,7 +193,7 @@ __global__ void __launch_bounds__(32 * WS_WPB) ssw_block_kernel(const ItemT* __r
                                                                  uint32_t node0) {
   const uint32_t w = blockIdx.x * WS_WPB + (threadIdx.x >> 5);
   if (w >= count) return;
-  warp_summarize<ItemT, CPL>(items, n, p, r0 + w, out, node0 + w);
+  summarize_one<ItemT, CPL>(items, n, p, r0 + w, out, node0 + w);
 }
 
 // Persistent form: each warp takes (stream, block) tasks from the counter.
@@ -185,7 +210,7 @@ __global__ void __launch_bounds__(32 * WS_WPB) ssw_batch_kernel(const BatchStrea
     const BatchTask task = tasks[t];
     const BatchStream st = streams[task.stream];
     const SetView<ItemT> out = set_view_dev<ItemT>(st.level0, st.p, st.k);
-    warp_summarize<ItemT, CPL>((const ItemT*)st.items, st.n, st.p, task.index, out, task.index);
+    summarize_one<ItemT, CPL>((const ItemT*)st.items, st.n, st.p, task.index, out, task.index);
   }
 }
 
