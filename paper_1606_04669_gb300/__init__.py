@@ -10,7 +10,7 @@ from .pss import (  # noqa: F401
     Batch, PSS_EDEVICE, PSS_EINVAL, PSS_EMISMATCH, PSS_ENOMEM, PSS_ERANGE, PSS_MAX_K, PSS_MAX_K_RESIDENT, PSS_OK,
     Exported,
     PssError, Server, Summary, Tree, gen_zipf, lib_path, load, merge, profile_enable, profile_read, strerror,
-    plan_blocks, plan_kernel, set_round_kmax, set_warp_kmax, summarize, summarize_host, summarize_tree, exact_counts,
+    plan_blocks, plan_cta_shape, plan_kernel, set_round_kmax, set_warp_kmax, summarize, summarize_host, summarize_tree, exact_counts,
     QUERY_CANDIDATES, QUERY_GUARANTEED, import_summary, set_host_direct,
     KIND_SPACE_SAVING, KIND_FREQUENT, frequent, frequent_host, frequent_tree, estimate_skew,
     skew_of_pairs)

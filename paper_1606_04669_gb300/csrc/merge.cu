@@ -28,6 +28,8 @@ template <typename ItemT>
 struct MSmem {
   ItemT* ia;
   ItemT* ib;
+  u64* ca;  // STAGED: S1's counts, then its errors
+  u64* cb;  // STAGED: S2's counts, then its errors
   u64* uc;
   uint16_t* srcA;
   uint16_t* srcB;
@@ -38,8 +40,9 @@ struct MSmem {
 
 // Shared-memory layout (returns its bytes).  BIG (k above what fits): the
 // union's counts and source indices live in a per-CTA slice of global memory
-// (gbase; bytes to *gbytes).
-template <typename ItemT, int BS, bool BIG>
+// (gbase; bytes to *gbytes).  STAGED: both inputs' counts (later their
+// errors) are copied into shared memory as well.
+template <typename ItemT, int BS, bool BIG, bool STAGED = false>
 __host__ __device__ inline size_t merge_carve(uint32_t k, unsigned char* base, unsigned char* gbase,
                                               MSmem<ItemT>* s, size_t* gbytes = nullptr) {
   size_t off = 0, goff = 0;
@@ -58,6 +61,8 @@ __host__ __device__ inline size_t merge_carve(uint32_t k, unsigned char* base, u
   L.red = (u64*)take(8ull * (BS / 32 + 1));
   L.ia = (ItemT*)take(sizeof(ItemT) * k);
   L.ib = (ItemT*)take(sizeof(ItemT) * k);
+  L.ca = STAGED ? (u64*)take(8ull * k) : nullptr;
+  L.cb = STAGED ? (u64*)take(8ull * k) : nullptr;
   L.hist = (uint32_t*)take(4ull * 512);
   L.wsum = (uint32_t*)take(4ull * 2 * (BS / 32 + 1));
   L.srcA = (uint16_t*)(BIG ? gtake(2ull * 2 * k) : take(2ull * 2 * k));
@@ -78,6 +83,33 @@ __device__ __forceinline__ uint32_t merge_path(const ItemT* a, uint32_t sa, cons
     if (a[mid] <= b[d - mid - 1]) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+// Asynchronous copies into shared memory (completed by cp_wait_all).
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The whole CTA copies n elements from global to shared memory: 16-byte
+// pieces when both addresses are 16-byte aligned, the rest element by element.
+template <int BS, typename E>
+__device__ __forceinline__ void stage_copy(E* dst, const E* src, uint32_t n) {
+  uint32_t done = 0;
+  if (((reinterpret_cast<uintptr_t>(src) | (uintptr_t)__cvta_generic_to_shared(dst)) & 15u) == 0) {
+    const uint32_t pieces = (uint32_t)(n * sizeof(E) / 16);
+    for (uint32_t i = threadIdx.x; i < pieces; i += BS)
+      cp_async(reinterpret_cast<char*>(dst) + 16 * i, reinterpret_cast<const char*>(src) + 16 * i, 16);
+    done = pieces * (uint32_t)(16 / sizeof(E));
+  }
+  for (uint32_t i = done + threadIdx.x; i < n; i += BS) cp_async(dst + i, src + i, (int)sizeof(E));
 }
 
 template <int BS>
@@ -110,7 +142,8 @@ __device__ __forceinline__ u64 block_reduce_u64(u64 v, u64* scratch, bool is_max
 // radix histogram adds each warp's equal digits with one atomic.  (Bounding
 // the kernels to three CTAs per SM, as many as the shared memory of k = 2000
 // allows, forces spills at 40 registers and was slower.)
-template <typename ItemT, int BS, bool BIG, bool MG = false>
+template <typename ItemT, int BS, bool BIG, bool MG = false, bool STAGED = false,
+          bool STATUS = true>
 __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<ItemT>& B,
                             uint32_t nb, const SetView<ItemT>& O, uint32_t no,
                             unsigned char* smem, unsigned char* gslice) {
@@ -121,12 +154,21 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
   __shared__ uint32_t sh_dup[NW];
   MSmem<ItemT> s;
   const uint32_t k = O.k;
-  merge_carve<ItemT, BS, BIG>(k, smem, gslice, &s);
+  merge_carve<ItemT, BS, BIG, STAGED>(k, smem, gslice, &s);
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t sa = A.size[na], sb = B.size[nb];
   const u64 mA = A.m[na], mB = B.m[nb];
   const size_t ba = (size_t)na * k, bb = (size_t)nb * k, bo = (size_t)no * k;
+  if constexpr (STAGED) {
+    // One round of copies: both inputs' items and counts (all k slots of
+    // each node, so that the copies need not wait for the sizes).
+    stage_copy<BS>(s.ia, A.item + ba, k);
+    stage_copy<BS>(s.ib, B.item + bb, k);
+    stage_copy<BS>(s.ca, A.count + ba, k);
+    stage_copy<BS>(s.cb, B.count + bb, k);
+    cp_commit();
+  } else {
   for (uint32_t base = 0; base < sa; base += G * BS) {
     ItemT v[G];
 #pragma unroll
@@ -153,7 +195,9 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
       if (j < sb) s.ib[j] = v[t];
     }
   }
+  }
   if (tid < 256) s.hist[tid] = 0;  // first radix pass (BS >= 256)
+  if constexpr (STAGED) cp_wait_all();
   __syncthreads();
 
   // The union in merged order: position d holds the entry of the d-th
@@ -162,7 +206,39 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
   // (an odd length, so that lanes' 8-byte stores fall in different banks),
   // WS steps at a time with their global loads issued together.
   const uint32_t L = sa + sb;
-  {
+  if constexpr (STAGED) {
+    const uint32_t per = ((L + BS - 1) / BS) | 1u;
+    const uint32_t d0 = min(L, tid * per), d1 = min(L, d0 + per);
+    uint32_t i = merge_path(s.ia, sa, s.ib, sb, d0), j = d0 - i, ndup = 0;
+    for (uint32_t d = d0; d < d1; ++d) {
+      uint16_t pa = NONE, pb = NONE;
+      u64 v = EMPTY;
+      if (j >= sb || (i < sa && s.ia[i] <= s.ib[j])) {
+        pa = (uint16_t)i;
+        if (j < sb && s.ib[j] == s.ia[i]) {
+          pb = (uint16_t)j;
+          v = s.ca[i] + s.cb[j];
+        } else {
+          v = s.ca[i] + mB;
+        }
+        ++i;
+      } else {
+        if (i > 0 && s.ia[i - 1] == s.ib[j]) {
+          ++ndup;
+        } else {
+          pb = (uint16_t)j;
+          v = s.cb[j] + mA;
+        }
+        ++j;
+      }
+      s.uc[d] = v;
+      s.srcA[d] = pa;
+      s.srcB[d] = pb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ndup += __shfl_xor_sync(0xffffffffu, ndup, o);
+    if (lane == 0) sh_dup[warp] = ndup;
+  } else {
     constexpr int WS = 3;
     const uint32_t per = ((L + BS - 1) / BS) | 1u;
     const uint32_t d0 = min(L, tid * per), d1 = min(L, d0 + per);
@@ -211,6 +287,12 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     if (lane == 0) sh_dup[warp] = ndup;
   }
   __syncthreads();
+  if constexpr (STAGED) {
+    // The counts are dead: the errors take their place while the select runs.
+    stage_copy<BS>(s.ca, A.err + ba, k);
+    stage_copy<BS>(s.cb, B.err + bb, k);
+    cp_commit();
+  }
   uint32_t dups = 0;
   for (uint32_t w = 0; w < NW; ++w) dups += sh_dup[w];
   const uint32_t U = L - dups;
@@ -308,6 +390,7 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
       s.wsum[warp] = ngt;
       s.wsum[NW + 1 + warp] = neq;
     }
+    if constexpr (STAGED) cp_wait_all();
     __syncthreads();
     uint32_t gbefore = 0, ebefore = 0, gtot = 0, etot = 0;
     for (uint32_t w = 0; w < NW; ++w) {
@@ -342,8 +425,13 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
 #pragma unroll
       for (int t = 0; t < G; ++t) {
         if (keep[t]) {
-          ea[t] = a[t] != NONE ? A.err[ba + a[t]] : mA;
-          eb[t] = b[t] != NONE ? B.err[bb + b[t]] : mB;
+          if constexpr (STAGED) {
+            ea[t] = a[t] != NONE ? s.ca[a[t]] : mA;
+            eb[t] = b[t] != NONE ? s.cb[b[t]] : mB;
+          } else {
+            ea[t] = a[t] != NONE ? A.err[ba + a[t]] : mA;
+            eb[t] = b[t] != NONE ? B.err[bb + b[t]] : mB;
+          }
         }
       }
 #pragma unroll
@@ -370,12 +458,14 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     O.size[no] = nkeep;
     O.m[no] = mout;
     O.ncov[no] = A.ncov[na] + B.ncov[nb];
-    const uint32_t st = *A.status | *B.status;
-    if (st) atomicOr(O.status, st);
+    if (STATUS) {
+      const uint32_t st = *A.status | *B.status;
+      if (st) atomicOr(O.status, st);
+    }
   }
 }
 
-template <typename ItemT, int BS>
+template <typename ItemT, int BS, bool STATUS = true>
 __device__ void copy_node(const SetView<ItemT>& in, uint32_t ni, const SetView<ItemT>& O,
                           uint32_t no) {
   const uint32_t k = O.k, sz = in.size[ni];
@@ -389,11 +479,11 @@ __device__ void copy_node(const SetView<ItemT>& in, uint32_t ni, const SetView<I
     O.size[no] = sz;
     O.m[no] = in.m[ni];
     O.ncov[no] = in.ncov[ni];
-    if (*in.status) atomicOr(O.status, *in.status);
+    if (STATUS && *in.status) atomicOr(O.status, *in.status);
   }
 }
 
-template <typename ItemT, int BS, bool BIG, bool MG>
+template <typename ItemT, int BS, bool BIG, bool MG, bool STAGED>
 __global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out,
                                                          unsigned char* gscratch, size_t gslice) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -402,21 +492,21 @@ __global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetV
     copy_node<ItemT, BS>(in, 2 * j, out, j);
     return;
   }
-  merge_nodes<ItemT, BS, BIG, MG>(in, 2 * j, in, 2 * j + 1, out, j, smem,
-                                  BIG ? gscratch + (size_t)j * gslice : nullptr);
+  merge_nodes<ItemT, BS, BIG, MG, STAGED>(in, 2 * j, in, 2 * j + 1, out, j, smem,
+                                          BIG ? gscratch + (size_t)j * gslice : nullptr);
 }
 
-template <typename ItemT, int BS, bool BIG, bool MG>
+template <typename ItemT, int BS, bool BIG, bool MG, bool STAGED>
 __global__ void __launch_bounds__(BS) merge_pair_kernel(SetView<ItemT> a, uint32_t ia,
                                                         SetView<ItemT> b, uint32_t ib,
                                                         SetView<ItemT> out, unsigned char* gscratch) {
   extern __shared__ __align__(16) unsigned char smem[];
-  merge_nodes<ItemT, BS, BIG, MG>(a, ia, b, ib, out, 0, smem, gscratch);
+  merge_nodes<ItemT, BS, BIG, MG, STAGED>(a, ia, b, ib, out, 0, smem, gscratch);
 }
 
 // Batch form: task (d, j) builds node j of the next level of descriptor d
 // (MG: the Frequent merge).
-template <typename ItemT, int BS, bool MG>
+template <typename ItemT, int BS, bool MG, bool STAGED>
 __global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __restrict__ descs,
                                                          const BatchTask* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -429,7 +519,48 @@ __global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __rest
     copy_node<ItemT, BS>(in, 2 * j, out, j);
     return;
   }
-  merge_nodes<ItemT, BS, false, MG>(in, 2 * j, in, 2 * j + 1, out, j, smem, nullptr);
+  merge_nodes<ItemT, BS, false, MG, STAGED>(in, 2 * j, in, 2 * j + 1, out, j, smem, nullptr);
+}
+
+// Every merge level of one tree in one launch.  CTA j builds node j of level
+// 1; a CTA that has finished a node of level L announces it on the parent's
+// arrival counter, and the CTA that completes the parent's inputs (the second
+// of two children, or the only one of a carried node) goes on to build the
+// parent.  No CTA waits for another: the others end.  The producer of the root
+// finishes last and writes every merge level's status word (the status of
+// level 0, which every level inherits).
+template <typename ItemT, int BS, bool MG, bool STAGED>
+__global__ void __launch_bounds__(BS) merge_tree_kernel(MergeTreeArgs t) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t go;
+  uint32_t j = blockIdx.x;
+  for (uint32_t L = 1;; ++L) {
+    const SetView<ItemT> in = set_view_dev<ItemT>(t.mem[L - 1], t.nodes[L - 1], t.k);
+    const SetView<ItemT> out = set_view_dev<ItemT>(t.mem[L], t.nodes[L], t.k);
+    if (2 * j + 1 >= in.nodes)
+      copy_node<ItemT, BS, false>(in, 2 * j, out, j);
+    else
+      merge_nodes<ItemT, BS, false, MG, STAGED, false>(in, 2 * j, in, 2 * j + 1, out, j, smem,
+                                                       nullptr);
+    if (L + 1 == t.levels) break;
+    // release this node, then count it at the parent
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t parent = j >> 1;
+      const uint32_t children = 2 * parent + 1 < t.nodes[L] ? 2u : 1u;
+      go = atomicAdd(t.arrive + t.arrive_off[L] + parent, 1u) + 1u == children;
+    }
+    __syncthreads();
+    if (!go) return;
+    __threadfence();  // acquire the sibling's node
+    j >>= 1;
+  }
+  if (threadIdx.x == 0) {
+    const uint32_t st = *set_view_dev<ItemT>(t.mem[0], t.nodes[0], t.k).status;
+    for (uint32_t L = 1; L < t.levels; ++L)
+      *set_view_dev<ItemT>(t.mem[L], t.nodes[L], t.k).status = st;
+  }
 }
 
 template <typename ItemT, int BS>
@@ -440,10 +571,27 @@ __global__ void __launch_bounds__(BS) copy_node_kernel(SetView<ItemT> in, uint32
 
 }  // namespace
 
+namespace {
+
+// Shared memory a staged combine may take: below the 227 KB a CTA can opt
+// into, with room for the kernel's static shared memory.
+constexpr size_t MERGE_STAGED_MAX = 224 * 1024;
+
+// Whether the combine of k-entry summaries runs staged (both inputs' items
+// and counts copied into shared memory in one round).
+template <typename ItemT>
+bool merge_staged(uint32_t k) {
+  return k <= SS_SMEM_MAX_K &&
+         merge_carve<ItemT, MERGE_BS, false, true>(k, nullptr, nullptr, nullptr) <= MERGE_STAGED_MAX;
+}
+
+}  // namespace
+
 template <typename ItemT>
 size_t merge_smem_bytes(uint32_t k) {
-  return k > SS_SMEM_MAX_K ? merge_carve<ItemT, MERGE_BS, true>(k, nullptr, nullptr, nullptr)
-                           : merge_carve<ItemT, MERGE_BS, false>(k, nullptr, nullptr, nullptr);
+  if (k > SS_SMEM_MAX_K) return merge_carve<ItemT, MERGE_BS, true>(k, nullptr, nullptr, nullptr);
+  return merge_staged<ItemT>(k) ? merge_carve<ItemT, MERGE_BS, false, true>(k, nullptr, nullptr, nullptr)
+                                : merge_carve<ItemT, MERGE_BS, false>(k, nullptr, nullptr, nullptr);
 }
 
 namespace {
@@ -461,22 +609,19 @@ template <typename ItemT>
 cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream,
                                bool mg) {
   const size_t smem = merge_smem_bytes<ItemT>(in.k);
-  if (mg) {
-    if (in.k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;
-    auto kern = merge_level_kernel<ItemT, MERGE_BS, false, true>;
-    cudaError_t e = ensure_kernel_attrs((const void*)kern);
-    if (e != cudaSuccess) return e;
-    kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out, nullptr, 0);
-    return cudaGetLastError();
-  }
+  if (mg && in.k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;
   if (in.k <= SS_SMEM_MAX_K) {
-    auto kern = merge_level_kernel<ItemT, MERGE_BS, false, false>;
+    const bool st = merge_staged<ItemT>(in.k);
+    auto kern = mg ? (st ? merge_level_kernel<ItemT, MERGE_BS, false, true, true>
+                         : merge_level_kernel<ItemT, MERGE_BS, false, true, false>)
+                   : (st ? merge_level_kernel<ItemT, MERGE_BS, false, false, true>
+                         : merge_level_kernel<ItemT, MERGE_BS, false, false, false>);
     cudaError_t e = ensure_kernel_attrs((const void*)kern);
     if (e != cudaSuccess) return e;
     kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out, nullptr, 0);
     return cudaGetLastError();
   }
-  auto kern = merge_level_kernel<ItemT, MERGE_BS, true, false>;
+  auto kern = merge_level_kernel<ItemT, MERGE_BS, true, false, false>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   void* g = nullptr;
@@ -488,26 +633,58 @@ cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream
   return e != cudaSuccess ? e : f;
 }
 
+uint32_t merge_tree_arrivals(const uint32_t* nodes, uint32_t levels, uint32_t* off) {
+  uint32_t total = 0;
+  for (uint32_t L = 0; L < levels; ++L) {
+    if (off) off[L] = total;
+    if (L >= 1 && L + 1 < levels) total += nodes[L + 1];
+  }
+  return total;
+}
+
+template <typename ItemT>
+cudaError_t launch_merge_tree(void* const* mems, const uint32_t* nodes, uint32_t levels,
+                              uint32_t k, uint32_t* arrive, cudaStream_t stream, bool mg) {
+  if (k > SS_SMEM_MAX_K || levels > MERGE_TREE_MAX_LEVELS) return cudaErrorInvalidValue;
+  if (levels < 2) return cudaSuccess;
+  MergeTreeArgs t{};
+  for (uint32_t L = 0; L < levels; ++L) {
+    t.mem[L] = mems[L];
+    t.nodes[L] = nodes[L];
+  }
+  merge_tree_arrivals(nodes, levels, t.arrive_off);
+  t.arrive = arrive;
+  t.levels = levels;
+  t.k = k;
+  const size_t smem = merge_smem_bytes<ItemT>(k);
+  const bool st = merge_staged<ItemT>(k);
+  auto kern = mg ? (st ? merge_tree_kernel<ItemT, MERGE_BS, true, true>
+                       : merge_tree_kernel<ItemT, MERGE_BS, true, false>)
+                 : (st ? merge_tree_kernel<ItemT, MERGE_BS, false, true>
+                       : merge_tree_kernel<ItemT, MERGE_BS, false, false>);
+  cudaError_t e = ensure_kernel_attrs((const void*)kern);
+  if (e != cudaSuccess) return e;
+  kern<<<nodes[1], MERGE_BS, smem, stream>>>(t);
+  return cudaGetLastError();
+}
+
 template <typename ItemT>
 cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, uint32_t ib,
                               SetView<ItemT> out, cudaStream_t stream, bool mg) {
   const size_t smem = merge_smem_bytes<ItemT>(out.k);
-  if (mg) {
-    if (out.k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;
-    auto kern = merge_pair_kernel<ItemT, MERGE_BS, false, true>;
-    cudaError_t e = ensure_kernel_attrs((const void*)kern);
-    if (e != cudaSuccess) return e;
-    kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out, nullptr);
-    return cudaGetLastError();
-  }
+  if (mg && out.k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;
   if (out.k <= SS_SMEM_MAX_K) {
-    auto kern = merge_pair_kernel<ItemT, MERGE_BS, false, false>;
+    const bool st = merge_staged<ItemT>(out.k);
+    auto kern = mg ? (st ? merge_pair_kernel<ItemT, MERGE_BS, false, true, true>
+                         : merge_pair_kernel<ItemT, MERGE_BS, false, true, false>)
+                   : (st ? merge_pair_kernel<ItemT, MERGE_BS, false, false, true>
+                         : merge_pair_kernel<ItemT, MERGE_BS, false, false, false>);
     cudaError_t e = ensure_kernel_attrs((const void*)kern);
     if (e != cudaSuccess) return e;
     kern<<<1, MERGE_BS, smem, stream>>>(a, ia, b, ib, out, nullptr);
     return cudaGetLastError();
   }
-  auto kern = merge_pair_kernel<ItemT, MERGE_BS, true, false>;
+  auto kern = merge_pair_kernel<ItemT, MERGE_BS, true, false, false>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   void* g = nullptr;
@@ -531,7 +708,11 @@ cudaError_t launch_merge_tasks(const MergeDesc* descs, const BatchTask* tasks, u
                                uint32_t k, cudaStream_t stream, bool mg) {
   if (k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;  // the batch keeps k in shared memory
   const size_t smem = merge_smem_bytes<ItemT>(k);
-  auto kern = mg ? merge_tasks_kernel<ItemT, MERGE_BS, true> : merge_tasks_kernel<ItemT, MERGE_BS, false>;
+  const bool st = merge_staged<ItemT>(k);
+  auto kern = mg ? (st ? merge_tasks_kernel<ItemT, MERGE_BS, true, true>
+                       : merge_tasks_kernel<ItemT, MERGE_BS, true, false>)
+                 : (st ? merge_tasks_kernel<ItemT, MERGE_BS, false, true>
+                       : merge_tasks_kernel<ItemT, MERGE_BS, false, false>);
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
   if (ntasks == 0) return cudaSuccess;
@@ -548,6 +729,10 @@ template size_t merge_smem_bytes<u64>(uint32_t);
 template cudaError_t launch_merge_level<uint32_t>(SetView<uint32_t>, SetView<uint32_t>, cudaStream_t,
                                                   bool);
 template cudaError_t launch_merge_level<u64>(SetView<u64>, SetView<u64>, cudaStream_t, bool);
+template cudaError_t launch_merge_tree<uint32_t>(void* const*, const uint32_t*, uint32_t, uint32_t,
+                                                 uint32_t*, cudaStream_t, bool);
+template cudaError_t launch_merge_tree<u64>(void* const*, const uint32_t*, uint32_t, uint32_t,
+                                            uint32_t*, cudaStream_t, bool);
 template cudaError_t launch_merge_pair<uint32_t>(SetView<uint32_t>, uint32_t, SetView<uint32_t>,
                                                  uint32_t, SetView<uint32_t>, cudaStream_t, bool);
 template cudaError_t launch_merge_pair<u64>(SetView<u64>, uint32_t, SetView<u64>, uint32_t,

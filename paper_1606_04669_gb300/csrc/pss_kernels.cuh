@@ -44,6 +44,11 @@ constexpr int SS_IPT = 2;      // items per thread per window (window = SS_BS * 
 constexpr int SS_BS_NARROW = 256;
 constexpr int SS_IPT_NARROW = 4;
 static_assert(SS_BS * SS_IPT == SS_BS_NARROW * SS_IPT_NARROW, "both shapes use one window size");
+// Small shape: a 512-item window on 256 threads, whose smaller state lets four
+// CTAs share an SM at k where the narrow shape fits only three.
+constexpr int SS_BS_SMALL = 256;
+constexpr int SS_IPT_SMALL = 2;
+enum SSShape { SS_SHAPE_WIDE = 0, SS_SHAPE_NARROW = 1, SS_SHAPE_SMALL = 2 };
 constexpr int MERGE_BS = 512;  // threads per CTA of the combine kernel
 constexpr int CANON_BS = 1024; // threads per CTA of the query/export kernel
 
@@ -52,12 +57,14 @@ constexpr int CANON_BS = 1024; // threads per CTA of the query/export kernel
 template <typename ItemT>
 size_t ss_smem_bytes(uint32_t k);
 
-// Threads per CTA of the summarize kernel for k counters (SS_BS or
-// SS_BS_NARROW; `batch`: the persistent batch kernel): the narrow shape when
-// it keeps at least as many threads resident per SM as the wide one.
-// Decided once per (item type, k, kernel) by the occupancy calculator.
+// Shape of the summarize kernel for k counters (`batch`: the persistent
+// batch kernel): the shape that keeps the most threads resident per SM; on a
+// tie the narrow shape, then the small one, then the wide one (measured:
+// the 1024-item window wins where four CTAs of it fit, the 512-item window
+// where only it fits four).  Decided once per (item type, k, kernel) by the
+// occupancy calculator.
 template <typename ItemT>
-int ss_shape_bs(uint32_t k, bool batch);
+int ss_shape(uint32_t k, bool batch);
 
 // Blocks r0 .. r0+count-1 of p (Algorithm 1 bounds over n items) into nodes
 // node0 .. node0+count-1 of `out`.
@@ -72,6 +79,24 @@ size_t merge_smem_bytes(uint32_t k);
 // One level of the reduction tree: out node j = combine(in node 2j, in node
 // 2j+1), or a copy of in node 2j when it has no partner.  mg: the merge of
 // Frequent (Misra–Gries) summaries of capacity in.k instead.
+// Every merge level of one tree (k <= SS_SMEM_MAX_K) in one launch: mems[L]
+// is the set of level L (nodes[L] nodes; level 0 written, its status word set;
+// the merge levels' status words are written by the launch), `arrive` holds
+// merge_tree_arrivals(nodes, levels) zeroed counters.
+constexpr uint32_t MERGE_TREE_MAX_LEVELS = 33;
+struct MergeTreeArgs {
+  void* mem[MERGE_TREE_MAX_LEVELS];
+  uint32_t nodes[MERGE_TREE_MAX_LEVELS];
+  uint32_t arrive_off[MERGE_TREE_MAX_LEVELS];
+  uint32_t* arrive;
+  uint32_t levels;
+  uint32_t k;
+};
+uint32_t merge_tree_arrivals(const uint32_t* nodes, uint32_t levels, uint32_t* off = nullptr);
+template <typename ItemT>
+cudaError_t launch_merge_tree(void* const* mems, const uint32_t* nodes, uint32_t levels,
+                              uint32_t k, uint32_t* arrive, cudaStream_t stream, bool mg);
+
 template <typename ItemT>
 cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream,
                                bool mg = false);
@@ -166,7 +191,7 @@ template <typename ItemT>
 int summarize_warp_ctas_per_sm(uint32_t k);
 
 // Resident CTAs per SM of the persistent CTA kernel for k counters, in the
-// shape ss_shape_bs(k, true) picks (0 if it cannot run).
+// shape ss_shape(k, true) picks (0 if it cannot run).
 template <typename ItemT>
 int summarize_ctas_per_sm(uint32_t k);
 

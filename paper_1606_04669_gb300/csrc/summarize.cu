@@ -1371,45 +1371,60 @@ int resident_ctas(const void* kern, int bs, size_t smem) {
 }
 
 template <typename ItemT>
-size_t shape_smem(uint32_t k, int bs) {
-  return bs == SS_BS_NARROW
+size_t shape_smem(uint32_t k, int shape) {
+  return shape == SS_SHAPE_NARROW
              ? ss_carve<ItemT, SS_BS_NARROW, SS_IPT_NARROW, false>(k, nullptr, nullptr, nullptr)
+         : shape == SS_SHAPE_SMALL
+             ? ss_carve<ItemT, SS_BS_SMALL, SS_IPT_SMALL, false>(k, nullptr, nullptr, nullptr)
              : ss_smem_bytes<ItemT>(k);
 }
 
+inline int shape_threads(int shape) {
+  return shape == SS_SHAPE_NARROW ? SS_BS_NARROW : shape == SS_SHAPE_SMALL ? SS_BS_SMALL : SS_BS;
+}
+
 template <typename ItemT>
-const void* block_kernel_of(int bs) {
-  return bs == SS_BS_NARROW
+const void* block_kernel_of(int shape) {
+  return shape == SS_SHAPE_NARROW
              ? (const void*)ss_block_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW, false>
+         : shape == SS_SHAPE_SMALL
+             ? (const void*)ss_block_kernel<ItemT, SS_BS_SMALL, SS_IPT_SMALL, false>
              : (const void*)ss_block_kernel<ItemT, SS_BS, SS_IPT, false>;
 }
 
 template <typename ItemT>
-const void* batch_kernel_of(int bs) {
-  return bs == SS_BS_NARROW ? (const void*)ss_batch_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW>
-                            : (const void*)ss_batch_kernel<ItemT, SS_BS, SS_IPT>;
+const void* batch_kernel_of(int shape) {
+  return shape == SS_SHAPE_NARROW
+             ? (const void*)ss_batch_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW>
+         : shape == SS_SHAPE_SMALL ? (const void*)ss_batch_kernel<ItemT, SS_BS_SMALL, SS_IPT_SMALL>
+                                   : (const void*)ss_batch_kernel<ItemT, SS_BS, SS_IPT>;
 }
 
 }  // namespace
 
 template <typename ItemT>
-int ss_shape_bs(uint32_t k, bool batch) {
-  if (k > SS_SMEM_MAX_K) return SS_BS;
-  // 0 = not decided yet; decided on the first device that asks (one kind of
-  // GPU per process), so that later launches and stream captures only read it
+int ss_shape(uint32_t k, bool batch) {
+  if (k > SS_SMEM_MAX_K) return SS_SHAPE_WIDE;
+  // shape + 1, 0 = not decided yet; decided on the first device that asks
+  // (one kind of GPU per process), so that later launches and stream captures
+  // only read it
   static std::atomic<int> memo[2][SS_SMEM_MAX_K + 1];
   std::atomic<int>& m = memo[batch ? 1 : 0][k];
-  int bs = m.load(std::memory_order_relaxed);
-  if (bs) return bs;
-  const void* narrow =
-      batch ? batch_kernel_of<ItemT>(SS_BS_NARROW) : block_kernel_of<ItemT>(SS_BS_NARROW);
-  const void* wide = batch ? batch_kernel_of<ItemT>(SS_BS) : block_kernel_of<ItemT>(SS_BS);
-  const int tn =
-      resident_ctas(narrow, SS_BS_NARROW, shape_smem<ItemT>(k, SS_BS_NARROW)) * SS_BS_NARROW;
-  const int tw = resident_ctas(wide, SS_BS, shape_smem<ItemT>(k, SS_BS)) * SS_BS;
-  bs = (tn > 0 && tn >= tw) ? SS_BS_NARROW : SS_BS;
-  m.store(bs, std::memory_order_relaxed);
-  return bs;
+  const int known = m.load(std::memory_order_relaxed);
+  if (known) return known - 1;
+  int best = SS_SHAPE_WIDE, best_threads = -1;
+  // in order of preference on a tie
+  for (int shape : {SS_SHAPE_NARROW, SS_SHAPE_SMALL, SS_SHAPE_WIDE}) {
+    const void* kern = batch ? batch_kernel_of<ItemT>(shape) : block_kernel_of<ItemT>(shape);
+    const int t = resident_ctas(kern, shape_threads(shape), shape_smem<ItemT>(k, shape)) *
+                  shape_threads(shape);
+    if (t > best_threads) {
+      best = shape;
+      best_threads = t;
+    }
+  }
+  m.store(best + 1, std::memory_order_relaxed);
+  return best;
 }
 
 template <typename ItemT>
@@ -1421,15 +1436,18 @@ cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint3
   if (use_round_kernel<ItemT>(out.k, count))
     return launch_summarize_round_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
   if (out.k <= SS_SMEM_MAX_K) {
-    const int bs = ss_shape_bs<ItemT>(out.k, false);
-    const void* kern = block_kernel_of<ItemT>(bs);
+    const int shape = ss_shape<ItemT>(out.k, false);
+    const void* kern = block_kernel_of<ItemT>(shape);
     cudaError_t e = ensure_kernel_attrs(kern);
     if (e != cudaSuccess) return e;
     if (count == 0) return cudaSuccess;
-    const size_t smem = shape_smem<ItemT>(out.k, bs);
-    if (bs == SS_BS_NARROW)
+    const size_t smem = shape_smem<ItemT>(out.k, shape);
+    if (shape == SS_SHAPE_NARROW)
       ss_block_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW, false>
           <<<count, SS_BS_NARROW, smem, stream>>>(items, n, p, r0, out, node0, nullptr, 0);
+    else if (shape == SS_SHAPE_SMALL)
+      ss_block_kernel<ItemT, SS_BS_SMALL, SS_IPT_SMALL, false>
+          <<<count, SS_BS_SMALL, smem, stream>>>(items, n, p, r0, out, node0, nullptr, 0);
     else
       ss_block_kernel<ItemT, SS_BS, SS_IPT, false>
           <<<count, SS_BS, smem, stream>>>(items, n, p, r0, out, node0, nullptr, 0);
@@ -1457,14 +1475,17 @@ cudaError_t launch_summarize_batch(const BatchStream* streams, const BatchTask* 
                                    uint32_t ntasks, uint32_t* counter, uint32_t k, uint32_t grid,
                                    cudaStream_t stream) {
   if (k > SS_SMEM_MAX_K) return cudaErrorInvalidValue;  // the batch keeps k in shared memory
-  const int bs = ss_shape_bs<ItemT>(k, true);
-  cudaError_t e = ensure_kernel_attrs(batch_kernel_of<ItemT>(bs));
+  const int shape = ss_shape<ItemT>(k, true);
+  cudaError_t e = ensure_kernel_attrs(batch_kernel_of<ItemT>(shape));
   if (e != cudaSuccess) return e;
   if (ntasks == 0 || grid == 0) return cudaSuccess;
-  const size_t smem = shape_smem<ItemT>(k, bs);
-  if (bs == SS_BS_NARROW)
+  const size_t smem = shape_smem<ItemT>(k, shape);
+  if (shape == SS_SHAPE_NARROW)
     ss_batch_kernel<ItemT, SS_BS_NARROW, SS_IPT_NARROW>
         <<<grid, SS_BS_NARROW, smem, stream>>>(streams, tasks, ntasks, counter);
+  else if (shape == SS_SHAPE_SMALL)
+    ss_batch_kernel<ItemT, SS_BS_SMALL, SS_IPT_SMALL>
+        <<<grid, SS_BS_SMALL, smem, stream>>>(streams, tasks, ntasks, counter);
   else
     ss_batch_kernel<ItemT, SS_BS, SS_IPT>
         <<<grid, SS_BS, smem, stream>>>(streams, tasks, ntasks, counter);
@@ -1474,8 +1495,9 @@ cudaError_t launch_summarize_batch(const BatchStream* streams, const BatchTask* 
 template <typename ItemT>
 int summarize_ctas_per_sm(uint32_t k) {
   if (k > SS_SMEM_MAX_K) return 0;
-  const int bs = ss_shape_bs<ItemT>(k, true);
-  return resident_ctas(batch_kernel_of<ItemT>(bs), bs, shape_smem<ItemT>(k, bs));
+  const int shape = ss_shape<ItemT>(k, true);
+  return resident_ctas(batch_kernel_of<ItemT>(shape), shape_threads(shape),
+                       shape_smem<ItemT>(k, shape));
 }
 
 template cudaError_t launch_summarize_batch<uint32_t>(const BatchStream*, const BatchTask*, uint32_t,
@@ -1486,8 +1508,8 @@ template int summarize_ctas_per_sm<uint32_t>(uint32_t);
 template int summarize_ctas_per_sm<u64>(uint32_t);
 template size_t ss_smem_bytes<uint32_t>(uint32_t);
 template size_t ss_smem_bytes<u64>(uint32_t);
-template int ss_shape_bs<uint32_t>(uint32_t, bool);
-template int ss_shape_bs<u64>(uint32_t, bool);
+template int ss_shape<uint32_t>(uint32_t, bool);
+template int ss_shape<u64>(uint32_t, bool);
 template cudaError_t launch_summarize_blocks<uint32_t>(const uint32_t*, u64, uint32_t, uint32_t,
                                                        uint32_t, SetView<uint32_t>, uint32_t,
                                                        cudaStream_t);
@@ -1502,6 +1524,20 @@ extern "C" int pss_plan_kernel(uint32_t k, uint32_t count, int item_bytes) {
   const bool round = item_bytes == 4 ? pss::use_round_kernel<uint32_t>(k, count)
                                      : pss::use_round_kernel<pss::u64>(k, count);
   return round ? PSS_KERNEL_ROUND : PSS_KERNEL_CTA;
+}
+
+extern "C" int pss_plan_cta_shape(uint32_t k, int item_bytes, int batch, int* threads,
+                                  int* items_per_thread) {
+  if (k < 2 || k > PSS_MAX_K || (item_bytes != 4 && item_bytes != 8) || !threads ||
+      !items_per_thread)
+    return PSS_EINVAL;
+  const int shape = item_bytes == 4 ? pss::ss_shape<uint32_t>(k, batch != 0)
+                                    : pss::ss_shape<pss::u64>(k, batch != 0);
+  *threads = pss::shape_threads(shape);
+  *items_per_thread = shape == pss::SS_SHAPE_NARROW  ? pss::SS_IPT_NARROW
+                      : shape == pss::SS_SHAPE_SMALL ? pss::SS_IPT_SMALL
+                                                     : pss::SS_IPT;
+  return PSS_OK;
 }
 
 extern "C" uint32_t pss_set_round_kmax(uint32_t kmax) {

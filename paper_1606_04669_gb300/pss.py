@@ -160,6 +160,8 @@ SIGNATURES = {
     "pss_set_warp_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
     "pss_set_round_kmax": (ctypes.c_uint32, [ctypes.c_uint32]),
     "pss_plan_kernel": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int]),
+    "pss_plan_cta_shape": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pss_set_host_direct": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pss_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
@@ -528,6 +530,16 @@ def plan_kernel(k: int, count: int, item_bytes: int = 4) -> str:
     if code < 0:
         raise ValueError("invalid k or item width")
     return KERNEL_NAMES[code]
+
+
+def plan_cta_shape(k: int, item_bytes: int = 4, batch: bool = False) -> tuple[int, int]:
+    """pss_plan_cta_shape: (threads per CTA, items per thread) of the
+    window-parallel block-summary kernel for k counters."""
+    t = ctypes.c_int()
+    ipt = ctypes.c_int()
+    _check(load().pss_plan_cta_shape(int(k), int(item_bytes), 1 if batch else 0, ctypes.byref(t),
+                                     ctypes.byref(ipt)), "pss_plan_cta_shape")
+    return int(t.value), int(ipt.value)
 
 
 def set_round_kmax(kmax: int) -> int:

@@ -89,15 +89,42 @@ def test_random_configs(n, k, p, w, s, log2u, seed):
     compare_tree(x, k, p)
 
 
-@pytest.mark.parametrize("k,w", [(544, 4), (545, 4), (304, 8), (305, 8)])
-def test_cta_shape_boundaries(k, w):
-    # The CTA kernel runs 256 threads x 4 items when that keeps as many threads
-    # resident as 512 x 2 (small state); on GB300 the switch falls between
-    # these k (u32: 544 | 545, u64: 304 | 305).  Both sides, with cut windows.
-    x = oracle.gen_zipf(180_000 + k, seed=900 + k, s=0.9, log2u=32, width=w)
-    compare_tree(x, k, 3)
-    y = oracle.gen_zipf(120_000, seed=950 + k, s=1.8, log2u=18, width=w)
-    compare_tree(y, k, 2)
+def shape_switches(w: int):
+    """The k where the CTA kernel's shape changes (last k of one shape, first
+    of the next), found through pss_plan_cta_shape."""
+    out = []
+    prev = P.plan_cta_shape(2, w)
+    for k in range(3, 4097):
+        cur = P.plan_cta_shape(k, w)
+        if cur != prev:
+            out.append((k - 1, k, prev, cur))
+        prev = cur
+    return out
+
+
+def test_cta_shapes_in_order():
+    # 256 x 4 (1024-item window) at the smallest k, then 256 x 2 (512-item
+    # window), then 512 x 2.  Where k is so large that every shape keeps the
+    # same 512 threads resident, the tie order picks again (256 x 4 first).
+    for w in (4, 8):
+        seq = [P.plan_cta_shape(2, w)] + [c[3] for c in shape_switches(w)]
+        assert seq[:3] == [(256, 4), (256, 2), (512, 2)], (w, seq)
+        assert set(seq) == {(256, 4), (256, 2), (512, 2)}, (w, seq)
+    assert P.plan_cta_shape(8192, 4) == (512, 2)
+    with pytest.raises(P.PssError):
+        P.plan_cta_shape(1, 4)
+
+
+@pytest.mark.parametrize("w", [4, 8])
+def test_cta_shape_boundaries(w):
+    # Both sides of every shape switch, with cut windows (weak skew over a
+    # large universe) and with hits (strong skew over a small one).
+    for last, first, _, _ in shape_switches(w):
+        for k in (last, first):
+            x = oracle.gen_zipf(180_000 + k, seed=900 + k, s=0.9, log2u=32, width=w)
+            compare_tree(x, k, 3)
+            y = oracle.gen_zipf(120_000, seed=950 + k, s=1.8, log2u=18, width=w)
+            compare_tree(y, k, 2)
 
 
 def test_edge_empty_and_tiny():
