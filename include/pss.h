@@ -577,10 +577,12 @@ int pss_plan_kernel(uint32_t k, uint32_t count, int item_bytes);
  * (item_bytes 4 or 8; `batch` != 0: the persistent kernel of the batch API):
  * *threads per CTA and *items_per_thread of one window.  Three shapes exist
  * (512 x 2, 256 x 4, 256 x 2); the one that keeps the most threads resident
- * per SM at this k is used (on a tie 256 x 4, then 256 x 2, then 512 x 2).
- * The summaries do not depend on the shape.  Queries the device's occupancy
- * once per k.  PSS_EINVAL for invalid arguments or null outputs; k above
- * 4096 always reports 512 x 2. */
+ * per SM at this k is used (on a tie 256 x 4, then 256 x 2, then 512 x 2) by
+ * launches of more blocks than the SMs hold at once in the 512 x 2 shape;
+ * smaller launches run 256 x 2 as 512 x 2 (a launch that waits for no slot
+ * takes as long as one block).  The summaries do not depend on the shape.
+ * Queries the device's occupancy once per k.  PSS_EINVAL for invalid
+ * arguments or null outputs; k above 4096 always reports 512 x 2. */
 int pss_plan_cta_shape(uint32_t k, int item_bytes, int batch, int* threads,
                        int* items_per_thread);
 

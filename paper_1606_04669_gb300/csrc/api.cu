@@ -65,16 +65,13 @@ cudaError_t prepare_device() {
   return cudaSuccess;
 }
 
-// zero_status = false: the producer of the set writes its status word.
-cudaError_t alloc_set(uint32_t nodes, uint32_t k, int w, cudaStream_t s, void** mem,
-                      bool zero_status = true) {
+cudaError_t alloc_set(uint32_t nodes, uint32_t k, int w, cudaStream_t s, void** mem) {
   SetLayout L = set_layout(nodes, k, w);
   cudaError_t e = cudaMallocAsync(mem, L.total, s);
   if (e != cudaSuccess) {
     *mem = nullptr;
     return e;
   }
-  if (!zero_status) return cudaSuccess;
   e = cudaMemsetAsync((char*)*mem + L.status, 0, 4, s);
   if (e != cudaSuccess) {
     cudaFreeAsync(*mem, s);
@@ -123,39 +120,6 @@ int run_tree(uint32_t k, uint32_t p, cudaStream_t s, bool keep, std::vector<void
   uint32_t levels = 0;
   for (uint32_t w2 = p; w2 > 1; w2 = (w2 + 1) / 2) ++levels;
   ProfScope prof(PROF_MERGE, s, levels);
-  // k in shared memory: every merge level in one launch (all levels
-  // allocated at once, about twice level 0's bytes)
-  if (levels > 0 && k <= SS_SMEM_MAX_K && levels + 1 <= MERGE_TREE_MAX_LEVELS) {
-    for (uint32_t cur = p; cur > 1;) {
-      cur = (cur + 1) / 2;
-      void* mm = nullptr;
-      e = alloc_set(cur, k, w, s, &mm, false);
-      if (e != cudaSuccess) return fail(e);
-      mems.push_back(mm);
-      nodes.push_back(cur);
-    }
-    const uint32_t narr = merge_tree_arrivals(nodes.data(), levels + 1);
-    uint32_t* arrive = nullptr;
-    if (narr) {
-      e = cudaMallocAsync((void**)&arrive, 4ull * narr, s);
-      if (e != cudaSuccess) return fail(e);
-      e = cudaMemsetAsync(arrive, 0, 4ull * narr, s);
-    }
-    if (e == cudaSuccess)
-      e = launch_merge_tree<ItemT>(mems.data(), nodes.data(), levels + 1, k, arrive, s, mg);
-    count_launches(1);
-    if (arrive) {
-      const cudaError_t f = cudaFreeAsync(arrive, s);
-      if (e == cudaSuccess) e = f;
-    }
-    if (e != cudaSuccess) return fail(e);
-    if (!keep)
-      for (size_t i = 0; i + 1 < mems.size(); ++i) {
-        cudaFreeAsync(mems[i], s);
-        mems[i] = nullptr;
-      }
-    return PSS_OK;
-  }
   while (nodes.back() > 1) {
     const uint32_t cur = nodes.back(), nxt = (cur + 1) / 2;
     void* mm = nullptr;

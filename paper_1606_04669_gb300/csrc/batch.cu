@@ -412,7 +412,8 @@ int batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out, int 
         return PSS_EINVAL;
       }
     } else if (c.ntasks) {
-      const int per_sm = w == 4 ? summarize_ctas_per_sm<uint32_t>(c.k) : summarize_ctas_per_sm<u64>(c.k);
+      const int per_sm = w == 4 ? summarize_ctas_per_sm<uint32_t>(c.k, c.ntasks)
+                                : summarize_ctas_per_sm<u64>(c.k, c.ntasks);
       if (per_sm <= 0) {
         destroy(b);
         return PSS_EINVAL;

@@ -142,15 +142,14 @@ __device__ __forceinline__ u64 block_reduce_u64(u64 v, u64* scratch, bool is_max
 // radix histogram adds each warp's equal digits with one atomic.  (Bounding
 // the kernels to three CTAs per SM, as many as the shared memory of k = 2000
 // allows, forces spills at 40 registers and was slower.)
-template <typename ItemT, int BS, bool BIG, bool MG = false, bool STAGED = false,
-          bool STATUS = true>
+template <typename ItemT, int BS, bool BIG, bool MG = false, bool STAGED = false>
 __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<ItemT>& B,
                             uint32_t nb, const SetView<ItemT>& O, uint32_t no,
                             unsigned char* smem, unsigned char* gslice) {
   constexpr uint32_t NW = BS / 32;
   constexpr int G = 2;
   __shared__ u64 sh_prefix;
-  __shared__ uint32_t sh_need;
+  __shared__ uint32_t sh_need, sh_found;
   __shared__ uint32_t sh_dup[NW];
   MSmem<ItemT> s;
   const uint32_t k = O.k;
@@ -298,13 +297,75 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
   const uint32_t U = L - dups;
 
   // Prune(k): the k-th largest count c*, and how many entries equal to c* to
-  // keep (MG: the (k+1)-th largest, none kept).  Most-significant digit
-  // first, 8 bits a pass; two histogram buffers alternate, so a pass needs
-  // two barriers.
+  // keep (MG: the (k+1)-th largest, none kept).  c* is the (U - need + 1)-th
+  // smallest count.  A first histogram of the counts' distances from the
+  // union's minimum (255 and above in one bin), scanned from the bottom,
+  // finds it when it lies within 254 of the minimum: the union's low end is
+  // dense (every item absent from one input sits at m1 + m2 or just above),
+  // and in the trees measured c* is the minimum or one above.  Otherwise a
+  // most-significant-digit radix select finds it, 8 bits a pass; two
+  // histogram buffers alternate, so a pass needs two barriers.
   const bool cut = U > k;
   u64 cstar = 0;
   uint32_t need = 0;
   if (cut) {
+    need = MG ? k + 1 : k;
+    u64 mn = EMPTY;
+    for (uint32_t u = tid; u < L; u += BS) {
+      const u64 c = s.uc[u];
+      mn = c < mn ? c : mn;  // EMPTY is the largest value
+    }
+    mn = block_reduce_u64<BS>(mn, s.red, false);
+    for (uint32_t base = 0; base < L; base += BS) {
+      const uint32_t u = base + tid;
+      const u64 c = u < L ? s.uc[u] : EMPTY;
+      const bool in = c != EMPTY;
+      if (__any_sync(0xffffffffu, in)) {
+        const uint32_t d = in ? (uint32_t)min(c - mn, (u64)255) : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (in && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s.hist[d], (uint32_t)__popc(peers));
+      }
+    }
+    if (tid < 256) s.hist[256 + tid] = 0;  // the radix select's first buffer
+    __syncthreads();
+    if (warp == 0) {
+      // lane l holds bins 8l .. 8l + 7; the total over all bins is U >= r
+      const uint32_t r = U - need + 1;
+      uint32_t v[8], sum = 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        v[t] = s.hist[8 * lane + t];
+        sum += v[t];
+      }
+      uint32_t inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
+      }
+      const unsigned reach = __ballot_sync(0xffffffffu, inc >= r);
+      if (lane == (uint32_t)(__ffs(reach) - 1)) {
+        uint32_t acc = inc - sum, b = 255;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          acc += v[t];
+          if (acc >= r) {
+            b = 8 * lane + t;
+            break;
+          }
+        }
+        // acc: entries with a count <= c*, so need - (U - acc) of those equal to c* are kept
+        sh_found = b < 255u;
+        sh_prefix = mn + b;
+        sh_need = need - (U - acc);
+      }
+    }
+    __syncthreads();
+  }
+  if (cut && sh_found) {
+    cstar = sh_prefix;
+    need = sh_need;
+  } else if (cut) {
     u64 mx = 0;
     for (uint32_t u = tid; u < L; u += BS) {
       const u64 c = s.uc[u];
@@ -313,8 +374,7 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     mx = block_reduce_u64<BS>(mx, s.red, true);
     int shift = ((63 - __clzll((long long)mx)) / 8) * 8;
     u64 prefix = 0, pmask = 0;
-    need = MG ? k + 1 : k;
-    for (uint32_t buf = 0; shift >= 0; shift -= 8, buf ^= 1u) {
+    for (uint32_t buf = 1; shift >= 0; shift -= 8, buf ^= 1u) {
       uint32_t* h = s.hist + 256 * buf;
       for (uint32_t base = 0; base < L; base += BS) {
         const uint32_t u = base + tid;
@@ -458,14 +518,12 @@ __device__ void merge_nodes(const SetView<ItemT>& A, uint32_t na, const SetView<
     O.size[no] = nkeep;
     O.m[no] = mout;
     O.ncov[no] = A.ncov[na] + B.ncov[nb];
-    if (STATUS) {
-      const uint32_t st = *A.status | *B.status;
-      if (st) atomicOr(O.status, st);
-    }
+    const uint32_t st = *A.status | *B.status;
+    if (st) atomicOr(O.status, st);
   }
 }
 
-template <typename ItemT, int BS, bool STATUS = true>
+template <typename ItemT, int BS>
 __device__ void copy_node(const SetView<ItemT>& in, uint32_t ni, const SetView<ItemT>& O,
                           uint32_t no) {
   const uint32_t k = O.k, sz = in.size[ni];
@@ -479,7 +537,7 @@ __device__ void copy_node(const SetView<ItemT>& in, uint32_t ni, const SetView<I
     O.size[no] = sz;
     O.m[no] = in.m[ni];
     O.ncov[no] = in.ncov[ni];
-    if (STATUS && *in.status) atomicOr(O.status, *in.status);
+    if (*in.status) atomicOr(O.status, *in.status);
   }
 }
 
@@ -520,47 +578,6 @@ __global__ void __launch_bounds__(BS) merge_tasks_kernel(const MergeDesc* __rest
     return;
   }
   merge_nodes<ItemT, BS, false, MG, STAGED>(in, 2 * j, in, 2 * j + 1, out, j, smem, nullptr);
-}
-
-// Every merge level of one tree in one launch.  CTA j builds node j of level
-// 1; a CTA that has finished a node of level L announces it on the parent's
-// arrival counter, and the CTA that completes the parent's inputs (the second
-// of two children, or the only one of a carried node) goes on to build the
-// parent.  No CTA waits for another: the others end.  The producer of the root
-// finishes last and writes every merge level's status word (the status of
-// level 0, which every level inherits).
-template <typename ItemT, int BS, bool MG, bool STAGED>
-__global__ void __launch_bounds__(BS) merge_tree_kernel(MergeTreeArgs t) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t go;
-  uint32_t j = blockIdx.x;
-  for (uint32_t L = 1;; ++L) {
-    const SetView<ItemT> in = set_view_dev<ItemT>(t.mem[L - 1], t.nodes[L - 1], t.k);
-    const SetView<ItemT> out = set_view_dev<ItemT>(t.mem[L], t.nodes[L], t.k);
-    if (2 * j + 1 >= in.nodes)
-      copy_node<ItemT, BS, false>(in, 2 * j, out, j);
-    else
-      merge_nodes<ItemT, BS, false, MG, STAGED, false>(in, 2 * j, in, 2 * j + 1, out, j, smem,
-                                                       nullptr);
-    if (L + 1 == t.levels) break;
-    // release this node, then count it at the parent
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const uint32_t parent = j >> 1;
-      const uint32_t children = 2 * parent + 1 < t.nodes[L] ? 2u : 1u;
-      go = atomicAdd(t.arrive + t.arrive_off[L] + parent, 1u) + 1u == children;
-    }
-    __syncthreads();
-    if (!go) return;
-    __threadfence();  // acquire the sibling's node
-    j >>= 1;
-  }
-  if (threadIdx.x == 0) {
-    const uint32_t st = *set_view_dev<ItemT>(t.mem[0], t.nodes[0], t.k).status;
-    for (uint32_t L = 1; L < t.levels; ++L)
-      *set_view_dev<ItemT>(t.mem[L], t.nodes[L], t.k).status = st;
-  }
 }
 
 template <typename ItemT, int BS>
@@ -633,41 +650,6 @@ cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream
   return e != cudaSuccess ? e : f;
 }
 
-uint32_t merge_tree_arrivals(const uint32_t* nodes, uint32_t levels, uint32_t* off) {
-  uint32_t total = 0;
-  for (uint32_t L = 0; L < levels; ++L) {
-    if (off) off[L] = total;
-    if (L >= 1 && L + 1 < levels) total += nodes[L + 1];
-  }
-  return total;
-}
-
-template <typename ItemT>
-cudaError_t launch_merge_tree(void* const* mems, const uint32_t* nodes, uint32_t levels,
-                              uint32_t k, uint32_t* arrive, cudaStream_t stream, bool mg) {
-  if (k > SS_SMEM_MAX_K || levels > MERGE_TREE_MAX_LEVELS) return cudaErrorInvalidValue;
-  if (levels < 2) return cudaSuccess;
-  MergeTreeArgs t{};
-  for (uint32_t L = 0; L < levels; ++L) {
-    t.mem[L] = mems[L];
-    t.nodes[L] = nodes[L];
-  }
-  merge_tree_arrivals(nodes, levels, t.arrive_off);
-  t.arrive = arrive;
-  t.levels = levels;
-  t.k = k;
-  const size_t smem = merge_smem_bytes<ItemT>(k);
-  const bool st = merge_staged<ItemT>(k);
-  auto kern = mg ? (st ? merge_tree_kernel<ItemT, MERGE_BS, true, true>
-                       : merge_tree_kernel<ItemT, MERGE_BS, true, false>)
-                 : (st ? merge_tree_kernel<ItemT, MERGE_BS, false, true>
-                       : merge_tree_kernel<ItemT, MERGE_BS, false, false>);
-  cudaError_t e = ensure_kernel_attrs((const void*)kern);
-  if (e != cudaSuccess) return e;
-  kern<<<nodes[1], MERGE_BS, smem, stream>>>(t);
-  return cudaGetLastError();
-}
-
 template <typename ItemT>
 cudaError_t launch_merge_pair(SetView<ItemT> a, uint32_t ia, SetView<ItemT> b, uint32_t ib,
                               SetView<ItemT> out, cudaStream_t stream, bool mg) {
@@ -729,10 +711,6 @@ template size_t merge_smem_bytes<u64>(uint32_t);
 template cudaError_t launch_merge_level<uint32_t>(SetView<uint32_t>, SetView<uint32_t>, cudaStream_t,
                                                   bool);
 template cudaError_t launch_merge_level<u64>(SetView<u64>, SetView<u64>, cudaStream_t, bool);
-template cudaError_t launch_merge_tree<uint32_t>(void* const*, const uint32_t*, uint32_t, uint32_t,
-                                                 uint32_t*, cudaStream_t, bool);
-template cudaError_t launch_merge_tree<u64>(void* const*, const uint32_t*, uint32_t, uint32_t,
-                                            uint32_t*, cudaStream_t, bool);
 template cudaError_t launch_merge_pair<uint32_t>(SetView<uint32_t>, uint32_t, SetView<uint32_t>,
                                                  uint32_t, SetView<uint32_t>, cudaStream_t, bool);
 template cudaError_t launch_merge_pair<u64>(SetView<u64>, uint32_t, SetView<u64>, uint32_t,

@@ -79,24 +79,6 @@ size_t merge_smem_bytes(uint32_t k);
 // One level of the reduction tree: out node j = combine(in node 2j, in node
 // 2j+1), or a copy of in node 2j when it has no partner.  mg: the merge of
 // Frequent (Misra–Gries) summaries of capacity in.k instead.
-// Every merge level of one tree (k <= SS_SMEM_MAX_K) in one launch: mems[L]
-// is the set of level L (nodes[L] nodes; level 0 written, its status word set;
-// the merge levels' status words are written by the launch), `arrive` holds
-// merge_tree_arrivals(nodes, levels) zeroed counters.
-constexpr uint32_t MERGE_TREE_MAX_LEVELS = 33;
-struct MergeTreeArgs {
-  void* mem[MERGE_TREE_MAX_LEVELS];
-  uint32_t nodes[MERGE_TREE_MAX_LEVELS];
-  uint32_t arrive_off[MERGE_TREE_MAX_LEVELS];
-  uint32_t* arrive;
-  uint32_t levels;
-  uint32_t k;
-};
-uint32_t merge_tree_arrivals(const uint32_t* nodes, uint32_t levels, uint32_t* off = nullptr);
-template <typename ItemT>
-cudaError_t launch_merge_tree(void* const* mems, const uint32_t* nodes, uint32_t levels,
-                              uint32_t k, uint32_t* arrive, cudaStream_t stream, bool mg);
-
 template <typename ItemT>
 cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream_t stream,
                                bool mg = false);
@@ -190,10 +172,10 @@ cudaError_t launch_summarize_warp_batch(const BatchStream* streams, const BatchT
 template <typename ItemT>
 int summarize_warp_ctas_per_sm(uint32_t k);
 
-// Resident CTAs per SM of the persistent CTA kernel for k counters, in the
-// shape ss_shape(k, true) picks (0 if it cannot run).
+// Resident CTAs per SM of the persistent CTA kernel for k counters and
+// ntasks blocks, in the shape the launch picks (0 if it cannot run).
 template <typename ItemT>
-int summarize_ctas_per_sm(uint32_t k);
+int summarize_ctas_per_sm(uint32_t k, uint64_t ntasks);
 
 // One CTA per task: node task.index of the next level of descriptor task.stream
 // (mg: the Frequent merge).

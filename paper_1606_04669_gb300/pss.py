@@ -534,7 +534,8 @@ def plan_kernel(k: int, count: int, item_bytes: int = 4) -> str:
 
 def plan_cta_shape(k: int, item_bytes: int = 4, batch: bool = False) -> tuple[int, int]:
     """pss_plan_cta_shape: (threads per CTA, items per thread) of the
-    window-parallel block-summary kernel for k counters."""
+    window-parallel block-summary kernel for k counters (launches of more
+    blocks than the wide shape keeps resident)."""
     t = ctypes.c_int()
     ipt = ctypes.c_int()
     _check(load().pss_plan_cta_shape(int(k), int(item_bytes), 1 if batch else 0, ctypes.byref(t),

@@ -118,13 +118,18 @@ def test_cta_shapes_in_order():
 @pytest.mark.parametrize("w", [4, 8])
 def test_cta_shape_boundaries(w):
     # Both sides of every shape switch, with cut windows (weak skew over a
-    # large universe) and with hits (strong skew over a small one).
+    # large universe) and with hits (strong skew over a small one).  Launches
+    # that fit on the SMs at once in the wide shape run it, so a few blocks of
+    # the k-sized state test the wide shape and 320 blocks (more than the 304
+    # wide CTAs a GB300 keeps resident below k ~ 2000) the shape of the switch.
     for last, first, _, _ in shape_switches(w):
         for k in (last, first):
             x = oracle.gen_zipf(180_000 + k, seed=900 + k, s=0.9, log2u=32, width=w)
             compare_tree(x, k, 3)
             y = oracle.gen_zipf(120_000, seed=950 + k, s=1.8, log2u=18, width=w)
             compare_tree(y, k, 2)
+            z = oracle.gen_zipf(320 * 1536 + k, seed=970 + k, s=0.9, log2u=32, width=w)
+            compare_tree(z, k, 320)
 
 
 def test_edge_empty_and_tiny():
@@ -183,6 +188,58 @@ def test_merge_api():
     with pytest.raises(P.PssError) as ei:
         P.merge(a, b)
     assert ei.value.code == P.PSS_EMISMATCH
+
+
+def select_edge_pair(rng, k: int, gap: int, w: int):
+    """Two summaries of disjoint items (fewer than k entries each, so m = 0
+    and every union count is the entry's own count) whose union keeps k of
+    U > k entries, with the cut value c* exactly `gap` above the union's
+    minimum, ties at c* on both sides of the cut."""
+    U = k + 1 + int(rng.integers(0, k - 2))   # <= 2k - 2: both sides fit below k
+    r = U - k + 1                      # c* is the r-th smallest
+    base = int(rng.integers(1, 1000))
+    low = [base] + [base + int(rng.integers(0, gap + 1)) for _ in range(r - 2)] if r >= 2 else []
+    cstar = base + gap
+    high = [cstar + (0 if rng.random() < 0.3 else int(rng.integers(1, 10_000))) for _ in range(U - r)]
+    counts = np.array(low + [cstar] + high, np.uint64)
+    rng.shuffle(counts)
+    hi_item = (1 << 32) if w == 4 else (1 << 40)
+    items = rng.choice(hi_item, size=U, replace=False).astype(np.uint64)
+    na = int(rng.integers(max(1, U - k + 1), k))   # both sides below k entries
+    parts = []
+    for it, ct in ((items[:na], counts[:na]), (items[na:], counts[na:])):
+        order = np.lexsort((it, -ct.astype(np.int64)))
+        parts.append(oracle.Summary(it[order], ct[order], np.zeros(len(it), np.uint64), 0,
+                                    int(ct.sum())))
+    return parts
+
+
+@pytest.mark.parametrize("w", [4, 8])
+def test_merge_select_both_paths(w):
+    # The combine finds c* with one histogram of distances from the union's
+    # minimum when c* lies within 254 of it, else with the radix select:
+    # distances on both sides of that edge, against Algorithm 2 in the oracle.
+    rng = np.random.default_rng(400 + w)
+    for gap in (0, 1, 253, 254, 255, 256, 70_000, 5_000_000_000):
+        for k in (3, 5, 100, 2000):
+            ra, rb = select_edge_pair(rng, k, gap, w)
+            da = P.import_summary(P.Exported(ra.item, ra.count, ra.err, 0, ra.n_covered), k, w)
+            db = P.import_summary(P.Exported(rb.item, rb.count, rb.err, 0, rb.n_covered), k, w)
+            e = P.merge(da, db).export()
+            rc = oracle.combine(ra, rb, k)
+            assert list(zip(e.item.tolist(), e.count.tolist(), e.err.tolist())) == \
+                summary_entries(rc), (gap, k)
+            assert (e.m, e.n_covered) == (rc.m, rc.n_covered), (gap, k)
+            # the Frequent merge selects the same way (k - 1 counters: the
+            # entries fit, and U > k - 1 cuts at the k-th largest)
+            fa = P.import_summary(P.Exported(ra.item, ra.count, ra.err, 0, ra.n_covered), k, w,
+                                  frequent=True)
+            fb = P.import_summary(P.Exported(rb.item, rb.count, rb.err, 0, rb.n_covered), k, w,
+                                  frequent=True)
+            f = P.merge(fa, fb).export()
+            rf = oracle.frequent_combine(ra, rb, k)
+            assert list(zip(f.item.tolist(), f.count.tolist())) == \
+                list(zip(rf.item.tolist(), rf.count.tolist())), ("frequent", gap, k)
 
 
 def test_argument_errors():
