@@ -447,7 +447,8 @@ void pss_free(pss_summary* summary);
  * a scheduler thread admits them while the device-memory budget and the
  * per-tick limit allow, so requests that arrive while others are on the GPU
  * join the next tick, and ticks overlap on the device (segment work on
- * alternating streams, tenant merges in order on one stream).  Results are
+ * streams taken in turn, each tenant's merges in order on the tenant's own
+ * stream; ticks complete in the order they finish).  Results are
  * independent of the mix: a request's results equal those of running its
  * tenant's requests alone, in order.
  */

@@ -9,13 +9,16 @@
 //     thread releases each at its time (open loop), admits released requests
 //     while the device-memory budget, the result slots and the per-tick limit
 //     allow, and enqueues one tick per admission round;
-//   * a tick's segment generation and summaries go to one of two segment
-//     streams (alternating), so consecutive ticks overlap on the device; the
-//     tenant merges and queries of every tick go, in arrival order, to one
-//     tenant stream, which waits for the tick's segments -- so every tenant
-//     sees its segments in arrival order whatever the mix;
+//   * a tick's segment generation and summaries go to one of NSEG segment
+//     streams (in turn), so consecutive ticks overlap on the device; the
+//     tenant merges and queries go, in arrival order, to the tenant's own
+//     stream (tenant t on tenant stream t mod NTEN), which waits for the
+//     tick's segments -- so every tenant sees its segments in arrival order
+//     whatever the mix, and a long segment of one tenant holds up only the
+//     tenants that share its tick or its tenant stream;
 //   * results land in pinned host slots; the scheduler completes a tick when
-//     its event has passed, in tick order.
+//     the events of every stream it used have passed, in whatever order the
+//     ticks finish.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -56,9 +59,12 @@ struct Admitted {
 
 struct Tick {
   std::vector<Admitted> reqs;
-  pss_batch* batch = nullptr;  // the tick's segment summaries
-  cudaEvent_t done = nullptr;
+  pss_batch* batch = nullptr;     // the tick's segment summaries
+  std::vector<cudaEvent_t> done;  // one per stream the tick used
 };
+
+constexpr int NSEG = 4;   // segment streams, taken in turn by the ticks
+constexpr int NTEN = 8;   // tenant streams (tenant t on t mod NTEN)
 
 struct Result {
   std::vector<pss_entry> seg, ten;
@@ -87,8 +93,8 @@ struct pss_server {
   std::vector<void*> tenant_mem[2];
   std::vector<int> tenant_cur;
   std::vector<uint64_t> tenant_items;
-  cudaStream_t seg_stream[2] = {nullptr, nullptr};
-  cudaStream_t tenant_stream = nullptr;
+  cudaStream_t seg_stream[NSEG] = {};
+  cudaStream_t tenant_stream[NTEN] = {};
   cudaStream_t plan_stream = nullptr;  // batch set-up, independent of segment work
   pss_entry* d_q = nullptr;    // per slot: 2 k entries
   uint32_t* d_qn = nullptr;    // per slot: 4 words
@@ -123,7 +129,7 @@ uint64_t request_bytes(const pss_request& r, uint32_t cap, uint32_t p) {
 void launch_tick(pss_server* sv, Tick& t) {
   const uint32_t k = sv->cfg.k, cap = sv->cap;
   const bool mg = sv->kind == PSS_KIND_FREQUENT;
-  cudaStream_t seg = sv->seg_stream[sv->ticks & 1];
+  cudaStream_t seg = sv->seg_stream[sv->ticks % NSEG];
   ++sv->ticks;
   const uint32_t nr = (uint32_t)t.reqs.size();
   std::vector<const void*> items(nr);
@@ -164,16 +170,22 @@ void launch_tick(pss_server* sv, Tick& t) {
     for (Admitted& a : t.reqs)
       if (a.status == PSS_OK) a.status = rc;
   }
+  // the generated items are read by the batch only (on seg)
+  for (Admitted& a : t.reqs)
+    if (a.gen) cudaFreeAsync(a.gen, seg);
   cudaEvent_t segs_done;
   cudaEventCreateWithFlags(&segs_done, cudaEventDisableTiming);
   cudaEventRecord(segs_done, seg);
-  cudaStreamWaitEvent(sv->tenant_stream, segs_done, 0);
-  cudaEventDestroy(segs_done);
-  cudaStream_t ts = sv->tenant_stream;
+  bool used[NTEN] = {};
   for (uint32_t i = 0; i < nr; ++i) {
     Admitted& a = t.reqs[i];
     if (a.status != PSS_OK) continue;
     const uint32_t T = a.r.tenant;
+    cudaStream_t ts = sv->tenant_stream[T % NTEN];
+    if (!used[T % NTEN]) {
+      cudaStreamWaitEvent(ts, segs_done, 0);
+      used[T % NTEN] = true;
+    }
     const int cur = sv->tenant_cur[T];
     void* in = sv->tenant_mem[cur][T];
     void* out = sv->tenant_mem[cur ^ 1][T];
@@ -208,18 +220,34 @@ void launch_tick(pss_server* sv, Tick& t) {
                           cudaMemcpyDeviceToHost, ts);
     if (e != cudaSuccess) a.status = from_cuda(e);
   }
-  for (Admitted& a : t.reqs)
-    if (a.gen) cudaFreeAsync(a.gen, ts);
-  cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
-  cudaEventRecord(t.done, ts);
+  cudaEventDestroy(segs_done);
+  auto mark = [&](cudaStream_t st) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return;
+    cudaEventRecord(ev, st);
+    t.done.push_back(ev);
+  };
+  mark(seg);
+  for (int j = 0; j < NTEN; ++j)
+    if (used[j]) mark(sv->tenant_stream[j]);
 }
 
-// Complete finished ticks in order (lock held by the caller).
+// Complete the ticks whose work has finished, in any order (lock held by
+// the caller).
 void reap(pss_server* sv) {
   const uint32_t k = sv->cfg.k;
-  while (!sv->inflight.empty()) {
-    Tick& t = sv->inflight.front();
-    if (cudaEventQuery(t.done) == cudaErrorNotReady) break;
+  for (size_t ti = 0; ti < sv->inflight.size();) {
+    Tick& t = sv->inflight[ti];
+    bool finished = true;
+    for (cudaEvent_t ev : t.done)
+      if (cudaEventQuery(ev) == cudaErrorNotReady) {
+        finished = false;
+        break;
+      }
+    if (!finished) {
+      ++ti;
+      continue;
+    }
     const double done = sv->now();
     for (Admitted& a : t.reqs) {
       pss_completion c{};
@@ -249,9 +277,9 @@ void reap(pss_server* sv) {
       sv->inflight_bytes -= a.bytes;
       ++sv->completed;
     }
-    cudaEventDestroy(t.done);
+    for (cudaEvent_t ev : t.done) cudaEventDestroy(ev);
     if (t.batch) pss_batch_free(t.batch);  // its work has completed
-    sv->inflight.pop_front();
+    sv->inflight.erase(sv->inflight.begin() + (std::ptrdiff_t)ti);
     sv->cv.notify_all();
   }
 }
@@ -325,11 +353,12 @@ void destroy(pss_server* sv) {
     sv->th.join();
   }
   cudaSetDevice(sv->dev);
-  if (sv->tenant_stream) cudaStreamSynchronize(sv->tenant_stream);
+  for (auto st : sv->tenant_stream)
+    if (st) cudaStreamSynchronize(st);
   for (auto st : sv->seg_stream)
     if (st) cudaStreamSynchronize(st);
   for (auto& t : sv->inflight)
-    if (t.done) cudaEventDestroy(t.done);
+    for (cudaEvent_t ev : t.done) cudaEventDestroy(ev);
   for (int b = 0; b < 2; ++b)
     for (void* m : sv->tenant_mem[b])
       if (m) cudaFree(m);
@@ -339,7 +368,8 @@ void destroy(pss_server* sv) {
   if (sv->h_qn) cudaFreeHost(sv->h_qn);
   for (auto& t : sv->inflight)
     if (t.batch) pss_batch_free(t.batch);
-  if (sv->tenant_stream) cudaStreamDestroy(sv->tenant_stream);
+  for (auto st : sv->tenant_stream)
+    if (st) cudaStreamDestroy(st);
   if (sv->plan_stream) {
     cudaStreamSynchronize(sv->plan_stream);
     cudaStreamDestroy(sv->plan_stream);
@@ -381,9 +411,10 @@ int server_create(const pss_server_config* cfg, pss_server** out, int kind) {
   if (e == cudaSuccess) e = cudaMalloc(&sv->d_qn, sizeof(uint32_t) * 4 * slots);
   if (e == cudaSuccess) e = cudaHostAlloc(&sv->h_q, sizeof(pss_entry) * 2 * k * slots, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc(&sv->h_qn, sizeof(uint32_t) * 4 * slots, cudaHostAllocDefault);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+  for (int i = 0; i < NSEG && e == cudaSuccess; ++i)
     e = cudaStreamCreateWithFlags(&sv->seg_stream[i], cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->tenant_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < NTEN && e == cudaSuccess; ++i)
+    e = cudaStreamCreateWithFlags(&sv->tenant_stream[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->plan_stream, cudaStreamNonBlocking);
   for (uint32_t i = 0; i < slots; ++i) sv->free_slots.push_back((uint32_t)(slots - 1 - i));
   if (e != cudaSuccess) {
@@ -511,7 +542,7 @@ extern "C" int pss_server_tenant_export(pss_server* sv, uint32_t tenant, pss_ent
   cudaError_t e = cudaMalloc(&d_out, sizeof(pss_entry) * k + 16);
   if (e != cudaSuccess) return from_cuda(e);
   uint32_t* d_n = (uint32_t*)((char*)d_out + sizeof(pss_entry) * k);
-  cudaStream_t ts = sv->tenant_stream;
+  cudaStream_t ts = sv->tenant_stream[tenant % NTEN];
   const SetLayout L = set_layout(1, k, 4);
   uint32_t hn[2] = {0, 0};
   uint64_t hm = 0, hc = 0;
