@@ -130,6 +130,8 @@ struct pss_batch {
   cudaStream_t capture = nullptr;  // the graph is captured here, launched on the caller's stream
   uint64_t graph_launches = 0;     // kernels per graph launch
   cudaEvent_t fork = nullptr;
+  cudaEvent_t ready = nullptr;            // the descriptors have landed (on the creating stream)
+  std::vector<std::vector<char>> staged;  // host images of the descriptors, kept until destroy
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -273,6 +275,10 @@ void destroy(pss_batch* b) {
     if (c.join) cudaEventDestroy(c.join);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->ready) {
+    cudaEventSynchronize(b->ready);  // the staged host images may still be read
+    cudaEventDestroy(b->ready);
+  }
   if (b->capture) {
     cudaStreamSynchronize(b->capture);
     cudaStreamDestroy(b->capture);
@@ -471,7 +477,6 @@ int batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out, int 
     destroy(b);
     return from_cuda(e);
   }
-  e = cudaStreamSynchronize(s);
   std::vector<BatchStream> bs(ns);
   std::vector<QueryDesc> qd(ns);
   for (uint32_t i = 0; i < ns && e == cudaSuccess; ++i) {
@@ -491,13 +496,20 @@ int batch_create(const pss_batch_desc* desc, void* stream, pss_batch** out, int 
           }
         }
   }
-  if (e == cudaSuccess) e = cudaMemcpy(b->arena + b->streams_off, bs.data(), sizeof(BatchStream) * ns, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->arena + b->qdesc_off, qd.data(), sizeof(QueryDesc) * ns, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !status_offs.empty())
-    e = cudaMemcpy(b->arena + b->status_offs_off, status_offs.data(), sizeof(size_t) * status_offs.size(), cudaMemcpyHostToDevice);
-  for (Pending& pd : uploads)
-    if (e == cudaSuccess && !pd.bytes.empty())
-      e = cudaMemcpy(b->arena + pd.off, pd.bytes.data(), pd.bytes.size(), cudaMemcpyHostToDevice);
+  // The descriptors go up in stream order after the arena's allocation; the
+  // host does not wait for them (a batch per serving tick would otherwise
+  // wait for the copy engine at every tick).  b->ready marks their arrival.
+  auto stage = [&](size_t o, const void* src, size_t bytes) {
+    if (e != cudaSuccess || bytes == 0) return;
+    b->staged.emplace_back((const char*)src, (const char*)src + bytes);
+    e = cudaMemcpyAsync(b->arena + o, b->staged.back().data(), bytes, cudaMemcpyHostToDevice, s);
+  };
+  stage(b->streams_off, bs.data(), sizeof(BatchStream) * ns);
+  stage(b->qdesc_off, qd.data(), sizeof(QueryDesc) * ns);
+  stage(b->status_offs_off, status_offs.data(), sizeof(size_t) * status_offs.size());
+  for (Pending& pd : uploads) stage(pd.off, pd.bytes.data(), pd.bytes.size());
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ready, s);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   for (KClass& c : b->kc) {
@@ -540,8 +552,16 @@ extern "C" int pss_batch_plan(const pss_batch* b, uint32_t* p) {
 extern "C" int pss_batch_run(pss_batch* b, int use_graph, void* stream) {
   if (!b) return PSS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (!use_graph) return b->w == 4 ? enqueue<uint32_t>(b, s) : enqueue<u64>(b, s);
+  if (!use_graph) {
+    const cudaError_t e = cudaStreamWaitEvent(s, b->ready, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    return b->w == 4 ? enqueue<uint32_t>(b, s) : enqueue<u64>(b, s);
+  }
   if (!b->exec) {
+    // the capture cannot wait on an event recorded outside it: the host waits
+    // once for the descriptors instead
+    cudaError_t e0 = cudaEventSynchronize(b->ready);
+    if (e0 != cudaSuccess) return from_cuda(e0);
     // Capture on the batch's own stream (the caller's may be the legacy
     // default stream, which cannot be captured); launches are counted per
     // replay, not at capture.
