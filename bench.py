@@ -539,6 +539,15 @@ def run_served(args, emit: bool = True):
     srv.close()
     lat = np.array([c["completed"] - c["arrival"] for c in comps])
     wait_q = np.array([c["admitted"] - c["arrival"] for c in comps])
+    n_of = {r.index: r.n for r in reqs}
+    seg_n = np.array([n_of[c["id"]] for c in comps])
+    by_len = {}
+    for lo, hi, name in ((1e4, 1e5, "1e4-1e5"), (1e5, 1e6, "1e5-1e6"), (1e6, 1e7 + 1, "1e6-1e7")):
+        sel = (seg_n >= lo) & (seg_n < hi)
+        if sel.any():
+            by_len[name] = {"requests": int(sel.sum()),
+                            "p50": float(np.percentile(lat[sel], 50) * 1e3),
+                            "p99": float(np.percentile(lat[sel], 99) * 1e3)}
     total = sum(r.n for r in reqs)
     t_end = max(c["completed"] for c in comps)
     bad = sum(1 for c in comps if c["status"] != 0)
@@ -549,7 +558,8 @@ def run_served(args, emit: bool = True):
                        "p99": float(np.percentile(lat, 99) * 1e3),
                        "max": float(lat.max() * 1e3),
                        "queue_p50": float(np.percentile(wait_q, 50) * 1e3),
-                       "queue_p99": float(np.percentile(wait_q, 99) * 1e3)},
+                       "queue_p99": float(np.percentile(wait_q, 99) * 1e3),
+                       "by_segment_items": by_len},
         "requests": len(comps), "errors": bad, "offered_items_per_s": total / args.duration,
         "generator_items_per_s": gen_rate,
         "makespan_s": t_end, "gpu_launches": launches, "clocks": clk,
