@@ -112,6 +112,21 @@ int run_tree(uint32_t k, uint32_t p, cudaStream_t s, bool keep, std::vector<void
   if (e != cudaSuccess) return fail(e);
   mems.push_back(m0);
   nodes.push_back(p);
+  // k in shared memory: every level's set is allocated (and its status word
+  // cleared) before the first kernel, so that the block summaries and the
+  // merge levels follow one another on the stream with nothing in between
+  // and each level can be launched as a programmatic dependent of the one
+  // before (at the cost of holding every level, about twice level 0's bytes)
+  const bool chained = k <= SS_SMEM_MAX_K;
+  if (chained)
+    for (uint32_t cur = p; cur > 1;) {
+      cur = (cur + 1) / 2;
+      void* mm = nullptr;
+      e = alloc_set(cur, k, w, s, &mm);
+      if (e != cudaSuccess) return fail(e);
+      mems.push_back(mm);
+      nodes.push_back(cur);
+    }
   {
     ProfScope prof(PROF_SUMMARIZE, s, 1);
     e = level0(set_view<ItemT>(m0, p, k));
@@ -120,6 +135,20 @@ int run_tree(uint32_t k, uint32_t p, cudaStream_t s, bool keep, std::vector<void
   uint32_t levels = 0;
   for (uint32_t w2 = p; w2 > 1; w2 = (w2 + 1) / 2) ++levels;
   ProfScope prof(PROF_MERGE, s, levels);
+  if (chained) {
+    for (size_t L = 1; L < mems.size(); ++L) {
+      e = launch_merge_level<ItemT>(set_view<ItemT>(mems[L - 1], nodes[L - 1], k),
+                                    set_view<ItemT>(mems[L], nodes[L], k), s, mg);
+      count_launches(1);
+      if (e != cudaSuccess) return fail(e);
+    }
+    if (!keep)
+      for (size_t i = 0; i + 1 < mems.size(); ++i) {
+        cudaFreeAsync(mems[i], s);
+        mems[i] = nullptr;
+      }
+    return PSS_OK;
+  }
   while (nodes.back() > 1) {
     const uint32_t cur = nodes.back(), nxt = (cur + 1) / 2;
     void* mm = nullptr;

@@ -545,6 +545,12 @@ template <typename ItemT, int BS, bool BIG, bool MG, bool STAGED>
 __global__ void __launch_bounds__(BS) merge_level_kernel(SetView<ItemT> in, SetView<ItemT> out,
                                                          unsigned char* gscratch, size_t gslice) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // Launched as a programmatic dependent of the previous level: wait until
+  // that grid has finished and its writes are visible, then let the next
+  // level's CTAs be scheduled (they wait the same way).  Without the launch
+  // attribute both instructions return at once.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const uint32_t j = blockIdx.x;
   if (2 * j + 1 >= in.nodes) {
     copy_node<ItemT, BS>(in, 2 * j, out, j);
@@ -635,8 +641,21 @@ cudaError_t launch_merge_level(SetView<ItemT> in, SetView<ItemT> out, cudaStream
                          : merge_level_kernel<ItemT, MERGE_BS, false, false, false>);
     cudaError_t e = ensure_kernel_attrs((const void*)kern);
     if (e != cudaSuccess) return e;
-    kern<<<out.nodes, MERGE_BS, smem, stream>>>(in, out, nullptr, 0);
-    return cudaGetLastError();
+    // programmatic dependent launch: the level's CTAs may be scheduled while
+    // the previous kernel on the stream drains (the kernel waits for it)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(out.nodes);
+    cfg.blockDim = dim3(MERGE_BS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    unsigned char* noscratch = nullptr;
+    size_t noslice = 0;
+    return cudaLaunchKernelEx(&cfg, kern, in, out, noscratch, noslice);
   }
   auto kern = merge_level_kernel<ItemT, MERGE_BS, true, false, false>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
