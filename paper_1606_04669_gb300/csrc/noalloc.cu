@@ -88,7 +88,7 @@ int run(const void* d_items, uint64_t n, uint32_t k, uint32_t p, void* out_items
   if (e == cudaSuccess) {
     count_launches(1);
     e = launch_summarize_blocks<ItemT>((const ItemT*)d_items, n, p, 0, p,
-                                       set_view<ItemT>(region[0], nodes, k), 0, s);
+                                       set_view<ItemT>(region[0], nodes, k), 0, s, false);
   }
   while (e == cudaSuccess && nodes > 1) {
     const uint32_t nxt = (nodes + 1) / 2;

@@ -69,9 +69,11 @@ int ss_shape(uint32_t k, bool batch);
 // Blocks r0 .. r0+count-1 of p (Algorithm 1 bounds over n items) into nodes
 // node0 .. node0+count-1 of `out`.
 template <typename ItemT>
+// may_allocate = false: k <= SS_SMEM_MAX_K keeps the whole state in shared
+// memory (no stream-ordered scratch is taken).
 cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
                                     uint32_t count, SetView<ItemT> out, uint32_t node0,
-                                    cudaStream_t stream);
+                                    cudaStream_t stream, bool may_allocate = true);
 
 template <typename ItemT>
 size_t merge_smem_bytes(uint32_t k);

@@ -1475,15 +1475,37 @@ int ss_launch_shape(uint32_t k, bool batch, uint64_t count) {
 
 }  // namespace
 
+// Whether a launch with k counters (k <= SS_SMEM_MAX_K) runs the large-k
+// form (part of the state in global scratch, table at <= 3/4 load): for
+// 2048 < k <= 3072, where it keeps two 512-thread CTAs per SM instead of one
+// (measured at n = 2^30, k = 3000: 15-28% less time at s = 0.5-2.0, equal
+// results; at k = 4000 it lost 15% at s = 0.5, so the range stops short).
+template <typename ItemT>
+bool use_large_k_form(uint32_t k) {
+  if (k <= 2048 || k > 3072) return false;
+  static std::atomic<int> memo[3072 - 2048 + 1];  // 1 + decision, 0 = not decided yet
+  std::atomic<int>& m = memo[k - 2049];
+  const int known = m.load(std::memory_order_relaxed);
+  if (known) return known == 2;
+  const int std_ctas = resident_ctas((const void*)ss_block_kernel<ItemT, SS_BS, SS_IPT, false>,
+                                     SS_BS, ss_smem_bytes<ItemT>(k));
+  const int big_ctas =
+      resident_ctas((const void*)ss_block_kernel<ItemT, SS_BS, SS_IPT, true>, SS_BS,
+                    ss_carve<ItemT, SS_BS, SS_IPT, true>(k, nullptr, nullptr, nullptr));
+  const bool big = big_ctas > std_ctas;
+  m.store(big ? 2 : 1, std::memory_order_relaxed);
+  return big;
+}
+
 template <typename ItemT>
 cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint32_t r0,
                                     uint32_t count, SetView<ItemT> out, uint32_t node0,
-                                    cudaStream_t stream) {
+                                    cudaStream_t stream, bool may_allocate) {
   if (out.k <= warp_kmax())
     return launch_summarize_warp_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
   if (use_round_kernel<ItemT>(out.k, count))
     return launch_summarize_round_blocks<ItemT>(items, n, p, r0, count, out, node0, stream);
-  if (out.k <= SS_SMEM_MAX_K) {
+  if (out.k <= SS_SMEM_MAX_K && !(may_allocate && use_large_k_form<ItemT>(out.k))) {
     const int shape = ss_launch_shape<ItemT>(out.k, false, count);
     const void* kern = block_kernel_of<ItemT>(shape);
     cudaError_t e = ensure_kernel_attrs(kern);
@@ -1502,7 +1524,7 @@ cudaError_t launch_summarize_blocks(const ItemT* items, u64 n, uint32_t p, uint3
     return cudaGetLastError();
   }
   // large k: a slice of global scratch per CTA, ordered on the stream
-  const size_t smem = ss_smem_bytes<ItemT>(out.k);
+  const size_t smem = ss_carve<ItemT, SS_BS, SS_IPT, true>(out.k, nullptr, nullptr, nullptr);
   auto kern = ss_block_kernel<ItemT, SS_BS, SS_IPT, true>;
   cudaError_t e = ensure_kernel_attrs((const void*)kern);
   if (e != cudaSuccess) return e;
@@ -1560,9 +1582,9 @@ template int ss_shape<uint32_t>(uint32_t, bool);
 template int ss_shape<u64>(uint32_t, bool);
 template cudaError_t launch_summarize_blocks<uint32_t>(const uint32_t*, u64, uint32_t, uint32_t,
                                                        uint32_t, SetView<uint32_t>, uint32_t,
-                                                       cudaStream_t);
+                                                       cudaStream_t, bool);
 template cudaError_t launch_summarize_blocks<u64>(const u64*, u64, uint32_t, uint32_t, uint32_t,
-                                                  SetView<u64>, uint32_t, cudaStream_t);
+                                                  SetView<u64>, uint32_t, cudaStream_t, bool);
 
 }  // namespace pss
 

@@ -83,6 +83,8 @@ def test_config1_full_tree():
     (70_000, 333, 31, 4, 0.5, 32, 109),       # nearly every item misses
     (150_000, 1024, 1, 8, 2.0, 32, 110),      # p = 1: plain sequential Space Saving
     (262_144, 2000, 1, 4, 1.1, 24, 2),        # one block of the 2^30 stream's shape
+    (300_000, 3000, 5, 4, 1.0, 32, 111),      # 2048 < k <= 3072: the large-k form in shared memory
+    (200_000, 2500, 3, 8, 1.5, 32, 112),
 ])
 def test_random_configs(n, k, p, w, s, log2u, seed):
     x = oracle.gen_zipf(n, seed=seed, s=s, log2u=log2u, width=w)
