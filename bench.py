@@ -80,15 +80,15 @@ WORKLOADS = {
 # block shape it was measured at.  Traffic grows with the number of blocks, so
 # a launch of p such blocks moves p times the per-block bytes.
 #   ss_block_kernel: profiles/ss_block_kernel_wave_k2000.md, 304 blocks of
-#     262144 u32 items, k = 2000 -> 319.29 MB read + 3.01 MB written.
+#     262144 u32 items, k = 2000 -> 319.19 MB read + 3.02 MB written.
 #   ssr_block_kernel: profiles/ssr_block_kernel_k256.md, 8192 blocks of 32768
 #     u32 items, k = 256 -> 1077.7 MB read + 32.5 MB written.
 #   frequent_block_kernel: profiles/frequent_block_kernel_wave_k2000.md, 1368
 #     blocks of 262144 u32 items, k = 2000 -> 1434.60 MB read + 3.76 MB written.
 TRAFFIC = {
     "ss_block_kernel": {"src": "summarize.cu",
-                        "sha1": "be3384881a6102eef7e918cf73c5874ca084459c",
-                        "bytes_per_block": (319.287e6 + 3.007e6) / 304, "block_items": 262144,
+                        "sha1": "958f8314d26b6998cc5b8c223972a560bd33cbad",
+                        "bytes_per_block": (319.187e6 + 3.016e6) / 304, "block_items": 262144,
                         "k": 2000, "w": 4},
     "ssr_block_kernel": {"src": "summarize_round.cu",
                          "sha1": "0e210092b09dbb8f0a1656928b774624097af347",
