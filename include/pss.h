@@ -583,7 +583,11 @@ int pss_plan_kernel(uint32_t k, uint32_t count, int item_bytes);
  * smaller launches run 256 x 2 as 512 x 2 (a launch that waits for no slot
  * takes as long as one block).  The summaries do not depend on the shape.
  * Queries the device's occupancy once per k.  PSS_EINVAL for invalid
- * arguments or null outputs; k above 4096 always reports 512 x 2. */
+ * arguments or null outputs; k above 4096 always reports 512 x 2.  This is
+ * the shape of the kernel that keeps the whole state in shared memory: for
+ * 2048 < k <= 3072 the plain path (batch == 0) runs the 512 x 2 form with
+ * part of the state in stream-ordered HBM scratch instead, where that keeps
+ * more CTAs resident (pss_summarize_noalloc never does). */
 int pss_plan_cta_shape(uint32_t k, int item_bytes, int batch, int* threads,
                        int* items_per_thread);
 
